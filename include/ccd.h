@@ -1,0 +1,184 @@
+/*
+ * ccd.h -- C ABI of the GB300 continuous-collision-detection library.
+ *
+ * The library computes, for two triangle meshes given at t = 0 and t = 1 with
+ * linear vertex trajectories and a shared topology, the earliest time of
+ * impact t* in [0, 1] (+inf when nothing collides), as defined in Section
+ * "Preliminaries" and Algorithm 1 (CCD = BuildBoxes, BroadPhase, NarrowPhase)
+ * of "Time of Impact Dataset for Continuous Collision Detection and a Scalable
+ * Conservative Algorithm" (Belgrod et al.).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA global-memory pointers on the context's device,
+ *     owned by the caller, never freed or retained by the library.
+ *   - V0, V1: FP64 vertex positions, structure of arrays [3][nV]: x[0..nV),
+ *     then y, then z.  E: int32 [nE][2] vertex ids.  F: int32 [nF][3].
+ *     Ids must lie in [0, nV); coordinates must be finite with magnitude
+ *     below 2^100 (the single-precision boxes and the error bound assume it).
+ *   - Box numbering: vertices 0..nV-1, edges nV..nV+nE-1, faces after.
+ *   - Pair lists: int32 [n][2].  Vertex-face pairs are (vertex id, face id);
+ *     edge-edge pairs are (lower edge id, higher edge id).
+ *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Calls return after enqueueing unless stated otherwise.
+ *   - Return value: a CCD_* status.  On an error nothing is guaranteed about
+ *     the outputs.  ccd_status_str() describes a status.
+ *   - A context is not thread-safe: one host thread and one stream at a time.
+ */
+#ifndef GB300_CCD_H
+#define GB300_CCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ccd_ctx ccd_ctx;
+
+enum {
+    CCD_OK = 0,
+    CCD_EINVAL = 1,    /* bad argument: null pointer, negative size, bad option */
+    CCD_ENOMEM = 2,    /* device allocation failed */
+    CCD_ETRUNC = 3,    /* an output list was too small; counts hold the sizes needed */
+    CCD_EQUEUE = 4,    /* the narrow-phase interval queue overflowed (work was kept
+                          on the lane that owned it, results stay correct) */
+    CCD_ETIMEOUT = 5,  /* a bounded device-side wait gave up; results are invalid */
+    CCD_ECUDA = 6,     /* a CUDA runtime call failed */
+    CCD_EDEVICE = 7    /* the device is not a compute capability 10.3 GPU */
+};
+
+/* Per-query flag bits written by ccd_narrow. */
+#define CCD_FLAG_ITER_CAP 1u   /* more than max_iter intervals: the TOI is the
+                                  earliest left end of the live intervals */
+#define CCD_FLAG_LEVEL_CAP 2u  /* an interval could not be split further
+                                  (53 levels on every axis); accepted as a hit */
+
+/* Options fixed at context creation (ccd_default_opts fills the defaults). */
+typedef struct {
+    double delta;            /* codomain tolerance of the stop rule w(B) < delta
+                                (Algorithm 3); default 1e-6 */
+    double min_sep;          /* minimum separation, added to the error box on every
+                                axis (Section "Avoiding Time of Impacts Equal to
+                                Zero"); default 0 */
+    int64_t max_iter;        /* per-query cap on processed intervals; default 1e6 */
+    int32_t broad_fp64;      /* 0 (default): single-precision outward-rounded boxes
+                                then an exact FP64 filter; 1: FP64 boxes throughout */
+    int32_t sweep_block;     /* threads per block of the sweep kernel (0 = auto) */
+    int64_t pair_capacity;   /* initial pair-buffer capacity used by ccd_step
+                                (0 = auto); grows on demand in synchronous calls */
+    int64_t queue_capacity;  /* interval-queue slots, a power of two (0 = auto) */
+    int32_t export_budget;   /* intervals a lane processes before handing its
+                                remaining intervals to the queue (0 = auto) */
+    int32_t profile_stages;  /* 1: record CUDA events around the stages of each
+                                call (read with ccd_stage_times); default 0 */
+} ccd_opts;
+
+/* Work counters of the last broad/narrow/step call (see ccd_get_status). */
+typedef struct {
+    int64_t n_boxes;         /* boxes built */
+    int32_t sweep_axis;      /* axis of largest centre variance (0 x, 1 y, 2 z) */
+    int32_t pad0;
+    int64_t n_superset;      /* pairs passing the single-precision box test */
+    int64_t n_vf, n_ee;      /* candidate pairs after the exact test */
+    int64_t n_intervals;     /* narrow-phase intervals evaluated */
+    int64_t n_exported;      /* intervals handed to the queue */
+    int64_t n_capped;        /* queries that hit max_iter */
+    int64_t queue_peak;      /* largest queue occupancy seen */
+    int32_t device_status;   /* CCD_* status raised by the kernels */
+    int32_t pad1;
+    int64_t n_launches;      /* kernels this context launched since creation */
+} ccd_stats;
+
+/* Fill *o with the defaults. */
+void ccd_default_opts(ccd_opts *o);
+
+/* Create a context on CUDA device `device`: checks the device, keeps a copy
+ * of *o (NULL = defaults) and allocates the fixed scratch (status words,
+ * counters).  Size-dependent scratch grows on first use.  *out receives the
+ * context; free it with ccd_destroy. */
+int ccd_create(ccd_ctx **out, const ccd_opts *o, int device);
+
+/* Release every device buffer of the context (synchronizes its device). */
+int ccd_destroy(ccd_ctx *ctx);
+
+/*
+ * Broad phase (Section "Broad-Phase", Algorithm 2, with the boxes of Section
+ * "Construction of the Boxes"): every vertex-face pair (v, f) with v not a
+ * vertex of f, and every edge-edge pair without a shared endpoint, whose
+ * boxes swept over [0, 1] overlap on all three axes (closed intervals).  The
+ * set is exactly the one defined by the FP64 extents (the single-precision
+ * sweep is followed by an exact FP64 test), returned in unspecified order.
+ *
+ * vf_out [vf_cap][2], ee_out [ee_cap][2]: device outputs.
+ * n_vf, n_ee: HOST pointers, receive the total numbers of pairs found.
+ * Synchronizes `stream`.  Returns CCD_ETRUNC when a total exceeds its
+ * capacity (only the first `cap` pairs were written; call again with room
+ * for the returned totals).
+ */
+int ccd_broad(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV,
+              const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
+              int32_t *vf_out, int64_t vf_cap, int64_t *n_vf,
+              int32_t *ee_out, int64_t ee_cap, int64_t *n_ee, void *stream);
+
+/*
+ * Narrow phase (Section "Narrow-Phase", Algorithm 3): conservative interval
+ * bisection over (t, u, v) with an FP64 inclusion function and error box, for
+ * the given pairs.  mode 0: each pair gets its own time of impact (toi_vf,
+ * toi_ee: device double [n], +inf for no collision; flags_vf, flags_ee:
+ * device uint8 [n], CCD_FLAG_* bits).  mode 1: only the earliest time over
+ * all pairs is wanted (Algorithm 3 as printed: one shared t* prunes every
+ * pair); the per-pair arrays may be NULL and are not meaningful.
+ * toi_min: device double [1], receives the earliest time over all pairs.
+ * delta, min_sep, max_iter override the context options for this call.
+ * Asynchronous; device errors are reported by ccd_get_status.
+ */
+int ccd_narrow(ccd_ctx *ctx, const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee,
+               const double *V0, const double *V1, int64_t nV,
+               const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
+               double delta, double min_sep, int64_t max_iter, int32_t mode,
+               double *toi_vf, double *toi_ee, uint8_t *flags_vf, uint8_t *flags_ee,
+               double *toi_min, void *stream);
+
+/*
+ * Whole CCD step (Algorithm 1): boxes, broad phase, earliest-TOI narrow phase,
+ * using the context's own pair buffers.  toi_min may be a device pointer
+ * (asynchronous; an overflow of the pair buffers is reported by
+ * ccd_get_status as CCD_ETRUNC and the result must then be discarded) or a
+ * host pointer (synchronous; the pair buffers are grown and the step rerun
+ * when they overflow, and the device status is returned).
+ */
+int ccd_step(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV,
+             const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
+             double delta, double min_sep, int64_t max_iter, double *toi_min, void *stream);
+
+/* Synchronize the context's last stream and read its device status and
+ * counters (stats may be NULL).  Returns the device status. */
+int ccd_get_status(ccd_ctx *ctx, ccd_stats *stats);
+
+/* Stages timed when opts.profile_stages is set. */
+enum { CCD_STAGE_BOXES = 0, CCD_STAGE_SORT = 1, CCD_STAGE_SWEEP = 2, CCD_STAGE_NARROW = 3, CCD_NSTAGES = 4 };
+
+/* Milliseconds spent in each stage by the last ccd_broad / ccd_narrow /
+ * ccd_step call (CUDA events on its stream; boxes = box build and axis
+ * choice, sort = keys, radix sort and gather, sweep = sweep with the exact
+ * filter, narrow = narrow-phase kernel); stages the call did not run read 0.
+ * Synchronizes the stream.  Returns CCD_EINVAL unless profile_stages was set. */
+int ccd_stage_times(ccd_ctx *ctx, double ms[CCD_NSTAGES]);
+
+/* Human-readable text of a CCD_* status (static storage). */
+const char *ccd_status_str(int status);
+
+/*
+ * Measure this device's FP64 fused-multiply-add throughput with a kernel of
+ * independent DFMA chains (the narrow phase's bound).  *gflops receives
+ * 2 x DFMA per second / 1e9.  Synchronous; allocates and frees its own
+ * small buffer.
+ */
+int ccd_measure_fp64_peak(int device, double *gflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_CCD_H */

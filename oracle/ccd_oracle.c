@@ -266,18 +266,37 @@ int oracle_broad_sweep(int64_t nV, int64_t nE, const int32_t *E, int64_t nF, con
     g_sort_lo32 = lo32;
     qsort(order, (size_t)nB, sizeof(int64_t), use32 ? cmp_box32 : cmp_box64);
 
+    /* The outer loop is split over OpenMP threads, each with its own list;
+     * the lists are concatenated and sorted, so the result does not depend on
+     * the thread count. */
     pairlist pl = {0};
-    for (int64_t s = 0; s < nB; ++s) {
-        int64_t i = order[s];
-        for (int64_t r = s + 1; r < nB; ++r) {
-            int64_t j = order[r];
-            if (use32 ? (lo32[3 * j + ax] > hi32[3 * i + ax]) : (lo64[3 * j + ax] > hi64[3 * i + ax]))
-                break; /* sorted: no later box can overlap on the sweep axis */
-            int ov = use32 ? overlap32(lo32, hi32, i, j) : overlap64(lo64, hi64, i, j);
-            if (ov && emit_if_candidate(&pl, i, j, nV, nE, E, F)) { free(order); return -1; }
+    int failed = 0;
+#pragma omp parallel
+    {
+        pairlist mine = {0};
+#pragma omp for schedule(dynamic, 512)
+        for (int64_t s = 0; s < nB; ++s) {
+            int64_t i = order[s];
+            for (int64_t r = s + 1; r < nB; ++r) {
+                int64_t j = order[r];
+                if (use32 ? (lo32[3 * j + ax] > hi32[3 * i + ax]) : (lo64[3 * j + ax] > hi64[3 * i + ax]))
+                    break; /* sorted: no later box can overlap on the sweep axis */
+                int ov = use32 ? overlap32(lo32, hi32, i, j) : overlap64(lo64, hi64, i, j);
+                if (ov && emit_if_candidate(&mine, i, j, nV, nE, E, F)) failed = 1;
+            }
         }
+#pragma omp critical
+        {
+            for (int64_t k = 0; k < mine.nvf && !failed; ++k)
+                if (push(&pl.vf, &pl.nvf, &pl.cap_vf, mine.vf[k].a, mine.vf[k].b)) failed = 1;
+            for (int64_t k = 0; k < mine.nee && !failed; ++k)
+                if (push(&pl.ee, &pl.nee, &pl.cap_ee, mine.ee[k].a, mine.ee[k].b)) failed = 1;
+        }
+        free(mine.vf);
+        free(mine.ee);
     }
     free(order);
+    if (failed) { free(pl.vf); free(pl.ee); return -1; }
     finish_lists(&pl, vf_out, vf_cap, n_vf, ee_out, ee_cap, n_ee);
     return 0;
 }
@@ -458,7 +477,10 @@ static double process_query(const query *q, double delta, int64_t max_iter, doub
         }
         double tl = dyadic(I.n[0], I.l[0]);
         if (tl >= tstar) continue;
-        if (q->vf && dyadic(I.n[1], I.l[1]) + dyadic(I.n[2], I.l[2]) > 1.0) continue;
+        /* u_lo + v_lo > 1, decided exactly: 1 - v_lo is a dyadic of at most
+         * 53 bits, so it and the comparison are exact in FP64 (the sum may
+         * round at the deepest levels). */
+        if (q->vf && dyadic(I.n[1], I.l[1]) > 1.0 - dyadic(I.n[2], I.l[2])) continue;
         if (++count > max_iter) {
             double m = tl;
             for (int s = 0; s < sp; ++s) {

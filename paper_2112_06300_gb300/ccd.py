@@ -1,0 +1,281 @@
+"""Python binding of the C ABI in include/ccd.h (argument marshalling only).
+
+Every function here forwards to libccd.so; device memory and streams come
+from PyTorch tensors.  There is no CPU path: importing works anywhere, but
+every call raises when the CUDA library or a CUDA device is missing.
+
+Layouts (as in include/ccd.h):
+  V0, V1   float64 CUDA tensors, shape (3, nV) (structure of arrays)
+  E        int32 CUDA tensor (nE, 2);  F int32 CUDA tensor (nF, 3)
+  pairs    int32 CUDA tensors (n, 2): vertex-face (v, f), edge-edge (e_lo, e_hi)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libccd.so")
+
+CCD_OK, CCD_EINVAL, CCD_ENOMEM, CCD_ETRUNC, CCD_EQUEUE, CCD_ETIMEOUT, CCD_ECUDA, CCD_EDEVICE = range(8)
+CCD_FLAG_ITER_CAP = 1
+CCD_FLAG_LEVEL_CAP = 2
+
+
+class ccd_opts(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("min_sep", ctypes.c_double),
+                ("max_iter", ctypes.c_int64), ("broad_fp64", ctypes.c_int32),
+                ("sweep_block", ctypes.c_int32), ("pair_capacity", ctypes.c_int64),
+                ("queue_capacity", ctypes.c_int64), ("export_budget", ctypes.c_int32),
+                ("profile_stages", ctypes.c_int32)]
+
+
+class ccd_stats(ctypes.Structure):
+    _fields_ = [("n_boxes", ctypes.c_int64), ("sweep_axis", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("n_superset", ctypes.c_int64), ("n_vf", ctypes.c_int64), ("n_ee", ctypes.c_int64),
+                ("n_intervals", ctypes.c_int64), ("n_exported", ctypes.c_int64),
+                ("n_capped", ctypes.c_int64), ("queue_peak", ctypes.c_int64),
+                ("device_status", ctypes.c_int32), ("pad1", ctypes.c_int32),
+                ("n_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
+
+
+class CCDError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {ccd_status_str(status)} (status {status})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libccd.so (built by paper_2112_06300_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2112_06300_gb300.build.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    L.ccd_default_opts.argtypes = [ctypes.POINTER(ccd_opts)]
+    L.ccd_default_opts.restype = None
+    L.ccd_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ccd_opts), ctypes.c_int]
+    L.ccd_destroy.argtypes = [P]
+    L.ccd_broad.argtypes = [P, P, P, i64, P, i64, P, i64, P, i64, ctypes.POINTER(i64), P, i64,
+                            ctypes.POINTER(i64), P]
+    L.ccd_narrow.argtypes = [P, P, i64, P, i64, P, P, i64, P, i64, P, i64, d, d, i64, i32,
+                             P, P, P, P, P, P]
+    L.ccd_step.argtypes = [P, P, P, i64, P, i64, P, i64, d, d, i64, P, P]
+    L.ccd_get_status.argtypes = [P, ctypes.POINTER(ccd_stats)]
+    L.ccd_status_str.argtypes = [ctypes.c_int]
+    L.ccd_status_str.restype = ctypes.c_char_p
+    L.ccd_measure_fp64_peak.argtypes = [ctypes.c_int, ctypes.POINTER(d)]
+    L.ccd_stage_times.argtypes = [P, ctypes.POINTER(d)]
+    for f in ("ccd_create", "ccd_destroy", "ccd_broad", "ccd_narrow", "ccd_step", "ccd_get_status",
+              "ccd_measure_fp64_peak", "ccd_stage_times"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc: int, where: str):
+    if rc != CCD_OK:
+        raise CCDError(rc, where)
+
+
+def ccd_status_str(status: int) -> str:
+    return lib().ccd_status_str(int(status)).decode()
+
+
+def ccd_default_opts() -> ccd_opts:
+    o = ccd_opts()
+    lib().ccd_default_opts(ctypes.byref(o))
+    return o
+
+
+def ccd_create(opts: Optional[ccd_opts] = None, device: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().ccd_create(ctypes.byref(h), ctypes.byref(opts) if opts is not None else None, device),
+           "ccd_create")
+    return h
+
+
+def ccd_destroy(ctx) -> None:
+    _check(lib().ccd_destroy(ctx), "ccd_destroy")
+
+
+def _mesh(V0, V1, E, F):
+    nV = V0.shape[1] if V0.numel() else 0
+    assert V0.dtype == V1.dtype and V0.shape == V1.shape and V0.is_contiguous() and V1.is_contiguous()
+    assert E.is_contiguous() and F.is_contiguous()
+    return nV, E.shape[0], F.shape[0]
+
+
+def ccd_broad(ctx, V0, V1, E, F, vf_out, ee_out, stream=None, check=True) -> Tuple[int, int, int]:
+    """Broad phase into caller buffers; returns (status, n_vf, n_ee) totals."""
+    nV, nE, nF = _mesh(V0, V1, E, F)
+    nvf, nee = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().ccd_broad(ctx, _ptr(V0), _ptr(V1), nV, _ptr(E), nE, _ptr(F), nF,
+                         _ptr(vf_out), vf_out.shape[0], ctypes.byref(nvf),
+                         _ptr(ee_out), ee_out.shape[0], ctypes.byref(nee), _stream(stream))
+    if check and rc not in (CCD_OK, CCD_ETRUNC):
+        raise CCDError(rc, "ccd_broad")
+    return rc, nvf.value, nee.value
+
+
+def ccd_narrow(ctx, vf, ee, V0, V1, E, F, delta, min_sep, max_iter, mode,
+               toi_vf, toi_ee, flags_vf, flags_ee, toi_min, stream=None) -> None:
+    nV, nE, nF = _mesh(V0, V1, E, F)
+    rc = lib().ccd_narrow(ctx, _ptr(vf), vf.shape[0], _ptr(ee), ee.shape[0], _ptr(V0), _ptr(V1), nV,
+                          _ptr(E), nE, _ptr(F), nF, float(delta), float(min_sep), int(max_iter), int(mode),
+                          _ptr(toi_vf), _ptr(toi_ee), _ptr(flags_vf), _ptr(flags_ee), _ptr(toi_min),
+                          _stream(stream))
+    _check(rc, "ccd_narrow")
+
+
+def ccd_step(ctx, V0, V1, E, F, delta, min_sep, max_iter, toi_min, stream=None) -> int:
+    """toi_min: a CUDA float64 tensor of one element (asynchronous) or a numpy
+    float64 array of one element (synchronous; returns the device status)."""
+    nV, nE, nF = _mesh(V0, V1, E, F)
+    if isinstance(toi_min, np.ndarray):
+        assert toi_min.dtype == np.float64 and toi_min.size >= 1 and toi_min.flags.c_contiguous
+        out = toi_min.ctypes.data_as(ctypes.c_void_p)
+    else:
+        out = _ptr(toi_min)
+    rc = lib().ccd_step(ctx, _ptr(V0), _ptr(V1), nV, _ptr(E), nE, _ptr(F), nF, float(delta), float(min_sep),
+                        int(max_iter), out, _stream(stream))
+    if rc not in (CCD_OK,):
+        raise CCDError(rc, "ccd_step")
+    return rc
+
+
+def ccd_get_status(ctx) -> Tuple[int, dict]:
+    st = ccd_stats()
+    rc = lib().ccd_get_status(ctx, ctypes.byref(st))
+    return rc, st.as_dict()
+
+
+STAGES = ("boxes", "sort", "sweep", "narrow")
+
+
+def ccd_stage_times(ctx) -> dict:
+    ms = (ctypes.c_double * 4)()
+    _check(lib().ccd_stage_times(ctx, ms), "ccd_stage_times")
+    return dict(zip(STAGES, list(ms)))
+
+
+def ccd_measure_fp64_peak(device: int = 0) -> float:
+    g = ctypes.c_double()
+    _check(lib().ccd_measure_fp64_peak(device, ctypes.byref(g)), "ccd_measure_fp64_peak")
+    return g.value
+
+
+# ----------------------------------------------------------------------------
+# Convenience layer over the same calls.
+# ----------------------------------------------------------------------------
+
+def mesh_to_device(V0, V1, E, F, device="cuda"):
+    """numpy (nV, 3) / (nE, 2) / (nF, 3) arrays -> device tensors in the
+    library's layout (positions transposed to (3, nV))."""
+    import torch
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+    V0d = t(np.asarray(V0, np.float64).T, torch.float64).contiguous()
+    V1d = t(np.asarray(V1, np.float64).T, torch.float64).contiguous()
+    Ed = t(np.asarray(E, np.int32).reshape(-1, 2), torch.int32)
+    Fd = t(np.asarray(F, np.int32).reshape(-1, 3), torch.int32)
+    return V0d, V1d, Ed, Fd
+
+
+@dataclass
+class NarrowResult:
+    toi_vf: "object"
+    toi_ee: "object"
+    flags_vf: "object"
+    flags_ee: "object"
+    toi_min: float
+
+
+class CCD:
+    """A context on one GPU with the library's calls as methods."""
+
+    def __init__(self, device: int = 0, **opts):
+        o = ccd_default_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.opts = o
+        self.device = device
+        self.ctx = ccd_create(o, device)
+
+    def close(self):
+        if self.ctx:
+            ccd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def broad(self, V0, V1, E, F, stream=None):
+        """Candidate pairs as int32 CUDA tensors (vf (n, 2), ee (m, 2)),
+        unordered; sized with one retry when the first guess is too small."""
+        import torch
+        dev = V0.device
+        cap = max(1024, 4 * (V0.shape[1] + E.shape[0] + F.shape[0]))
+        for _ in range(2):
+            vf = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+            ee = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+            rc, nvf, nee = ccd_broad(self.ctx, V0, V1, E, F, vf, ee, stream)
+            if rc == CCD_OK:
+                return vf[:nvf], ee[:nee]
+            cap = max(nvf, nee) + 1
+        raise CCDError(CCD_ETRUNC, "CCD.broad")
+
+    def narrow(self, vf, ee, V0, V1, E, F, delta=None, min_sep=None, max_iter=None, mode=0, stream=None):
+        import torch
+        dev = V0.device
+        delta = self.opts.delta if delta is None else delta
+        min_sep = self.opts.min_sep if min_sep is None else min_sep
+        max_iter = self.opts.max_iter if max_iter is None else max_iter
+        tv = torch.empty(vf.shape[0], dtype=torch.float64, device=dev)
+        te = torch.empty(ee.shape[0], dtype=torch.float64, device=dev)
+        fv = torch.empty(vf.shape[0], dtype=torch.uint8, device=dev)
+        fe = torch.empty(ee.shape[0], dtype=torch.uint8, device=dev)
+        tm = torch.empty(1, dtype=torch.float64, device=dev)
+        ccd_narrow(self.ctx, vf, ee, V0, V1, E, F, delta, min_sep, max_iter, mode, tv, te, fv, fe, tm, stream)
+        rc, _ = ccd_get_status(self.ctx)
+        _check(rc, "ccd_narrow (device)")
+        return NarrowResult(tv, te, fv, fe, float(tm.item()))
+
+    def step(self, V0, V1, E, F, delta=None, min_sep=None, max_iter=None, stream=None) -> float:
+        out = np.empty(1, np.float64)
+        ccd_step(self.ctx, V0, V1, E, F,
+                 self.opts.delta if delta is None else delta,
+                 self.opts.min_sep if min_sep is None else min_sep,
+                 self.opts.max_iter if max_iter is None else max_iter, out, stream)
+        return float(out[0])
+
+    def status(self):
+        return ccd_get_status(self.ctx)
+
+    def stage_times(self):
+        return ccd_stage_times(self.ctx)

@@ -1,0 +1,505 @@
+// Host runtime and C ABI (include/ccd.h): context, device scratch, launch
+// sequence of Algorithm 1 (boxes, broad phase, narrow phase), status.
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ccd_common.cuh"
+#include "ccd_kernels.cuh"
+
+using namespace ccd;
+
+struct ccd_ctx {
+  int device = 0;
+  ccd_opts opts{};
+  int sm_count = 0;
+  int narrow_blocks = 0;
+  DevCtl *ctl = nullptr;
+  // broad-phase scratch, sized for cap_boxes boxes
+  int64_t cap_boxes = 0;
+  void *broad_mem = nullptr;
+  BroadBufs bb{};
+  // pair buffers of ccd_step
+  int64_t pair_cap = 0;
+  int32_t *vf = nullptr, *ee = nullptr;
+  // narrow-phase scratch, sized for cap_q queries
+  int64_t cap_q = 0;
+  uint32_t *qflags = nullptr;
+  unsigned long long *qiters = nullptr;
+  RingCell *ring = nullptr;
+  unsigned long long ring_cap = 0;
+  cudaStream_t last_stream = nullptr;
+  int64_t last_nB = 0;
+  long long n_launches = 0;
+  // stage events: ev[2k] before stage k, ev[2k+1] after; ran[k] for the last call
+  cudaEvent_t ev[2 * CCD_NSTAGES] = {};
+  bool ran[CCD_NSTAGES] = {};
+};
+
+namespace {
+
+#define CK(call)                                                     \
+  do {                                                               \
+    cudaError_t e_ = (call);                                         \
+    if (e_ != cudaSuccess) {                                         \
+      std::fprintf(stderr, "ccd: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? CCD_ENOMEM : CCD_ECUDA; \
+    }                                                                \
+  } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline void mark(ccd_ctx *c, int stage, bool begin, cudaStream_t s) {
+  if (!c->opts.profile_stages) return;
+  cudaEventRecord(c->ev[2 * stage + (begin ? 0 : 1)], s);
+  if (!begin) c->ran[stage] = true;
+}
+inline void clear_marks(ccd_ctx *c) {
+  for (int k = 0; k < CCD_NSTAGES; ++k) c->ran[k] = false;
+}
+
+__global__ void k_reset_broad(DevCtl *c) {
+  c->n_vf = c->n_ee = c->n_superset = 0;
+  for (int i = 0; i < 6; ++i) c->var_sum[i] = 0;
+  c->axis = 0;
+}
+__global__ void k_reset_narrow(DevCtl *c) {
+  c->q_next = 0;
+  c->pending = 0;
+  c->toi_bits = 0x7FF0000000000000ull;
+  c->n_intervals = c->n_exported = c->n_capped = c->queue_peak = 0;
+}
+__global__ void k_reset_status(DevCtl *c) { c->status = CCD_OK; }
+
+// Pair counts of the broad phase clamped to the buffer capacities (ccd_step:
+// the narrow phase reads them on the device, no host round trip).
+__global__ void k_counts_from_broad(DevCtl *c, int64_t vf_cap, int64_t ee_cap) {
+  unsigned long long a = c->n_vf, b = c->n_ee;
+  c->pair_counts[0] = (long long)min(a, (unsigned long long)vf_cap);
+  c->pair_counts[1] = (long long)min(b, (unsigned long long)ee_cap);
+}
+
+int ensure_broad(ccd_ctx *c, int64_t nB) {
+  if (nB <= c->cap_boxes) return CCD_OK;
+  if (c->broad_mem) CK(cudaFree(c->broad_mem));
+  c->broad_mem = nullptr;
+  c->cap_boxes = 0;
+  int64_t cap = std::max<int64_t>(nB, 1024);
+  int64_t ntiles = cdiv(cap, kSortTile);
+  int64_t nbuild = cdiv(cap, kBuildThreads);
+  size_t bytes = 0;
+  auto take = [&](size_t n) { size_t off = bytes; bytes += (n + 255) & ~size_t(255); return off; };
+  size_t o_lo32 = take(3 * cap * sizeof(float)), o_hi32 = take(3 * cap * sizeof(float));
+  size_t o_lo64 = take(3 * cap * sizeof(long long)), o_hi64 = take(3 * cap * sizeof(long long));
+  size_t o_vid = take(cap * sizeof(int4));
+  size_t o_k0 = take(cap * 4), o_k1 = take(cap * 4), o_v0 = take(cap * 4), o_v1 = take(cap * 4);
+  size_t o_hist = take(256 * ntiles * 4);
+  size_t o_salo = take(cap * 4), o_sahi = take(cap * 4);
+  size_t o_soth = take(cap * sizeof(float4)), o_svid = take(cap * sizeof(int4));
+  size_t o_part = take(6 * nbuild * sizeof(float));
+  char *m = nullptr;
+  CK(cudaMalloc(&m, bytes));
+  c->broad_mem = m;
+  c->cap_boxes = cap;
+  BroadBufs &B = c->bb;
+  B.lo32 = (float *)(m + o_lo32);
+  B.hi32 = (float *)(m + o_hi32);
+  B.lo64 = (long long *)(m + o_lo64);
+  B.hi64 = (long long *)(m + o_hi64);
+  B.vid = (int4 *)(m + o_vid);
+  B.keys[0] = (uint32_t *)(m + o_k0);
+  B.keys[1] = (uint32_t *)(m + o_k1);
+  B.vals[0] = (uint32_t *)(m + o_v0);
+  B.vals[1] = (uint32_t *)(m + o_v1);
+  B.hist = (uint32_t *)(m + o_hist);
+  B.s_alo = (float *)(m + o_salo);
+  B.s_ahi = (float *)(m + o_sahi);
+  B.s_oth = (float4 *)(m + o_soth);
+  B.s_vid = (int4 *)(m + o_svid);
+  B.partials = (float *)(m + o_part);
+  return CCD_OK;
+}
+
+int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
+  if (!c->ring) {
+    unsigned long long cap = c->opts.queue_capacity > 0 ? (unsigned long long)c->opts.queue_capacity : (1ull << 21);
+    if (cap & (cap - 1)) return CCD_EINVAL;
+    CK(cudaMalloc(&c->ring, cap * sizeof(RingCell)));
+    c->ring_cap = cap;
+    // ring positions start at 0: cell i expects sequence number i
+    k_ring_init<<<(unsigned)std::min<unsigned long long>(cdiv(cap, 256), 4096), 256, 0, s>>>(c->ring, cap, 0);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(&c->ctl->q_head, 0, 2 * sizeof(unsigned long long), s));
+  }
+  if (nq <= c->cap_q) return CCD_OK;
+  if (c->qflags) CK(cudaFree(c->qflags));
+  if (c->qiters) CK(cudaFree(c->qiters));
+  c->qflags = nullptr;
+  c->qiters = nullptr;
+  c->cap_q = 0;
+  int64_t cap = std::max<int64_t>(nq, 1024);
+  CK(cudaMalloc(&c->qflags, cap * sizeof(uint32_t)));
+  CK(cudaMalloc(&c->qiters, cap * sizeof(unsigned long long)));
+  c->cap_q = cap;
+  return CCD_OK;
+}
+
+int ensure_pairs(ccd_ctx *c, int64_t cap) {
+  if (cap <= c->pair_cap) return CCD_OK;
+  if (c->vf) CK(cudaFree(c->vf));
+  if (c->ee) CK(cudaFree(c->ee));
+  c->vf = c->ee = nullptr;
+  c->pair_cap = 0;
+  CK(cudaMalloc(&c->vf, cap * 2 * sizeof(int32_t)));
+  CK(cudaMalloc(&c->ee, cap * 2 * sizeof(int32_t)));
+  c->pair_cap = cap;
+  return CCD_OK;
+}
+
+bool mesh_args_ok(const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+                  const int32_t *F, int64_t nF) {
+  if (nV < 0 || nE < 0 || nF < 0) return false;
+  if (nV + nE + nF >= (1ll << 31)) return false;
+  if (nV > 0 && (!V0 || !V1)) return false;
+  if ((nE > 0 && !E) || (nF > 0 && !F)) return false;
+  return true;
+}
+
+// Launch sequence of the broad phase.  Outputs go to vf_out/ee_out (counts in
+// ctl->n_vf / n_ee, unclamped).
+int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+                 const int32_t *F, int64_t nF, int32_t *vf_out, int64_t vf_cap, int32_t *ee_out, int64_t ee_cap,
+                 cudaStream_t s) {
+  const int64_t nB = nV + nE + nF;
+  int rc = ensure_broad(c, nB);
+  if (rc) return rc;
+  c->last_nB = nB;
+  k_reset_broad<<<1, 1, 0, s>>>(c->ctl);
+  if (nB == 0) {
+    c->n_launches += 1;
+    return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ECUDA;
+  }
+  BroadBufs B = c->bb;
+  const int nbuild = (int)cdiv(nB, kBuildThreads);
+  mark(c, CCD_STAGE_BOXES, true, s);
+  k_build_boxes<<<nbuild, kBuildThreads, 0, s>>>(nV, nE, nF, V0, V1, E, F, B);
+  k_axis_select<<<1, 1024, 0, s>>>(B.partials, nbuild, nB, c->ctl);
+  mark(c, CCD_STAGE_BOXES, false, s);
+  mark(c, CCD_STAGE_SORT, true, s);
+  const int grid = (int)std::min<int64_t>(cdiv(nB, 256), (int64_t)c->sm_count * 8);
+  k_make_keys<<<grid, 256, 0, s>>>(nB, B.lo32, c->ctl, B.keys[0], B.vals[0]);
+  const int ntiles = (int)cdiv(nB, kSortTile);
+  int cur = 0;
+  for (int shift = 0; shift < 32; shift += 8) {
+    k_radix_hist<<<ntiles, kSortThreads, 0, s>>>(B.keys[cur], nB, shift, B.hist, ntiles);
+    k_radix_scan<<<1, 1024, 0, s>>>(B.hist, 256 * ntiles);
+    k_radix_scatter<<<ntiles, kSortThreads, 0, s>>>(B.keys[cur], B.vals[cur], B.keys[cur ^ 1], B.vals[cur ^ 1],
+                                                    nB, shift, B.hist, ntiles);
+    cur ^= 1;
+  }
+  k_gather_sorted<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
+  mark(c, CCD_STAGE_SORT, false, s);
+  SweepArgs A;
+  A.nB = nB;
+  A.nV = nV;
+  A.nE = nE;
+  A.s_alo = B.s_alo;
+  A.s_ahi = B.s_ahi;
+  A.s_oth = B.s_oth;
+  A.s_vid = B.s_vid;
+  A.lo64 = B.lo64;
+  A.hi64 = B.hi64;
+  A.vf_out = vf_out;
+  A.ee_out = ee_out;
+  A.vf_cap = vf_cap;
+  A.ee_cap = ee_cap;
+  A.ctl = c->ctl;
+  const int sblock = c->opts.sweep_block > 0 ? c->opts.sweep_block : 256;
+  const int sgrid = (int)std::min<int64_t>(cdiv(nB * 32, sblock), (int64_t)c->sm_count * 32);
+  mark(c, CCD_STAGE_SWEEP, true, s);
+  k_sweep<<<sgrid, sblock, 0, s>>>(A);
+  mark(c, CCD_STAGE_SWEEP, false, s);
+  c->n_launches += 19;   // reset, build, axis, keys, 4 x (hist, scan, scatter), gather, sweep
+  CK(cudaGetLastError());
+  return CCD_OK;
+}
+
+int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee,
+                  int counts_from_ctl, const double *V0, const double *V1, int64_t nV, const int32_t *E,
+                  const int32_t *F, double delta, double min_sep, int64_t max_iter, int mode,
+                  unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s) {
+  const int64_t nq = n_vf + n_ee;
+  int rc = ensure_narrow(c, nq, s);
+  if (rc) return rc;
+  k_reset_narrow<<<1, 1, 0, s>>>(c->ctl);
+  NarrowArgs A;
+  A.ctl = c->ctl;
+  A.vf = vf;
+  A.ee = ee;
+  A.n_vf = n_vf;
+  A.n_ee = n_ee;
+  A.counts_from_ctl = counts_from_ctl;
+  A.V0 = V0;
+  A.V1 = V1;
+  A.nV = nV;
+  A.E = E;
+  A.F = F;
+  A.delta = delta;
+  A.min_sep = min_sep;
+  A.max_iter = max_iter;
+  A.mode = mode;
+  A.budget = c->opts.export_budget > 0 ? c->opts.export_budget : 64;
+  A.toi_vf_bits = toi_vf_bits;
+  A.toi_ee_bits = toi_ee_bits;
+  A.qflags = c->qflags;
+  A.qiters = c->qiters;
+  A.ring = c->ring;
+  A.ring_mask = c->ring_cap - 1;
+  mark(c, CCD_STAGE_NARROW, true, s);
+  k_narrow<<<c->narrow_blocks, kNarrowThreads, 0, s>>>(A);
+  mark(c, CCD_STAGE_NARROW, false, s);
+  c->n_launches += 2;    // reset, narrow
+  CK(cudaGetLastError());
+  return CCD_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ccd_default_opts(ccd_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->delta = 1e-6;
+  o->min_sep = 0.0;
+  o->max_iter = 1000000;
+  o->broad_fp64 = 0;
+  o->sweep_block = 0;
+  o->pair_capacity = 0;
+  o->queue_capacity = 0;
+  o->export_budget = 0;
+  o->profile_stages = 0;
+}
+
+int ccd_create(ccd_ctx **out, const ccd_opts *o, int device) {
+  if (!out) return CCD_EINVAL;
+  *out = nullptr;
+  ccd_opts opts;
+  ccd_default_opts(&opts);
+  if (o) opts = *o;
+  if (!(opts.delta >= 0) || !(opts.min_sep >= 0) || opts.max_iter < 0 || opts.broad_fp64 != 0) return CCD_EINVAL;
+  if (opts.profile_stages != 0 && opts.profile_stages != 1) return CCD_EINVAL;
+  if (opts.queue_capacity < 0 || (opts.queue_capacity & (opts.queue_capacity - 1))) return CCD_EINVAL;
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return CCD_EINVAL;
+  cudaDeviceProp p;
+  CK(cudaGetDeviceProperties(&p, device));
+  if (p.major != 10 || p.minor != 3) return CCD_EDEVICE;
+  CK(cudaSetDevice(device));
+  ccd_ctx *c = new (std::nothrow) ccd_ctx();
+  if (!c) return CCD_ENOMEM;
+  c->device = device;
+  c->opts = opts;
+  c->sm_count = p.multiProcessorCount;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow, kNarrowThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  c->narrow_blocks = per_sm * c->sm_count;
+  if (cudaMalloc(&c->ctl, sizeof(DevCtl)) != cudaSuccess) {
+    delete c;
+    return CCD_ENOMEM;
+  }
+  cudaMemset(c->ctl, 0, sizeof(DevCtl));
+  if (opts.profile_stages)
+    for (int k = 0; k < 2 * CCD_NSTAGES; ++k)
+      if (cudaEventCreate(&c->ev[k]) != cudaSuccess) {
+        cudaFree(c->ctl);
+        delete c;
+        return CCD_ECUDA;
+      }
+  *out = c;
+  return CCD_OK;
+}
+
+int ccd_destroy(ccd_ctx *c) {
+  if (!c) return CCD_EINVAL;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  cudaFree(c->broad_mem);
+  cudaFree(c->vf);
+  cudaFree(c->ee);
+  cudaFree(c->qflags);
+  cudaFree(c->qiters);
+  cudaFree(c->ring);
+  cudaFree(c->ctl);
+  for (int k = 0; k < 2 * CCD_NSTAGES; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  delete c;
+  return CCD_OK;
+}
+
+int ccd_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+              const int32_t *F, int64_t nF, int32_t *vf_out, int64_t vf_cap, int64_t *n_vf, int32_t *ee_out,
+              int64_t ee_cap, int64_t *n_ee, void *stream) {
+  if (!c || !n_vf || !n_ee || vf_cap < 0 || ee_cap < 0) return CCD_EINVAL;
+  if (!mesh_args_ok(V0, V1, nV, E, nE, F, nF)) return CCD_EINVAL;
+  if ((vf_cap > 0 && !vf_out) || (ee_cap > 0 && !ee_out)) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  clear_marks(c);
+  k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+  c->n_launches += 1;
+  int rc = launch_broad(c, V0, V1, nV, E, nE, F, nF, vf_out, vf_cap, ee_out, ee_cap, s);
+  if (rc) return rc;
+  unsigned long long h[2];
+  CK(cudaMemcpyAsync(h, &c->ctl->n_vf, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *n_vf = (int64_t)h[0];
+  *n_ee = (int64_t)h[1];
+  return ((int64_t)h[0] > vf_cap || (int64_t)h[1] > ee_cap) ? CCD_ETRUNC : CCD_OK;
+}
+
+int ccd_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee, const double *V0,
+               const double *V1, int64_t nV, const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
+               double delta, double min_sep, int64_t max_iter, int32_t mode, double *toi_vf, double *toi_ee,
+               uint8_t *flags_vf, uint8_t *flags_ee, double *toi_min, void *stream) {
+  if (!c || n_vf < 0 || n_ee < 0 || !toi_min || (mode != 0 && mode != 1)) return CCD_EINVAL;
+  if (!(delta >= 0) || !(min_sep >= 0) || max_iter < 0) return CCD_EINVAL;
+  if ((n_vf > 0 && (!vf || !F)) || (n_ee > 0 && (!ee || !E))) return CCD_EINVAL;
+  if (!mesh_args_ok(V0, V1, nV, E, nE, F, nF)) return CCD_EINVAL;
+  if (mode == 0 && ((n_vf > 0 && !toi_vf) || (n_ee > 0 && !toi_ee))) return CCD_EINVAL;
+  if (n_vf + n_ee >= (1ll << 32)) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  clear_marks(c);
+  k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+  c->n_launches += 1;
+  int rc = ensure_narrow(c, n_vf + n_ee, s);
+  if (rc) return rc;
+  // mode 1 keeps no per-pair results
+  unsigned long long *tv = mode == 0 ? (unsigned long long *)toi_vf : nullptr;
+  unsigned long long *te = mode == 0 ? (unsigned long long *)toi_ee : nullptr;
+  const int g = (int)std::min<int64_t>(cdiv(std::max<int64_t>(n_vf + n_ee, 1), 256), (int64_t)c->sm_count * 8);
+  rc = launch_narrow(c, vf, n_vf, ee, n_ee, 0, V0, V1, nV, E, F, delta, min_sep, max_iter, mode, tv, te, s);
+  if (rc) return rc;
+  if (mode == 0 && n_vf + n_ee > 0) {
+    k_flags_out<<<g, 256, 0, s>>>(c->qflags, n_vf, n_ee, flags_vf, flags_ee, c->ctl);
+    c->n_launches += 1;
+  }
+  CK(cudaMemcpyAsync(toi_min, &c->ctl->toi_bits, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaGetLastError());
+  return CCD_OK;
+}
+
+int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+             const int32_t *F, int64_t nF, double delta, double min_sep, int64_t max_iter, double *toi_min,
+             void *stream) {
+  if (!c || !toi_min || !(delta >= 0) || !(min_sep >= 0) || max_iter < 0) return CCD_EINVAL;
+  if (!mesh_args_ok(V0, V1, nV, E, nE, F, nF)) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const bool host_out = !is_device_ptr(toi_min);
+  int64_t want = c->opts.pair_capacity > 0 ? c->opts.pair_capacity : std::max<int64_t>(1 << 20, 8 * (nV + nE + nF));
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    int rc = ensure_pairs(c, want);
+    if (rc) return rc;
+    rc = ensure_narrow(c, 2 * c->pair_cap, s);
+    if (rc) return rc;
+    clear_marks(c);
+    k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+    rc = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, s);
+    if (rc) return rc;
+    k_counts_from_broad<<<1, 1, 0, s>>>(c->ctl, c->pair_cap, c->pair_cap);
+    c->n_launches += 2;
+    rc = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep,
+                       max_iter, 1, nullptr, nullptr, s);
+    if (rc) return rc;
+    if (!host_out) {
+      CK(cudaMemcpyAsync(toi_min, &c->ctl->toi_bits, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      return CCD_OK;
+    }
+    struct {
+      unsigned long long nvf, nee, toi;
+      int status;
+    } h;
+    CK(cudaMemcpyAsync(&h.nvf, &c->ctl->n_vf, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&h.toi, &c->ctl->toi_bits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&h.status, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if ((int64_t)h.nvf <= c->pair_cap && (int64_t)h.nee <= c->pair_cap) {
+      std::memcpy(toi_min, &h.toi, sizeof(double));
+      return h.status;
+    }
+    want = (int64_t)std::max(h.nvf, h.nee) + (int64_t)(std::max(h.nvf, h.nee) / 8) + 1024;
+  }
+  return CCD_ETRUNC;
+}
+
+int ccd_get_status(ccd_ctx *c, ccd_stats *st) {
+  if (!c) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  DevCtl h;
+  CK(cudaMemcpyAsync(&h, c->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->last_stream));
+  CK(cudaStreamSynchronize(c->last_stream));
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->n_boxes = c->last_nB;
+    st->sweep_axis = h.axis;
+    st->n_superset = (int64_t)h.n_superset;
+    st->n_vf = (int64_t)h.n_vf;
+    st->n_ee = (int64_t)h.n_ee;
+    st->n_intervals = (int64_t)h.n_intervals;
+    st->n_exported = (int64_t)h.n_exported;
+    st->n_capped = (int64_t)h.n_capped;
+    st->queue_peak = (int64_t)h.queue_peak;
+    st->device_status = h.status;
+    st->n_launches = c->n_launches;
+  }
+  return h.status;
+}
+
+int ccd_stage_times(ccd_ctx *c, double ms[CCD_NSTAGES]) {
+  if (!c || !ms || !c->opts.profile_stages) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->last_stream));
+  for (int k = 0; k < CCD_NSTAGES; ++k) {
+    ms[k] = 0.0;
+    if (!c->ran[k]) continue;
+    float f = 0.f;
+    CK(cudaEventElapsedTime(&f, c->ev[2 * k], c->ev[2 * k + 1]));
+    ms[k] = f;
+  }
+  return CCD_OK;
+}
+
+const char *ccd_status_str(int s) {
+  switch (s) {
+    case CCD_OK: return "ok";
+    case CCD_EINVAL: return "invalid argument";
+    case CCD_ENOMEM: return "device allocation failed";
+    case CCD_ETRUNC: return "output list too small (counts hold the sizes needed)";
+    case CCD_EQUEUE: return "narrow-phase interval queue overflowed";
+    case CCD_ETIMEOUT: return "a bounded device wait gave up; results invalid";
+    case CCD_ECUDA: return "CUDA runtime error";
+    case CCD_EDEVICE: return "device is not compute capability 10.3";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// Broad phase: boxes (Section "Construction of the Boxes") and
+// sweep-and-prune (Section "Broad-Phase", Algorithm 2).
+//
+//   k_build_boxes   one thread per box: FP64 extents over t = 0 and t = 1 of
+//                   the box's 1-3 vertices, single-precision box by directed
+//                   rounding (round-down / round-up, the same float the paper's
+//                   round-to-nearest-then-nextafterf rule gives), order-
+//                   preserving integer keys of the FP64 extents for the exact
+//                   test, and per-block sums for the centre variance.
+//   k_axis_select   axis of largest centre variance (affects speed only).
+//   k_radix_*       stable LSD radix sort of (key = ordered bits of the
+//                   minimum on the sweep axis, value = box id), 4 x 8 bits.
+//   k_gather_sorted box data in sorted order, structure of arrays.
+//   k_sweep         one warp per sorted box i: lanes test i against
+//                   j = i+1, i+2, ... while min_a(j) <= max_a(i), with the two
+//                   other axes, the vertex-face / edge-edge rule, the
+//                   shared-vertex filter and the exact FP64 box test fused;
+//                   surviving pairs are appended with one atomic per warp.
+
+#include "ccd_common.cuh"
+#include "ccd_kernels.cuh"
+
+namespace ccd {
+
+__global__ void __launch_bounds__(kBuildThreads)
+k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *__restrict__ V0,
+              const double *__restrict__ V1, const int32_t *__restrict__ E,
+              const int32_t *__restrict__ F, BroadBufs B) {
+  const int64_t nB = nV + nE + nF;
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float c[3] = {0.f, 0.f, 0.f};
+  if (b < nB) {
+    int ids[3] = {-1, -1, -1};
+    int k;
+    if (b < nV) {
+      ids[0] = (int)b;
+      k = 1;
+    } else if (b < nV + nE) {
+      ids[0] = __ldg(&E[2 * (b - nV)]);
+      ids[1] = __ldg(&E[2 * (b - nV) + 1]);
+      k = 2;
+    } else {
+      int64_t f = b - nV - nE;
+      ids[0] = __ldg(&F[3 * f]);
+      ids[1] = __ldg(&F[3 * f + 1]);
+      ids[2] = __ldg(&F[3 * f + 2]);
+      k = 3;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double lo = __ldg(&V0[a * nV + ids[0]]), hi = lo;
+      double x = __ldg(&V1[a * nV + ids[0]]);
+      lo = dmin_int(lo, x);
+      hi = dmax_int(hi, x);
+      for (int i = 1; i < k; ++i) {
+        double y0 = __ldg(&V0[a * nV + ids[i]]);
+        double y1 = __ldg(&V1[a * nV + ids[i]]);
+        lo = dmin_int(dmin_int(lo, y0), y1);
+        hi = dmax_int(dmax_int(hi, y0), y1);
+      }
+      float lo32 = __double2float_rd(lo);
+      float hi32 = __double2float_ru(hi);
+      B.lo32[a * nB + b] = lo32;
+      B.hi32[a * nB + b] = hi32;
+      B.lo64[a * nB + b] = f64_ord(lo);
+      B.hi64[a * nB + b] = f64_ord(hi);
+      c[a] = 0.5f * (lo32 + hi32);
+    }
+    B.vid[b] = make_int4(ids[0], ids[1], ids[2], (int)b);
+  }
+  // per-block sums of centres and squared centres (axis choice only)
+  float s[6] = {c[0], c[1], c[2], c[0] * c[0], c[1] * c[1], c[2] * c[2]};
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    for (int o = 16; o; o >>= 1) s[i] += __shfl_xor_sync(0xFFFFFFFFu, s[i], o);
+  __shared__ float red[kBuildThreads / 32][6];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int i = 0; i < 6; ++i) red[w][i] = s[i];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float t = 0.f;
+    for (int j = 0; j < kBuildThreads / 32; ++j) t += red[j][threadIdx.x];
+    B.partials[6 * blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl) {
+  __shared__ double acc[6][32];
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x)
+    for (int j = 0; j < 6; ++j) s[j] += (double)partials[6 * i + j];
+  for (int j = 0; j < 6; ++j)
+    for (int o = 16; o; o >>= 1) s[j] += __shfl_xor_sync(0xFFFFFFFFu, s[j], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int j = 0; j < 6; ++j) acc[j][threadIdx.x >> 5] = s[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[6];
+    for (int j = 0; j < 6; ++j) {
+      t[j] = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[j] += acc[j][w];
+    }
+    double inv = nB > 0 ? 1.0 / (double)nB : 0.0;
+    int best = 0;
+    double bv = -1.0;
+    for (int a = 0; a < 3; ++a) {
+      double mean = t[a] * inv;
+      double var = t[3 + a] * inv - mean * mean;
+      ctl->var_sum[a] = t[a];
+      ctl->var_sum[3 + a] = t[3 + a];
+      if (var > bv) { bv = var; best = a; }
+    }
+    ctl->axis = best;
+  }
+}
+
+__global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, uint32_t *keys, uint32_t *vals) {
+  const int a = ctl->axis;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nB; i += (int64_t)gridDim.x * blockDim.x) {
+    keys[i] = f32_sort_key(lo32[a * nB + i]);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+// ---- radix sort: histogram / scan / stable scatter, 8 bits per pass --------
+
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift, uint32_t *hist, int ntiles) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t i = base + r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];   // digit-major
+}
+
+// Exclusive scan of the digit-major histogram, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int total) {
+  __shared__ uint32_t part[1024];
+  const int per = (total + 1023) / 1024;
+  const int beg = threadIdx.x * per;
+  const int end = min(beg + per, total);
+  uint32_t s = 0;
+  for (int i = beg; i < end; ++i) s += hist[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int i = beg; i < end; ++i) {
+    uint32_t v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+// Stable scatter of one tile: rounds of 256 consecutive keys; within a round
+// each key's rank among equal digits comes from __match_any_sync (warp) plus
+// the counts of earlier warps and earlier rounds.
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
+                const uint32_t *__restrict__ offsets, int ntiles) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ uint32_t run[256];              // running position per digit
+  __shared__ uint32_t wcnt[kWarps][256];     // per-warp digit counts of the round
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  run[threadIdx.x] = offsets[threadIdx.x * ntiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortItems; ++r) {
+    for (int j = 0; j < kWarps; ++j) wcnt[j][threadIdx.x] = 0;
+    __syncthreads();
+    int64_t i = base + r * kSortThreads + threadIdx.x;
+    bool valid = i < n;
+    uint32_t key = valid ? keys_in[i] : 0;
+    uint32_t val = valid ? vals_in[i] : 0;
+    uint32_t d = valid ? (key >> shift) & 0xFF : 256u + lane;   // invalid lanes never match
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    // exclusive prefix over warps for this thread's digit column
+    uint32_t before = 0, tot = 0;
+    {
+      uint32_t col = threadIdx.x;
+      uint32_t acc = 0;
+      for (int j = 0; j < kWarps; ++j) {
+        uint32_t c = wcnt[j][col];
+        wcnt[j][col] = acc;
+        acc += c;
+      }
+      tot = acc;
+    }
+    __syncthreads();
+    if (valid) {
+      before = wcnt[w][d];
+      uint32_t pos = run[d] + before + rank;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+    run[threadIdx.x] += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_gather_sorted(int64_t nB, const uint32_t *__restrict__ perm, const DevCtl *ctl, BroadBufs B) {
+  const int a = ctl->axis, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nB; s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = perm[s];
+    B.s_alo[s] = B.lo32[a * nB + b];
+    B.s_ahi[s] = B.hi32[a * nB + b];
+    B.s_oth[s] = make_float4(B.lo32[a1 * nB + b], B.hi32[a1 * nB + b], B.lo32[a2 * nB + b], B.hi32[a2 * nB + b]);
+    B.s_vid[s] = B.vid[b];
+  }
+}
+
+// ---- sweep ------------------------------------------------------------------
+
+__device__ __forceinline__ int box_kind(int b, int64_t nV, int64_t nE) {
+  return b < nV ? 0 : (b < nV + nE ? 1 : 2);   // vertex, edge, face
+}
+
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nB = A.nB;
+  for (int64_t i = warp; i < nB; i += nwarps) {
+    const float ahi = A.s_ahi[i];
+    const float4 oi = A.s_oth[i];
+    const int4 vi = A.s_vid[i];
+    const int bi = vi.w;
+    const int ki = box_kind(bi, A.nV, A.nE);
+    long long ilo[3], ihi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ilo[a] = A.lo64[a * nB + bi];
+      ihi[a] = A.hi64[a * nB + bi];
+    }
+    for (int64_t j0 = i + 1;; j0 += 32) {
+      const int64_t j = j0 + lane;
+      const float alo = j < nB ? A.s_alo[j] : __int_as_float(0x7F800000);
+      const bool in_a = alo <= ahi;
+      const unsigned run = __ballot_sync(0xFFFFFFFFu, in_a);
+      bool is_vf = false, is_ee = false, sup = false;
+      int p0 = 0, p1 = 0;
+      if (in_a) {
+        const float4 oj = A.s_oth[j];
+        if (oj.x <= oi.y && oi.x <= oj.y && oj.z <= oi.w && oi.z <= oj.w) {
+          const int4 vj = A.s_vid[j];
+          const int bj = vj.w;
+          const int kj = box_kind(bj, A.nV, A.nE);
+          const bool vfp = (ki == 0 && kj == 2) || (ki == 2 && kj == 0);
+          const bool eep = ki == 1 && kj == 1;
+          if (vfp || eep) {
+            // shared-vertex filter (i padded with -1, j with -2: no false match)
+            int j0v = vj.x, j1v = vj.y < 0 ? -2 : vj.y, j2v = vj.z < 0 ? -2 : vj.z;
+            bool share = false;
+            const int iv[3] = {vi.x, vi.y, vi.z};
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+              share |= (iv[u] == j0v) | (iv[u] == j1v) | (iv[u] == j2v);
+            if (!share) {
+              sup = true;
+              bool ov = true;
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                long long jlo = A.lo64[a * nB + bj], jhi = A.hi64[a * nB + bj];
+                ov &= (jlo <= ihi[a]) & (ilo[a] <= jhi);
+              }
+              if (ov) {
+                if (vfp) {
+                  is_vf = true;
+                  p0 = ki == 0 ? bi : bj;
+                  p1 = (int)((ki == 2 ? bi : bj) - A.nV - A.nE);
+                } else {
+                  is_ee = true;
+                  int e1 = (int)(bi - A.nV), e2 = (int)(bj - A.nV);
+                  p0 = min(e1, e2);
+                  p1 = max(e1, e2);
+                }
+              }
+            }
+          }
+        }
+      }
+      const unsigned mask = 0xFFFFFFFFu;
+      const unsigned bs = __ballot_sync(mask, sup);
+      if (bs && lane == 0) atomicAdd(&A.ctl->n_superset, (unsigned long long)__popc(bs));
+      if (__any_sync(mask, is_vf)) {
+        unsigned long long at = warp_append(&A.ctl->n_vf, is_vf, mask);
+        if (is_vf && (int64_t)at < A.vf_cap) {
+          A.vf_out[2 * at] = p0;
+          A.vf_out[2 * at + 1] = p1;
+        }
+      }
+      if (__any_sync(mask, is_ee)) {
+        unsigned long long at = warp_append(&A.ctl->n_ee, is_ee, mask);
+        if (is_ee && (int64_t)at < A.ee_cap) {
+          A.ee_out[2 * at] = p0;
+          A.ee_out[2 * at + 1] = p1;
+        }
+      }
+      if (run != 0xFFFFFFFFu) break;   // sorted: later boxes start beyond max_a(i)
+    }
+  }
+}
+
+}  // namespace ccd

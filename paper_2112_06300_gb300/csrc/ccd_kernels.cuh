@@ -1,0 +1,106 @@
+// Kernel interfaces and the device control block shared by the host runtime.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ccd.h"
+
+namespace ccd {
+
+// Device-resident control block: counters, status and the shared t*.  One
+// per context; reset (partially) by the host before each call.
+struct DevCtl {
+  // broad phase
+  unsigned long long n_vf, n_ee, n_superset;
+  double var_sum[6];             // sum of centres and squared centres per axis
+  int axis;
+  int status;                    // CCD_* raised by kernels (first error wins)
+  // narrow phase
+  unsigned long long q_next;     // next query to hand out
+  unsigned long long q_head, q_tail;  // ring positions (monotonic, never reset)
+  unsigned long long pending;    // units fetched or queued and not finished
+  unsigned long long toi_bits;   // earliest t* so far, bits of a non-negative double
+  unsigned long long n_intervals, n_exported, n_capped, queue_peak;
+  long long pair_counts[2];      // ccd_step: pairs for the narrow phase (clamped)
+};
+
+struct RingCell {
+  unsigned long long seq;
+  unsigned long long w[3];       // numerator | level << 54, for t, u, v
+  uint32_t q;
+  uint32_t pad;
+};
+
+constexpr int kNarrowThreads = 128;
+
+struct NarrowArgs {
+  DevCtl *ctl;
+  const int32_t *vf;             // [n_vf][2]
+  const int32_t *ee;             // [n_ee][2]
+  int64_t n_vf, n_ee;
+  int counts_from_ctl;           // 1: take n_vf, n_ee from ctl->pair_counts
+  const double *V0, *V1;         // [3][nV]
+  int64_t nV;
+  const int32_t *E, *F;
+  double delta, min_sep;
+  long long max_iter;
+  int mode;                      // 0 per pair, 1 earliest only
+  int budget;                    // intervals before a lane hands out its work
+  unsigned long long *toi_vf_bits, *toi_ee_bits;   // mode 0 outputs (bits of doubles)
+  uint32_t *qflags;              // [n_vf + n_ee] scratch
+  unsigned long long *qiters;    // [n_vf + n_ee] scratch
+  RingCell *ring;
+  unsigned long long ring_mask;  // capacity - 1
+};
+
+__global__ void k_narrow(NarrowArgs A);
+__global__ void k_ring_init(RingCell *ring, unsigned long long cap, unsigned long long base);
+__global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v);
+__global__ void k_flags_out(const uint32_t *qflags, int64_t n_vf, int64_t n_ee, uint8_t *flags_vf,
+                            uint8_t *flags_ee, DevCtl *ctl);
+
+// ---- broad phase ----
+constexpr int kBuildThreads = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;                  // keys per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+struct BroadBufs {
+  // by box id
+  float *lo32, *hi32;            // [3][nB]
+  long long *lo64, *hi64;        // [3][nB] ordered FP64 keys
+  int4 *vid;                     // [nB] (v0, v1, v2, box id), -1 padded
+  // sort
+  uint32_t *keys[2], *vals[2];   // [nB]
+  uint32_t *hist;                // [256 * nTiles]
+  // sorted by the minimum on the sweep axis
+  float *s_alo, *s_ahi;          // [nB]
+  float4 *s_oth;                 // [nB] (lo1, hi1, lo2, hi2)
+  int4 *s_vid;                   // [nB]
+  float *partials;               // [6 * nBuildBlocks]
+};
+
+__global__ void k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *V0, const double *V1,
+                              const int32_t *E, const int32_t *F, BroadBufs B);
+__global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl);
+__global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, uint32_t *keys, uint32_t *vals);
+__global__ void k_radix_hist(const uint32_t *keys, int64_t n, int shift, uint32_t *hist, int ntiles);
+__global__ void k_radix_scan(uint32_t *hist, int total);
+__global__ void k_radix_scatter(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
+                                uint32_t *vals_out, int64_t n, int shift, const uint32_t *offsets, int ntiles);
+__global__ void k_gather_sorted(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
+
+struct SweepArgs {
+  int64_t nB, nV, nE;
+  const float *s_alo, *s_ahi;
+  const float4 *s_oth;
+  const int4 *s_vid;
+  const long long *lo64, *hi64;  // [3][nB] by box id
+  int32_t *vf_out, *ee_out;
+  int64_t vf_cap, ee_cap;
+  DevCtl *ctl;
+};
+__global__ void k_sweep(SweepArgs A);
+
+}  // namespace ccd

@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Broad phase: the pair set is compared exactly (sorted; the GPU returns it in
+unspecified order), and the single-precision superset count equals the
+oracle's single-precision pair set.  Narrow phase: per-pair times of impact
+are bit-identical on every pair neither side flagged (the result of an
+uncapped query does not depend on the traversal order), flags agree, and the
+earliest time is bit-identical.  Sizes span several tiles and ragged tails;
+edge cases: empty inputs, vertices only, forced queue hand-offs, a tiny
+queue, max_iter = 0, min_sep > 0."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2112_06300_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ccd():
+    from paper_2112_06300_gb300 import build
+    build.build()
+    from paper_2112_06300_gb300 import ccd as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(ccd):
+    c = ccd.CCD(0)
+    yield c
+    c.close()
+
+
+def sorted_pairs(t):
+    a = t.cpu().numpy().astype(np.int64).reshape(-1, 2)
+    return a[np.lexsort((a[:, 1], a[:, 0]))] if len(a) else a
+
+
+def random_scene(seed, nv=300, nf=250, motion=0.05):
+    rng = np.random.default_rng(seed)
+    V0 = rng.uniform(-1, 1, (nv, 3))
+    V1 = V0 + rng.normal(0, motion, (nv, 3))
+    F = np.array([rng.choice(nv, 3, replace=False) for _ in range(nf)], np.int32)
+    return scenes.Scene(V0, V1, scenes.edges_of(F), F, {"name": f"random-{seed}"})
+
+
+def scene_list():
+    out = [scenes.icosphere_on_plane(0),                       # 21,635 boxes
+           scenes.icosphere_on_plane(3, level=2, plane_n=9),
+           scenes.folded_cloth(40, seed=1),
+           scenes.folded_cloth(97, seed=4),                    # ragged sort tiles
+           random_scene(0), random_scene(1, nv=31, nf=7)]
+    return out
+
+
+SCENES = scene_list()
+
+
+@pytest.mark.parametrize("s", SCENES, ids=[s.info["name"] + str(i) for i, s in enumerate(SCENES)])
+def test_broad_pairs_match_oracle(ctx, ccd, s):
+    V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+    vf, ee = ctx.broad(V0, V1, E, F)
+    ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+    np.testing.assert_array_equal(sorted_pairs(vf), ovf)
+    np.testing.assert_array_equal(sorted_pairs(ee), oee)
+    rc, st = ctx.status()
+    assert rc == 0
+    v32, e32 = O.broad(s.V0, s.V1, s.E, s.F, fp32=True)
+    assert st["n_superset"] == len(v32) + len(e32)
+    assert st["n_boxes"] == s.n_boxes
+
+
+def test_broad_empty_and_vertices_only(ctx, ccd):
+    z = np.zeros((0, 3))
+    V0, V1, E, F = ccd.mesh_to_device(z, z, np.zeros((0, 2), np.int32), np.zeros((0, 3), np.int32))
+    vf, ee = ctx.broad(V0, V1, E, F)
+    assert vf.shape[0] == 0 and ee.shape[0] == 0
+    pts = np.random.default_rng(0).uniform(0, 1, (500, 3))
+    V0, V1, E, F = ccd.mesh_to_device(pts, pts, np.zeros((0, 2), np.int32), np.zeros((0, 3), np.int32))
+    vf, ee = ctx.broad(V0, V1, E, F)
+    assert vf.shape[0] == 0 and ee.shape[0] == 0
+
+
+def test_broad_truncation_reports_totals(ctx, ccd):
+    s = scenes.icosphere_on_plane(0)
+    V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+    ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+    vf = torch.empty((10, 2), dtype=torch.int32, device="cuda")
+    ee = torch.empty((10, 2), dtype=torch.int32, device="cuda")
+    rc, nvf, nee = ccd.ccd_broad(ctx.ctx, V0, V1, E, F, vf, ee)
+    assert rc == ccd.CCD_ETRUNC
+    assert (nvf, nee) == (len(ovf), len(oee))
+    got = {tuple(p) for p in vf.cpu().numpy().tolist()}
+    assert got <= {tuple(p) for p in ovf.tolist()}
+
+
+def _narrow_both(ctx, ccd, s, vf, ee, delta=1e-6, ms=0.0, max_iter=10 ** 6, mode=0):
+    V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+    vfd = torch.from_numpy(np.ascontiguousarray(vf, np.int32)).cuda().reshape(-1, 2)
+    eed = torch.from_numpy(np.ascontiguousarray(ee, np.int32)).cuda().reshape(-1, 2)
+    r = ctx.narrow(vfd, eed, V0, V1, E, F, delta, ms, max_iter, mode)
+    o = O.narrow(vf, ee, s.V0, s.V1, s.E, s.F, delta, ms, max_iter, mode)
+    return r, o
+
+
+def _assert_per_pair(r, o):
+    g = np.concatenate([r.toi_vf.cpu().numpy(), r.toi_ee.cpu().numpy()])
+    gf = np.concatenate([r.flags_vf.cpu().numpy(), r.flags_ee.cpu().numpy()])
+    t = np.concatenate([o[0], o[1]])
+    f = np.concatenate([o[2], o[3]])
+    both = (gf == 0) & (f == 0)
+    assert both.mean() > 0.99
+    np.testing.assert_array_equal(g[both].view(np.uint64), t[both].view(np.uint64))
+    # a flagged result is still conservative: never later than the uncapped one
+    np.testing.assert_array_equal(gf, f)
+    assert r.toi_min == o[4]
+
+
+@pytest.mark.parametrize("s", SCENES[:5], ids=[s.info["name"] + str(i) for i, s in enumerate(SCENES[:5])])
+def test_narrow_per_pair_matches_oracle(ctx, ccd, s):
+    ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+    r, o = _narrow_both(ctx, ccd, s, ovf, oee)
+    _assert_per_pair(r, o)
+
+
+def _stress(n, seed):
+    X0, X1, is_vf, kind = scenes.narrow_stress_queries(n, seed)
+    sc, vf, ee, order = scenes.pack_queries(X0, X1, is_vf)
+    return sc, vf, ee
+
+
+@pytest.mark.parametrize("n,seed", [(5000, 2), (777, 5)])
+def test_narrow_stress_mix_matches_oracle(ctx, ccd, n, seed):
+    sc, vf, ee = _stress(n, seed)
+    r, o = _narrow_both(ctx, ccd, sc, vf, ee)
+    _assert_per_pair(r, o)
+
+
+def test_narrow_min_sep_matches_oracle(ctx, ccd):
+    sc, vf, ee = _stress(600, 8)
+    r, o = _narrow_both(ctx, ccd, sc, vf, ee, ms=1e-4, max_iter=20000)
+    g = np.concatenate([r.toi_vf.cpu().numpy(), r.toi_ee.cpu().numpy()])
+    gf = np.concatenate([r.flags_vf.cpu().numpy(), r.flags_ee.cpu().numpy()])
+    t = np.concatenate([o[0], o[1]])
+    f = np.concatenate([o[2], o[3]])
+    both = (gf == 0) & (f == 0)
+    np.testing.assert_array_equal(g[both].view(np.uint64), t[both].view(np.uint64))
+
+
+def test_narrow_max_iter_zero(ctx, ccd):
+    sc, vf, ee = _stress(300, 3)
+    r, o = _narrow_both(ctx, ccd, sc, vf, ee, max_iter=0)
+    g = np.concatenate([r.toi_vf.cpu().numpy(), r.toi_ee.cpu().numpy()])
+    t = np.concatenate([o[0], o[1]])
+    np.testing.assert_array_equal(g.view(np.uint64), t.view(np.uint64))
+
+
+def test_narrow_earliest_mode(ctx, ccd):
+    for s in SCENES[:4]:
+        ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+        r, o = _narrow_both(ctx, ccd, s, ovf, oee, mode=1)
+        per = O.narrow(ovf, oee, s.V0, s.V1, s.E, s.F, mode=0)
+        assert r.toi_min == o[4] == per[4]
+
+
+@pytest.mark.parametrize("budget,qcap", [(1, 0), (4, 0), (2, 64)])
+def test_narrow_handoff_paths_keep_results(ccd, budget, qcap):
+    # export after every interval (everything goes through the ring), and a
+    # ring too small to take most hand-offs: results must not change
+    c = ccd.CCD(0, export_budget=budget, queue_capacity=qcap)
+    try:
+        s = scenes.folded_cloth(40, seed=1)
+        ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+        r, o = _narrow_both(c, ccd, s, ovf, oee)
+        _assert_per_pair(r, o)
+        rc, st = c.status()
+        assert rc == 0
+        if qcap == 0:
+            assert st["n_exported"] > 0
+        r1, o1 = _narrow_both(c, ccd, s, ovf, oee, mode=1)
+        assert r1.toi_min == o1[4]
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("s", [SCENES[0], SCENES[2], SCENES[3]], ids=["icosphere", "cloth40", "cloth97"])
+def test_step_matches_oracle(ctx, ccd, s):
+    V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+    t = ctx.step(V0, V1, E, F)
+    assert t == O.step(s.V0, s.V1, s.E, s.F)
+    # device-pointer output, asynchronous path
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    ccd.ccd_step(ctx.ctx, V0, V1, E, F, 1e-6, 0.0, 10 ** 6, out)
+    torch.cuda.synchronize()
+    assert float(out.item()) == t
+
+
+def test_step_grows_pair_buffers(ccd):
+    c = ccd.CCD(0, pair_capacity=64)
+    try:
+        s = scenes.folded_cloth(40, seed=1)
+        V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+        assert c.step(V0, V1, E, F) == O.step(s.V0, s.V1, s.E, s.F)
+    finally:
+        c.close()
+
+
+def test_fp64_peak_probe(ccd):
+    g = ccd.ccd_measure_fp64_peak(0)
+    assert 10.0 < g < 1e6
