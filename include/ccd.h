@@ -64,7 +64,9 @@ typedef struct {
     int64_t max_iter;        /* per-query cap on processed intervals; default 1e6 */
     int32_t broad_fp64;      /* 0 (default): single-precision outward-rounded boxes
                                 then an exact FP64 filter; 1: FP64 boxes throughout */
-    int32_t sweep_block;     /* threads per block of the sweep kernel (0 = auto) */
+    int32_t sweep_kernel;    /* 0 (default): tiled sweep (a block walks the sweep
+                                ranges of 128 boxes through shared memory);
+                                1: one warp per box */
     int64_t pair_capacity;   /* initial pair-buffer capacity used by ccd_step
                                 (0 = auto); grows on demand in synchronous calls */
     int64_t queue_capacity;  /* interval-queue slots, a power of two (0 = auto) */

@@ -29,7 +29,7 @@ CCD_FLAG_LEVEL_CAP = 2
 class ccd_opts(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("min_sep", ctypes.c_double),
                 ("max_iter", ctypes.c_int64), ("broad_fp64", ctypes.c_int32),
-                ("sweep_block", ctypes.c_int32), ("pair_capacity", ctypes.c_int64),
+                ("sweep_kernel", ctypes.c_int32), ("pair_capacity", ctypes.c_int64),
                 ("queue_capacity", ctypes.c_int64), ("export_budget", ctypes.c_int32),
                 ("profile_stages", ctypes.c_int32)]
 

@@ -94,11 +94,12 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   size_t o_lo32 = take(3 * cap * sizeof(float)), o_hi32 = take(3 * cap * sizeof(float));
   size_t o_lo64 = take(3 * cap * sizeof(long long)), o_hi64 = take(3 * cap * sizeof(long long));
   size_t o_vid = take(cap * sizeof(int4));
-  size_t o_k0 = take(cap * 4), o_k1 = take(cap * 4), o_v0 = take(cap * 4), o_v1 = take(cap * 4);
+  size_t o_k0 = take(cap * 8), o_k1 = take(cap * 8), o_v0 = take(cap * 4), o_v1 = take(cap * 4);
   size_t o_hist = take(256 * ntiles * 4);
   size_t o_salo = take(cap * 4), o_sahi = take(cap * 4);
   size_t o_soth = take(cap * sizeof(float4)), o_svid = take(cap * sizeof(int4));
   size_t o_part = take(6 * nbuild * sizeof(float));
+  size_t o_salo64 = take(cap * 8), o_sahi64 = take(cap * 8), o_soth64 = take(2 * cap * sizeof(longlong2));
   char *m = nullptr;
   CK(cudaMalloc(&m, bytes));
   c->broad_mem = m;
@@ -109,8 +110,8 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   B.lo64 = (long long *)(m + o_lo64);
   B.hi64 = (long long *)(m + o_hi64);
   B.vid = (int4 *)(m + o_vid);
-  B.keys[0] = (uint32_t *)(m + o_k0);
-  B.keys[1] = (uint32_t *)(m + o_k1);
+  B.keys[0] = m + o_k0;
+  B.keys[1] = m + o_k1;
   B.vals[0] = (uint32_t *)(m + o_v0);
   B.vals[1] = (uint32_t *)(m + o_v1);
   B.hist = (uint32_t *)(m + o_hist);
@@ -119,6 +120,9 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   B.s_oth = (float4 *)(m + o_soth);
   B.s_vid = (int4 *)(m + o_svid);
   B.partials = (float *)(m + o_part);
+  B.s_alo64 = (long long *)(m + o_salo64);
+  B.s_ahi64 = (long long *)(m + o_sahi64);
+  B.s_oth64 = (longlong2 *)(m + o_soth64);
   return CCD_OK;
 }
 
@@ -189,17 +193,16 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   mark(c, CCD_STAGE_BOXES, false, s);
   mark(c, CCD_STAGE_SORT, true, s);
   const int grid = (int)std::min<int64_t>(cdiv(nB, 256), (int64_t)c->sm_count * 8);
-  k_make_keys<<<grid, 256, 0, s>>>(nB, B.lo32, c->ctl, B.keys[0], B.vals[0]);
-  const int ntiles = (int)cdiv(nB, kSortTile);
-  int cur = 0;
-  for (int shift = 0; shift < 32; shift += 8) {
-    k_radix_hist<<<ntiles, kSortThreads, 0, s>>>(B.keys[cur], nB, shift, B.hist, ntiles);
-    k_radix_scan<<<1, 1024, 0, s>>>(B.hist, 256 * ntiles);
-    k_radix_scatter<<<ntiles, kSortThreads, 0, s>>>(B.keys[cur], B.vals[cur], B.keys[cur ^ 1], B.vals[cur ^ 1],
-                                                    nB, shift, B.hist, ntiles);
-    cur ^= 1;
+  const bool fp64 = c->opts.broad_fp64 != 0;
+  if (!fp64) {
+    k_make_keys<<<grid, 256, 0, s>>>(nB, B.lo32, c->ctl, (uint32_t *)B.keys[0], B.vals[0]);
+    const int cur = radix_sort(B.keys, B.vals, 4, nB, B.hist, s);
+    k_gather_sorted<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
+  } else {
+    k_make_keys64<<<grid, 256, 0, s>>>(nB, B.lo64, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
+    const int cur = radix_sort(B.keys, B.vals, 8, nB, B.hist, s);
+    k_gather_sorted64<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
   }
-  k_gather_sorted<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
   mark(c, CCD_STAGE_SORT, false, s);
   SweepArgs A;
   A.nB = nB;
@@ -209,6 +212,9 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.s_ahi = B.s_ahi;
   A.s_oth = B.s_oth;
   A.s_vid = B.s_vid;
+  A.s_alo64 = B.s_alo64;
+  A.s_ahi64 = B.s_ahi64;
+  A.s_oth64 = B.s_oth64;
   A.lo64 = B.lo64;
   A.hi64 = B.hi64;
   A.vf_out = vf_out;
@@ -216,12 +222,17 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.vf_cap = vf_cap;
   A.ee_cap = ee_cap;
   A.ctl = c->ctl;
-  const int sblock = c->opts.sweep_block > 0 ? c->opts.sweep_block : 256;
-  const int sgrid = (int)std::min<int64_t>(cdiv(nB * 32, sblock), (int64_t)c->sm_count * 32);
+  const int sgrid = (int)std::min<int64_t>(cdiv(nB * 32, 256), (int64_t)c->sm_count * 32);
   mark(c, CCD_STAGE_SWEEP, true, s);
-  k_sweep<<<sgrid, sblock, 0, s>>>(A);
+  if (fp64)
+    k_sweep64<<<sgrid, 256, 0, s>>>(A);
+  else if (c->opts.sweep_kernel == 1)
+    k_sweep<<<sgrid, 256, 0, s>>>(A);
+  else
+    k_sweep_tiled<<<(unsigned)cdiv(nB, 128), 128, 0, s>>>(A);
   mark(c, CCD_STAGE_SWEEP, false, s);
-  c->n_launches += 19;   // reset, build, axis, keys, 4 x (hist, scan, scatter), gather, sweep
+  // reset, build, axis, keys, passes x (hist, scan, scatter), gather, sweep
+  c->n_launches += 6 + 3 * (fp64 ? 8 : 4);
   CK(cudaGetLastError());
   return CCD_OK;
 }
@@ -285,7 +296,7 @@ void ccd_default_opts(ccd_opts *o) {
   o->min_sep = 0.0;
   o->max_iter = 1000000;
   o->broad_fp64 = 0;
-  o->sweep_block = 0;
+  o->sweep_kernel = 0;
   o->pair_capacity = 0;
   o->queue_capacity = 0;
   o->export_budget = 0;
@@ -298,7 +309,9 @@ int ccd_create(ccd_ctx **out, const ccd_opts *o, int device) {
   ccd_opts opts;
   ccd_default_opts(&opts);
   if (o) opts = *o;
-  if (!(opts.delta >= 0) || !(opts.min_sep >= 0) || opts.max_iter < 0 || opts.broad_fp64 != 0) return CCD_EINVAL;
+  if (!(opts.delta >= 0) || !(opts.min_sep >= 0) || opts.max_iter < 0) return CCD_EINVAL;
+  if (opts.broad_fp64 != 0 && opts.broad_fp64 != 1) return CCD_EINVAL;
+  if (opts.sweep_kernel != 0 && opts.sweep_kernel != 1) return CCD_EINVAL;
   if (opts.profile_stages != 0 && opts.profile_stages != 1) return CCD_EINVAL;
   if (opts.queue_capacity < 0 || (opts.queue_capacity & (opts.queue_capacity - 1))) return CCD_EINVAL;
   int ndev = 0;

@@ -123,10 +123,22 @@ __global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, ui
   }
 }
 
+// FP64 form: the ordered int64 extent with its sign bit flipped is an
+// unsigned key in numeric order.
+__global__ void k_make_keys64(int64_t nB, const long long *lo64, const DevCtl *ctl, unsigned long long *keys,
+                              uint32_t *vals) {
+  const int a = ctl->axis;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nB; i += (int64_t)gridDim.x * blockDim.x) {
+    keys[i] = (unsigned long long)lo64[a * nB + i] ^ 0x8000000000000000ull;
+    vals[i] = (uint32_t)i;
+  }
+}
+
 // ---- radix sort: histogram / scan / stable scatter, 8 bits per pass --------
 
+template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift, uint32_t *hist, int ntiles) {
+k_radix_hist(const K *__restrict__ keys, int64_t n, int shift, uint32_t *hist, int ntiles) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -134,43 +146,58 @@ k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift, uint32_t *
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     int64_t i = base + r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+    if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 0xFFu], 1u);
   }
   __syncthreads();
   hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];   // digit-major
 }
 
-// Exclusive scan of the digit-major histogram, one block of 1024 threads.
+// Exclusive scan of the digit-major histogram, one block of 1024 threads:
+// consecutive chunks of 1024 entries (coalesced), warp-shuffle scan within a
+// chunk, carry across chunks.
 __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int total) {
-  __shared__ uint32_t part[1024];
-  const int per = (total + 1023) / 1024;
-  const int beg = threadIdx.x * per;
-  const int end = min(beg + per, total);
-  uint32_t s = 0;
-  for (int i = beg; i < end; ++i) s += hist[i];
-  part[threadIdx.x] = s;
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) carry = 0;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+  for (int base = 0; base < total; base += 1024) {
+    const int i = base + tid;
+    const uint32_t v = i < total ? hist[i] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    part[threadIdx.x] += v;
+    if (warp == 0) {
+      uint32_t s = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+        if (lane >= o) s += y;
+      }
+      wsum[lane] = s;
+    }
     __syncthreads();
-  }
-  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-  for (int i = beg; i < end; ++i) {
-    uint32_t v = hist[i];
-    hist[i] = run;
-    run += v;
+    const uint32_t excl = carry + (warp ? wsum[warp - 1] : 0u) + x - v;
+    if (i < total) hist[i] = excl;
+    __syncthreads();
+    if (tid == 1023) carry = excl + v;
+    __syncthreads();
   }
 }
 
 // Stable scatter of one tile: rounds of 256 consecutive keys; within a round
 // each key's rank among equal digits comes from __match_any_sync (warp) plus
 // the counts of earlier warps and earlier rounds.
+template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n, int shift,
-                const uint32_t *__restrict__ offsets, int ntiles) {
+k_radix_scatter(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
+                uint32_t *__restrict__ vals_out, int64_t n, int shift, const uint32_t *__restrict__ offsets,
+                int ntiles) {
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t run[256];              // running position per digit
   __shared__ uint32_t wcnt[kWarps][256];     // per-warp digit counts of the round
@@ -182,9 +209,9 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     __syncthreads();
     int64_t i = base + r * kSortThreads + threadIdx.x;
     bool valid = i < n;
-    uint32_t key = valid ? keys_in[i] : 0;
+    K key = valid ? keys_in[i] : K(0);
     uint32_t val = valid ? vals_in[i] : 0;
-    uint32_t d = valid ? (key >> shift) & 0xFF : 256u + lane;   // invalid lanes never match
+    uint32_t d = valid ? (uint32_t)(key >> shift) & 0xFFu : 256u + lane;   // invalid lanes never match
     unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
     uint32_t rank = __popc(peers & ((1u << lane) - 1u));
     if (valid && rank == 0) wcnt[w][d] = __popc(peers);
@@ -214,6 +241,41 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
   }
 }
 
+template <typename K>
+int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, uint32_t *hist, cudaStream_t s) {
+  const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+  int cur = 0;
+  for (int shift = 0; shift < (int)(8 * sizeof(K)); shift += 8) {
+    k_radix_hist<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, ntiles);
+    k_radix_scan<<<1, 1024, 0, s>>>(hist, 256 * ntiles);
+    k_radix_scatter<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
+                                                       hist, ntiles);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s) {
+  if (key_bytes == 4) {
+    uint32_t *k[2] = {(uint32_t *)keys[0], (uint32_t *)keys[1]};
+    return radix_sort_t<uint32_t>(k, vals, n, hist, s);
+  }
+  unsigned long long *k[2] = {(unsigned long long *)keys[0], (unsigned long long *)keys[1]};
+  return radix_sort_t<unsigned long long>(k, vals, n, hist, s);
+}
+
+__global__ void k_gather_sorted64(int64_t nB, const uint32_t *__restrict__ perm, const DevCtl *ctl, BroadBufs B) {
+  const int a = ctl->axis, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nB; s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = perm[s];
+    B.s_alo64[s] = B.lo64[a * nB + b];
+    B.s_ahi64[s] = B.hi64[a * nB + b];
+    B.s_oth64[2 * s] = make_longlong2(B.lo64[a1 * nB + b], B.hi64[a1 * nB + b]);
+    B.s_oth64[2 * s + 1] = make_longlong2(B.lo64[a2 * nB + b], B.hi64[a2 * nB + b]);
+    B.s_vid[s] = B.vid[b];
+  }
+}
+
 __global__ void k_gather_sorted(int64_t nB, const uint32_t *__restrict__ perm, const DevCtl *ctl, BroadBufs B) {
   const int a = ctl->axis, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nB; s += (int64_t)gridDim.x * blockDim.x) {
@@ -229,6 +291,52 @@ __global__ void k_gather_sorted(int64_t nB, const uint32_t *__restrict__ perm, c
 
 __device__ __forceinline__ int box_kind(int b, int64_t nV, int64_t nE) {
   return b < nV ? 0 : (b < nV + nE ? 1 : 2);   // vertex, edge, face
+}
+
+// Vertex-face / edge-edge rule and shared-vertex filter for a pair of boxes
+// whose extents overlap; on success writes the canonical pair.
+__device__ __forceinline__ bool candidate(const int4 vi, int ki, const int4 vj, int64_t nV, int64_t nE, bool &is_vf,
+                                          int &p0, int &p1) {
+  const int bi = vi.w, bj = vj.w;
+  const int kj = box_kind(bj, nV, nE);
+  const bool vfp = (ki == 0 && kj == 2) || (ki == 2 && kj == 0);
+  const bool eep = ki == 1 && kj == 1;
+  if (!(vfp || eep)) return false;
+  // shared vertex (i padded with -1, j with -2: padding never matches)
+  const int j0v = vj.x, j1v = vj.y < 0 ? -2 : vj.y, j2v = vj.z < 0 ? -2 : vj.z;
+  const int iv[3] = {vi.x, vi.y, vi.z};
+  bool share = false;
+#pragma unroll
+  for (int u = 0; u < 3; ++u) share |= (iv[u] == j0v) | (iv[u] == j1v) | (iv[u] == j2v);
+  if (share) return false;
+  is_vf = vfp;
+  if (vfp) {
+    p0 = ki == 0 ? bi : bj;
+    p1 = (int)((ki == 2 ? bi : bj) - nV - nE);
+  } else {
+    const int e1 = (int)(bi - nV), e2 = (int)(bj - nV);
+    p0 = min(e1, e2);
+    p1 = max(e1, e2);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void emit(const SweepArgs &A, bool is_vf, bool is_ee, int p0, int p1) {
+  const unsigned mask = 0xFFFFFFFFu;
+  if (__any_sync(mask, is_vf)) {
+    unsigned long long at = warp_append(&A.ctl->n_vf, is_vf, mask);
+    if (is_vf && (int64_t)at < A.vf_cap) {
+      A.vf_out[2 * at] = p0;
+      A.vf_out[2 * at + 1] = p1;
+    }
+  }
+  if (__any_sync(mask, is_ee)) {
+    unsigned long long at = warp_append(&A.ctl->n_ee, is_ee, mask);
+    if (is_ee && (int64_t)at < A.ee_cap) {
+      A.ee_out[2 * at] = p0;
+      A.ee_out[2 * at + 1] = p1;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs A) {
@@ -259,60 +367,165 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs A) {
         const float4 oj = A.s_oth[j];
         if (oj.x <= oi.y && oi.x <= oj.y && oj.z <= oi.w && oi.z <= oj.w) {
           const int4 vj = A.s_vid[j];
-          const int bj = vj.w;
-          const int kj = box_kind(bj, A.nV, A.nE);
-          const bool vfp = (ki == 0 && kj == 2) || (ki == 2 && kj == 0);
-          const bool eep = ki == 1 && kj == 1;
-          if (vfp || eep) {
-            // shared-vertex filter (i padded with -1, j with -2: no false match)
-            int j0v = vj.x, j1v = vj.y < 0 ? -2 : vj.y, j2v = vj.z < 0 ? -2 : vj.z;
-            bool share = false;
-            const int iv[3] = {vi.x, vi.y, vi.z};
+          bool vf;
+          if (candidate(vi, ki, vj, A.nV, A.nE, vf, p0, p1)) {
+            sup = true;
+            // exact test on the FP64 extents (ordered integer keys)
+            const int bj = vj.w;
+            bool ov = true;
 #pragma unroll
-            for (int u = 0; u < 3; ++u)
-              share |= (iv[u] == j0v) | (iv[u] == j1v) | (iv[u] == j2v);
-            if (!share) {
+            for (int a = 0; a < 3; ++a) {
+              long long jlo = A.lo64[a * nB + bj], jhi = A.hi64[a * nB + bj];
+              ov &= (jlo <= ihi[a]) & (ilo[a] <= jhi);
+            }
+            is_vf = ov && vf;
+            is_ee = ov && !vf;
+          }
+        }
+      }
+      const unsigned bs = __ballot_sync(0xFFFFFFFFu, sup);
+      if (bs && lane == 0) atomicAdd(&A.ctl->n_superset, (unsigned long long)__popc(bs));
+      emit(A, is_vf, is_ee, p0, p1);
+      if (run != 0xFFFFFFFFu) break;   // sorted: later boxes start beyond max_a(i)
+    }
+  }
+}
+
+// Tiled sweep (single-precision form).  A block owns kTI consecutive sorted
+// boxes, one per thread, and walks the union of their sweep ranges in tiles
+// of kTJ boxes staged in shared memory; at every step all lanes test their
+// own box i against the same box j, so the shared-memory reads are
+// broadcasts and each staged box is tested against kTI boxes.  Tests that
+// pass the three single-precision axes go through the candidate rule and the
+// exact FP64 test (box j's data is read once per hit, the same address for
+// every hitting lane of a warp).
+constexpr int kTI = 128;
+constexpr int kTJ = 256;
+
+__global__ void __launch_bounds__(kTI) k_sweep_tiled(SweepArgs A) {
+  __shared__ float sh_alo[kTJ];
+  __shared__ float4 sh_oth[kTJ];
+  __shared__ int4 sh_vid[kTJ];
+  __shared__ int64_t sh_end;
+  const int64_t nB = A.nB;
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = (int64_t)blockIdx.x * kTI; i0 < nB; i0 += (int64_t)gridDim.x * kTI) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool valid = i < nB;
+    float ahi = -__int_as_float(0x7F800000);
+    float4 oi = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 vi = make_int4(-1, -1, -1, 0);
+    int64_t end_i = i0;
+    if (valid) {
+      ahi = A.s_ahi[i];
+      oi = A.s_oth[i];
+      vi = A.s_vid[i];
+      // first sorted index whose minimum exceeds ahi (binary search, i < end)
+      int64_t lo = i + 1, hi = nB;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (A.s_alo[mid] <= ahi) lo = mid + 1; else hi = mid;
+      }
+      end_i = lo;
+    }
+    if (threadIdx.x == 0) sh_end = i0;
+    __syncthreads();
+    atomicMax((unsigned long long *)&sh_end, (unsigned long long)end_i);
+    __syncthreads();
+    const int64_t jend = sh_end;
+    const int ki = box_kind(vi.w, A.nV, A.nE);
+    long long ilo[3] = {0, 0, 0}, ihi[3] = {0, 0, 0};
+    bool have_exact = false;
+    for (int64_t jt = i0 + 1; jt < jend; jt += kTJ) {
+      __syncthreads();
+      for (int k = threadIdx.x; k < kTJ; k += kTI) {
+        int64_t j = jt + k;
+        if (j < nB) {
+          sh_alo[k] = A.s_alo[j];
+          sh_oth[k] = A.s_oth[j];
+          sh_vid[k] = A.s_vid[j];
+        } else {
+          sh_alo[k] = __int_as_float(0x7F800000);
+        }
+      }
+      __syncthreads();
+      const int cnt = (int)min((int64_t)kTJ, jend - jt);
+      for (int k = 0; k < cnt; ++k) {
+        const int64_t j = jt + k;
+        const float alo = sh_alo[k];
+        const float4 oj = sh_oth[k];
+        const bool hit = valid & (j > i) & (alo <= ahi) & (oj.x <= oi.y) & (oi.x <= oj.y) & (oj.z <= oi.w) &
+                         (oi.z <= oj.w);
+        bool is_vf = false, is_ee = false, sup = false;
+        int p0 = 0, p1 = 0;
+        if (__any_sync(0xFFFFFFFFu, hit)) {
+          if (hit) {
+            bool vf;
+            const int4 vj = sh_vid[k];
+            if (candidate(vi, ki, vj, A.nV, A.nE, vf, p0, p1)) {
               sup = true;
+              if (!have_exact) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  ilo[a] = A.lo64[a * nB + vi.w];
+                  ihi[a] = A.hi64[a * nB + vi.w];
+                }
+                have_exact = true;
+              }
+              const int bj = vj.w;
               bool ov = true;
 #pragma unroll
               for (int a = 0; a < 3; ++a) {
                 long long jlo = A.lo64[a * nB + bj], jhi = A.hi64[a * nB + bj];
                 ov &= (jlo <= ihi[a]) & (ilo[a] <= jhi);
               }
-              if (ov) {
-                if (vfp) {
-                  is_vf = true;
-                  p0 = ki == 0 ? bi : bj;
-                  p1 = (int)((ki == 2 ? bi : bj) - A.nV - A.nE);
-                } else {
-                  is_ee = true;
-                  int e1 = (int)(bi - A.nV), e2 = (int)(bj - A.nV);
-                  p0 = min(e1, e2);
-                  p1 = max(e1, e2);
-                }
-              }
+              is_vf = ov && vf;
+              is_ee = ov && !vf;
             }
+          }
+          const unsigned bs = __ballot_sync(0xFFFFFFFFu, sup);
+          if (bs && lane == 0) atomicAdd(&A.ctl->n_superset, (unsigned long long)__popc(bs));
+          emit(A, is_vf, is_ee, p0, p1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Plain FP64 form: the sweep runs directly on the FP64 extents (ordered
+// int64 keys, exact comparisons); no single-precision stage, no filter.
+__global__ void __launch_bounds__(256) k_sweep64(SweepArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nB = A.nB;
+  for (int64_t i = warp; i < nB; i += nwarps) {
+    const long long ahi = A.s_ahi64[i];
+    const longlong2 o1 = A.s_oth64[2 * i], o2 = A.s_oth64[2 * i + 1];
+    const int4 vi = A.s_vid[i];
+    const int ki = box_kind(vi.w, A.nV, A.nE);
+    for (int64_t j0 = i + 1;; j0 += 32) {
+      const int64_t j = j0 + lane;
+      const bool in_a = j < nB && A.s_alo64[j] <= ahi;
+      const unsigned run = __ballot_sync(0xFFFFFFFFu, in_a);
+      bool is_vf = false, is_ee = false, sup = false;
+      int p0 = 0, p1 = 0;
+      if (in_a) {
+        const longlong2 q1 = A.s_oth64[2 * j], q2 = A.s_oth64[2 * j + 1];
+        if (q1.x <= o1.y && o1.x <= q1.y && q2.x <= o2.y && o2.x <= q2.y) {
+          bool vf;
+          if (candidate(vi, ki, A.s_vid[j], A.nV, A.nE, vf, p0, p1)) {
+            sup = true;
+            is_vf = vf;
+            is_ee = !vf;
           }
         }
       }
-      const unsigned mask = 0xFFFFFFFFu;
-      const unsigned bs = __ballot_sync(mask, sup);
+      const unsigned bs = __ballot_sync(0xFFFFFFFFu, sup);
       if (bs && lane == 0) atomicAdd(&A.ctl->n_superset, (unsigned long long)__popc(bs));
-      if (__any_sync(mask, is_vf)) {
-        unsigned long long at = warp_append(&A.ctl->n_vf, is_vf, mask);
-        if (is_vf && (int64_t)at < A.vf_cap) {
-          A.vf_out[2 * at] = p0;
-          A.vf_out[2 * at + 1] = p1;
-        }
-      }
-      if (__any_sync(mask, is_ee)) {
-        unsigned long long at = warp_append(&A.ctl->n_ee, is_ee, mask);
-        if (is_ee && (int64_t)at < A.ee_cap) {
-          A.ee_out[2 * at] = p0;
-          A.ee_out[2 * at + 1] = p1;
-        }
-      }
-      if (run != 0xFFFFFFFFu) break;   // sorted: later boxes start beyond max_a(i)
+      emit(A, is_vf, is_ee, p0, p1);
+      if (run != 0xFFFFFFFFu) break;
     }
   }
 }

@@ -71,30 +71,39 @@ struct BroadBufs {
   float *lo32, *hi32;            // [3][nB]
   long long *lo64, *hi64;        // [3][nB] ordered FP64 keys
   int4 *vid;                     // [nB] (v0, v1, v2, box id), -1 padded
-  // sort
-  uint32_t *keys[2], *vals[2];   // [nB]
+  // sort (keys are 4 or 8 bytes: single-precision or FP64 form)
+  void *keys[2];                 // [nB]
+  uint32_t *vals[2];             // [nB]
   uint32_t *hist;                // [256 * nTiles]
   // sorted by the minimum on the sweep axis
   float *s_alo, *s_ahi;          // [nB]
   float4 *s_oth;                 // [nB] (lo1, hi1, lo2, hi2)
   int4 *s_vid;                   // [nB]
   float *partials;               // [6 * nBuildBlocks]
+  // FP64 form: sorted ordered-int64 extents
+  long long *s_alo64, *s_ahi64;  // [nB]
+  longlong2 *s_oth64;            // [2 * nB]: (lo1, hi1), (lo2, hi2)
 };
 
 __global__ void k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *V0, const double *V1,
                               const int32_t *E, const int32_t *F, BroadBufs B);
 __global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl);
 __global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, uint32_t *keys, uint32_t *vals);
-__global__ void k_radix_hist(const uint32_t *keys, int64_t n, int shift, uint32_t *hist, int ntiles);
-__global__ void k_radix_scan(uint32_t *hist, int total);
-__global__ void k_radix_scatter(const uint32_t *keys_in, const uint32_t *vals_in, uint32_t *keys_out,
-                                uint32_t *vals_out, int64_t n, int shift, const uint32_t *offsets, int ntiles);
+__global__ void k_make_keys64(int64_t nB, const long long *lo64, const DevCtl *ctl, unsigned long long *keys,
+                              uint32_t *vals);
+// Stable LSD radix sort of (key, value) pairs, 8 bits per pass, on stream s;
+// keys[0]/vals[0] hold the input; returns the index (0 or 1) of the buffers
+// holding the sorted output.  key_bytes = 4 or 8.  Launches 3 kernels per pass.
+int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s);
 __global__ void k_gather_sorted(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
+__global__ void k_gather_sorted64(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 
 struct SweepArgs {
   int64_t nB, nV, nE;
   const float *s_alo, *s_ahi;
   const float4 *s_oth;
+  const long long *s_alo64, *s_ahi64;
+  const longlong2 *s_oth64;
   const int4 *s_vid;
   const long long *lo64, *hi64;  // [3][nB] by box id
   int32_t *vf_out, *ee_out;
@@ -102,5 +111,7 @@ struct SweepArgs {
   DevCtl *ctl;
 };
 __global__ void k_sweep(SweepArgs A);
+__global__ void k_sweep_tiled(SweepArgs A);
+__global__ void k_sweep64(SweepArgs A);
 
 }  // namespace ccd

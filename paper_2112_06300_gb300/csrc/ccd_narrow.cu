@@ -210,40 +210,49 @@ __device__ __forceinline__ void inclusion(const QueryData &Q, bool vf, double tl
 }
 
 // ---- bounded MPMC ring of exported intervals -------------------------------
-// Cell: sequence number + interval.  Sequence protocol: a cell at position p
-// is free for a writer when seq == p, holds data when seq == p + 1, and is
-// released for the next lap (seq = p + cap) after it has been read.
+// Cell: sequence number + interval.  A cell at position p holds data when
+// seq == p + 1 and is free for position p + cap once its reader stores
+// seq = p + cap.  Writers first reserve all the positions they need with one
+// CAS on `tail`, and only while every reserved position is below
+// head + cap: each such position's previous occupant has already been popped,
+// so a writer never waits on a reader that has not started.  A hand-off that
+// does not fit is not made (the lane keeps the work), so pushes cannot block.
 
 __device__ __forceinline__ unsigned long long pack1(uint64_t n, int l) {
   return n | ((unsigned long long)l << 54);
 }
 
-__device__ bool ring_push(RingCell *ring, unsigned long long mask, unsigned long long *tail, uint32_t q,
-                          const Node &N, int *status) {
-  unsigned long long pos = ld_relaxed_u64(tail);
-  for (int spin = 0; spin < (1 << 20); ++spin) {
-    RingCell *c = &ring[pos & mask];
-    unsigned long long seq = ld_acquire_u64(&c->seq);
-    long long dif = (long long)(seq - pos);
-    if (dif == 0) {
-      if (atomicCAS(tail, pos, pos + 1) == pos) {
-        c->w[0] = pack1(N.n0, N.l0);
-        c->w[1] = pack1(N.n1, N.l1);
-        c->w[2] = pack1(N.n2, N.l2);
-        c->q = q;
-        st_release_u64(&c->seq, pos + 1);
-        return true;
-      }
-      pos = ld_relaxed_u64(tail);
-    } else if (dif < 0) {
-      __nanosleep(64);  // full: readers are draining it
-      pos = ld_relaxed_u64(tail);
-    } else {
-      pos = ld_relaxed_u64(tail);
-    }
+// Reserve m consecutive positions if the ring then stays below `limit`
+// occupied slots; returns the first position or ~0ull.
+__device__ unsigned long long ring_reserve(unsigned long long *tail, const unsigned long long *head,
+                                           unsigned long long m, unsigned long long limit) {
+  for (int tries = 0; tries < 32; ++tries) {
+    unsigned long long t = ld_relaxed_u64(tail);
+    unsigned long long h = ld_relaxed_u64(head);
+    if (t - h + m > limit) return ~0ull;
+    if (atomicCAS(tail, t, t + m) == t) return t;
   }
-  atomicExch(status, CCD_ETIMEOUT);
-  return false;
+  return ~0ull;
+}
+
+// Write one interval at a reserved position.  The wait is for a reader that
+// has already popped the previous occupant and is copying it out.
+__device__ bool ring_write(RingCell *ring, unsigned long long mask, unsigned long long pos, uint32_t q,
+                           const Node &N, int *status) {
+  RingCell *c = &ring[pos & mask];
+  for (int spin = 0; ld_acquire_u64(&c->seq) != pos; ++spin) {
+    if (spin > (1 << 22)) {
+      atomicExch(status, CCD_ETIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  c->w[0] = pack1(N.n0, N.l0);
+  c->w[1] = pack1(N.n1, N.l1);
+  c->w[2] = pack1(N.n2, N.l2);
+  c->q = q;
+  st_release_u64(&c->seq, pos + 1);
+  return true;
 }
 
 __device__ bool ring_pop(RingCell *ring, unsigned long long mask, unsigned long long *head, uint32_t &q,
@@ -269,7 +278,7 @@ __device__ bool ring_pop(RingCell *ring, unsigned long long mask, unsigned long 
       }
       pos = ld_relaxed_u64(head);
     } else if (dif < 0) {
-      return false;  // empty
+      return false;  // empty, or the next item is still being written
     } else {
       pos = ld_relaxed_u64(head);
     }
@@ -302,8 +311,12 @@ __device__ __forceinline__ void query_ids(int64_t q, int64_t n_vf, const int32_t
 
 }  // namespace
 
-constexpr int kIdleSpinLimit = 1 << 16;   // ~0.05 s of 512 ns naps, then a lane retires
+constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a warp retires
 
+// Control flow is warp-uniform at the loop level: refill, idling and exit are
+// decided for the whole warp (ballots and broadcasts), and the per-lane work
+// sits in structured branches, so the lanes of a warp reconverge every
+// iteration and the FP64 instructions of an interval issue once per warp.
 __global__ void __launch_bounds__(kNarrowThreads, 3)
 k_narrow(NarrowArgs A) {
   DevCtl *ctl = A.ctl;
@@ -311,14 +324,17 @@ k_narrow(NarrowArgs A) {
     A.n_vf = ctl->pair_counts[0];
     A.n_ee = ctl->pair_counts[1];
   }
+  const unsigned FULL = 0xFFFFFFFFu;
   const int64_t nq = A.n_vf + A.n_ee;
   const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned long long delta_bits = dbits(A.delta);
   const unsigned long long ring_cap = A.ring_mask + 1;
 
   QueryData Q;
   bool vf = false;
-  bool have = false, fresh = false, whole = false, exhausted = false;
+  bool have = false, fresh = false, whole = false;
+  bool exhausted = false;                    // warp-uniform
   int64_t q = 0;
   Node N{0, 0, 0, 0, 0, 0};
   int depth = 0, root_depth = 0;
@@ -326,47 +342,61 @@ k_narrow(NarrowArgs A) {
   long long cnt = 0, cap_left = 0;
   unsigned flags = 0;
   long long n_eval = 0, n_exp = 0, n_cap = 0;
-  int idle_spins = 0;
+  int idle_rounds = 0;
 
   while (true) {
-    // ---- 1. acquire work: exported intervals first, then new queries ------
-    if (!have && ld_relaxed_u64(&ctl->q_head) != ld_relaxed_u64(&ctl->q_tail)) {
-      uint32_t qq;
-      if (ring_pop(A.ring, A.ring_mask, &ctl->q_head, qq, N)) {
-        q = qq;
-        have = fresh = true;
-        whole = false;
+    // ---- 1. refill lanes without work: exported intervals, then queries ---
+    if (__any_sync(FULL, !have)) {
+      unsigned long long hd = 0, tl_ = 0;
+      if (lane == 0) {
+        hd = ld_relaxed_u64(&ctl->q_head);
+        tl_ = ld_relaxed_u64(&ctl->q_tail);
+      }
+      hd = __shfl_sync(FULL, hd, 0);
+      tl_ = __shfl_sync(FULL, tl_, 0);
+      if (!have && hd != tl_) {
+        uint32_t qq;
+        if (ring_pop(A.ring, A.ring_mask, &ctl->q_head, qq, N)) {
+          q = qq;
+          have = fresh = true;
+          whole = false;
+        }
+      }
+      const unsigned m = __ballot_sync(FULL, !have);
+      if (m && !exhausted) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->q_next, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL, base, 0);
+        if (base + __popc(m) >= (unsigned long long)nq) exhausted = true;
+        if (!have) {
+          const unsigned long long mine = base + __popc(m & lt_mask);
+          if ((int64_t)mine < nq) {
+            q = (int64_t)mine;
+            have = fresh = whole = true;
+            N = Node{0, 0, 0, 0, 0, 0};
+          }
+        }
+        const int got = base < (unsigned long long)nq
+                            ? (int)min((unsigned long long)__popc(m), (unsigned long long)nq - base)
+                            : 0;
+        if (lane == 0 && got) atomicAdd(&ctl->pending, (unsigned long long)got);
       }
     }
-    if (!have && !exhausted) {
-      unsigned m = __activemask();
-      int leader = __ffs(m) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(&ctl->q_next, (unsigned long long)__popc(m));
-      base = __shfl_sync(m, base, leader);
-      unsigned long long mine = base + __popc(m & ((1u << lane) - 1u));
-      bool got = (int64_t)mine < nq;
-      if (got) {
-        q = (int64_t)mine;
-        have = fresh = whole = true;
-        N = Node{0, 0, 0, 0, 0, 0};
-      } else {
-        exhausted = true;
+
+    // ---- 2. a warp with no work idles or retires (uniform) ----------------
+    if (__ballot_sync(FULL, have) == 0) {
+      int stop = 0;
+      if (lane == 0) {
+        bool empty = ld_relaxed_u64(&ctl->q_head) == ld_relaxed_u64(&ctl->q_tail);
+        stop = (exhausted && empty && ld_relaxed_u64(&ctl->pending) == 0) || ++idle_rounds > kIdleRounds;
       }
-      unsigned gm = __ballot_sync(m, got);
-      if (lane == leader && gm) atomicAdd(&ctl->pending, (unsigned long long)__popc(gm));
-      __syncwarp(m);
-    }
-    if (!have) {
-      if (ld_relaxed_u64(&ctl->q_head) == ld_relaxed_u64(&ctl->q_tail)) {
-        if (ld_relaxed_u64(&ctl->pending) == 0 || ++idle_spins > kIdleSpinLimit) break;
-        __nanosleep(512);
-      }
+      if (__shfl_sync(FULL, stop, 0)) break;
+      __nanosleep(1000);
       continue;
     }
-    idle_spins = 0;
+    idle_rounds = 0;
 
-    // ---- 2. set up a new unit ---------------------------------------------
+    // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
       int ids[4];
       query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
@@ -391,37 +421,45 @@ k_narrow(NarrowArgs A) {
       fresh = false;
     }
 
-    // ---- 3. ProcessInterval on the current node ---------------------------
+    // ---- 4. ProcessInterval on the current node ---------------------------
     unsigned long long cut = tq;
     if (A.mode == 1) {
-      unsigned long long g = ld_relaxed_u64(&ctl->toi_bits);
+      unsigned long long g = 0;
+      if (lane == 0) g = ld_relaxed_u64(&ctl->toi_bits);
+      g = __shfl_sync(FULL, g, 0);
       cut = g < cut ? g : cut;
     }
-    const double tl = dyadic(N.n0, N.l0);
     bool node_done = true;     // false when the node was split (go to its left child)
     bool unit_end = false;
-    if (dbits(tl) >= cut) {
-      // pruned: starts at or after the current t*
-    } else if (vf && dbits(dyadic(N.n1, N.l1)) > dbits(dyadic((1ull << N.l2) - N.n2, N.l2))) {
-      // vertex-face: u_lo > 1 - v_lo, the interval lies outside the simplex
-    } else if (++cnt > cap_left) {
-      // iteration cap: t* = min(t*, earliest left end among the live intervals)
-      unsigned long long m = dbits(tl);
-      Node W = N;
-      for (int d = depth; d > root_depth; --d) {
-        int a = last_axis(Q.K, W);
-        if ((W.n(a) & 1) == 0) {
-          unsigned long long sb = dbits(a == 0 ? dyadic(W.n0 + 1, W.l0) : dyadic(W.n0, W.l0));
-          m = sb < m ? sb : m;
+    bool evaluate = false;
+    const double tl = dyadic(N.n0, N.l0);
+    if (have) {
+      if (dbits(tl) >= cut) {
+        // pruned: starts at or after the current t*
+      } else if (vf && dbits(dyadic(N.n1, N.l1)) > dbits(dyadic((1ull << N.l2) - N.n2, N.l2))) {
+        // vertex-face: u_lo > 1 - v_lo, the interval lies outside the simplex
+      } else if (++cnt > cap_left) {
+        // iteration cap: t* = min(t*, earliest left end among the live intervals)
+        unsigned long long m = dbits(tl);
+        Node W = N;
+        for (int d = depth; d > root_depth; --d) {
+          int a = last_axis(Q.K, W);
+          if ((W.n(a) & 1) == 0) {
+            unsigned long long sb = dbits(a == 0 ? dyadic(W.n0 + 1, W.l0) : dyadic(W.n0, W.l0));
+            m = sb < m ? sb : m;
+          }
+          W.up(a);
         }
-        W.up(a);
+        tq = m < tq ? m : tq;
+        flags |= CCD_FLAG_ITER_CAP;
+        ++n_cap;
+        --cnt;
+        unit_end = true;
+      } else {
+        evaluate = true;
       }
-      tq = m < tq ? m : tq;
-      flags |= CCD_FLAG_ITER_CAP;
-      ++n_cap;
-      --cnt;
-      unit_end = true;
-    } else {
+    }
+    if (evaluate) {
       ++n_eval;
       const double tr = dyadic(N.n0 + 1, N.l0);
       const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
@@ -457,8 +495,8 @@ k_narrow(NarrowArgs A) {
       }
     }
 
-    // ---- 4. next node: backtrack to the deepest pending right sibling ------
-    if (node_done && !unit_end) {
+    // ---- 5. next node: backtrack to the deepest pending right sibling ------
+    if (have && node_done && !unit_end) {
       while (true) {
         if (depth == root_depth) {
           unit_end = true;
@@ -474,21 +512,21 @@ k_narrow(NarrowArgs A) {
       }
     }
 
-    // ---- 5. hand out the live intervals after `budget` evaluations --------
-    if (!unit_end && cnt >= A.budget) {
-      unsigned long long head = ld_relaxed_u64(&ctl->q_head);
-      unsigned long long tail = ld_relaxed_u64(&ctl->q_tail);
-      if (tail - head < (ring_cap >> 2)) {
-        int nexp = 1;
-        {
-          Node W = N;
-          for (int d = depth; d > root_depth; --d) {
-            int a = last_axis(Q.K, W);
-            nexp += (W.n(a) & 1) == 0;
-            W.up(a);
-          }
+    // ---- 6. hand out the live intervals after `budget` evaluations --------
+    if (have && !unit_end && cnt >= A.budget) {
+      int nexp = 1;
+      {
+        Node W = N;
+        for (int d = depth; d > root_depth; --d) {
+          int a = last_axis(Q.K, W);
+          nexp += (W.n(a) & 1) == 0;
+          W.up(a);
         }
-        // publish what the takers read before they can pop the items
+      }
+      const unsigned long long pos =
+          ring_reserve(&ctl->q_tail, &ctl->q_head, (unsigned long long)nexp, ring_cap >> 2);
+      if (pos != ~0ull) {
+        // publish what the takers read before any item becomes visible
         if (tq != kInfBits) {
           if (A.mode == 0)
             atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
@@ -497,18 +535,20 @@ k_narrow(NarrowArgs A) {
         }
         atomicAdd(&A.qiters[q], (unsigned long long)cnt);
         atomicAdd(&ctl->pending, (unsigned long long)nexp);
-        bool ok = ring_push(A.ring, A.ring_mask, &ctl->q_tail, (uint32_t)q, N, &ctl->status);
+        ring_write(A.ring, A.ring_mask, pos, (uint32_t)q, N, &ctl->status);
+        int k = 1;
         Node W = N;
-        for (int d = depth; d > root_depth && ok; --d) {
+        for (int d = depth; d > root_depth; --d) {
           int a = last_axis(Q.K, W);
           if ((W.n(a) & 1) == 0) {
             Node S = W;
             S.add(a, 1);
-            ok = ring_push(A.ring, A.ring_mask, &ctl->q_tail, (uint32_t)q, S, &ctl->status);
+            ring_write(A.ring, A.ring_mask, pos + k, (uint32_t)q, S, &ctl->status);
+            ++k;
           }
           W.up(a);
         }
-        unsigned long long occ = ld_relaxed_u64(&ctl->q_tail) - ld_relaxed_u64(&ctl->q_head);
+        const unsigned long long occ = pos + nexp - ld_relaxed_u64(&ctl->q_head);
         if (occ > ld_relaxed_u64(&ctl->queue_peak)) atomicMax(&ctl->queue_peak, occ);
         n_exp += nexp;
         unit_end = true;
@@ -516,8 +556,8 @@ k_narrow(NarrowArgs A) {
       }
     }
 
-    // ---- 6. finish the unit ------------------------------------------------
-    if (unit_end) {
+    // ---- 7. finish the unit ------------------------------------------------
+    if (have && unit_end) {
       if (tq != kInfBits) {
         if (A.mode == 0)
           atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
@@ -525,9 +565,11 @@ k_narrow(NarrowArgs A) {
       }
       if (flags) atomicOr(&A.qflags[q], flags);
       if (!whole && cnt) atomicAdd(&A.qiters[q], (unsigned long long)cnt);
-      atomicAdd(&ctl->pending, ~0ull);   // -1
       have = false;
     }
+    // one pending decrement per warp for all units that ended
+    const unsigned ended = __ballot_sync(FULL, unit_end);
+    if (lane == 0 && ended) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)__popc(ended)));
   }
 
   if (n_eval) atomicAdd(&ctl->n_intervals, (unsigned long long)n_eval);

@@ -211,3 +211,33 @@ def test_step_grows_pair_buffers(ccd):
 def test_fp64_peak_probe(ccd):
     g = ccd.ccd_measure_fp64_peak(0)
     assert 10.0 < g < 1e6
+
+
+@pytest.mark.parametrize("s", [SCENES[0], SCENES[3], SCENES[4]], ids=["icosphere", "cloth97", "random"])
+def test_plain_fp64_form_matches_oracle(ccd, s):
+    # all-FP64 broad phase: 64-bit keys, exact comparisons, no filter stage
+    c = ccd.CCD(0, broad_fp64=1)
+    try:
+        V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+        vf, ee = c.broad(V0, V1, E, F)
+        ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+        np.testing.assert_array_equal(sorted_pairs(vf), ovf)
+        np.testing.assert_array_equal(sorted_pairs(ee), oee)
+        rc, st = c.status()
+        assert rc == 0 and st["n_superset"] == len(ovf) + len(oee)
+        assert c.step(V0, V1, E, F) == O.step(s.V0, s.V1, s.E, s.F)
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("s", [SCENES[0], SCENES[3], SCENES[5]], ids=["icosphere", "cloth97", "tiny"])
+def test_warp_per_box_sweep_matches_oracle(ccd, s):
+    c = ccd.CCD(0, sweep_kernel=1)
+    try:
+        V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+        vf, ee = c.broad(V0, V1, E, F)
+        ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+        np.testing.assert_array_equal(sorted_pairs(vf), ovf)
+        np.testing.assert_array_equal(sorted_pairs(ee), oee)
+    finally:
+        c.close()
