@@ -90,6 +90,8 @@ typedef struct {
     int32_t device_status;   /* CCD_* status raised by the kernels */
     int32_t pad1;
     int64_t n_launches;      /* kernels this context launched since creation */
+    int64_t narrow_bulk_ns;  /* narrow kernel: start until every query was taken */
+    int64_t narrow_tail_ns;  /* narrow kernel: from then until the last lane ended */
 } ccd_stats;
 
 /* Fill *o with the defaults. */

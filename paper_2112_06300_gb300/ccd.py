@@ -40,7 +40,8 @@ class ccd_stats(ctypes.Structure):
                 ("n_intervals", ctypes.c_int64), ("n_exported", ctypes.c_int64),
                 ("n_capped", ctypes.c_int64), ("queue_peak", ctypes.c_int64),
                 ("device_status", ctypes.c_int32), ("pad1", ctypes.c_int32),
-                ("n_launches", ctypes.c_int64)]
+                ("n_launches", ctypes.c_int64), ("narrow_bulk_ns", ctypes.c_int64),
+                ("narrow_tail_ns", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}

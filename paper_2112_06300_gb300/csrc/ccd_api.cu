@@ -70,6 +70,7 @@ __global__ void k_reset_narrow(DevCtl *c) {
   c->pending = 0;
   c->toi_bits = 0x7FF0000000000000ull;
   c->n_intervals = c->n_exported = c->n_capped = c->queue_peak = 0;
+  c->t_start = c->t_exhausted = c->t_end = 0;
 }
 __global__ void k_reset_status(DevCtl *c) { c->status = CCD_OK; }
 
@@ -483,6 +484,11 @@ int ccd_get_status(ccd_ctx *c, ccd_stats *st) {
     st->queue_peak = (int64_t)h.queue_peak;
     st->device_status = h.status;
     st->n_launches = c->n_launches;
+    if (h.t_end > h.t_start && h.t_start) {
+      const unsigned long long tx = h.t_exhausted ? h.t_exhausted : h.t_end;
+      st->narrow_bulk_ns = (int64_t)(tx - h.t_start);
+      st->narrow_tail_ns = (int64_t)(h.t_end - tx);
+    }
   }
   return h.status;
 }

@@ -23,6 +23,7 @@ struct DevCtl {
   unsigned long long toi_bits;   // earliest t* so far, bits of a non-negative double
   unsigned long long n_intervals, n_exported, n_capped, queue_peak;
   long long pair_counts[2];      // ccd_step: pairs for the narrow phase (clamped)
+  unsigned long long t_start, t_exhausted, t_end;  // %globaltimer stamps of the narrow kernel
 };
 
 struct RingCell {

@@ -255,35 +255,10 @@ __device__ bool ring_write(RingCell *ring, unsigned long long mask, unsigned lon
   return true;
 }
 
-__device__ bool ring_pop(RingCell *ring, unsigned long long mask, unsigned long long *head, uint32_t &q,
-                         Node &N) {
-  unsigned long long pos = ld_relaxed_u64(head);
-  for (int spin = 0; spin < 64; ++spin) {
-    RingCell *c = &ring[pos & mask];
-    unsigned long long seq = ld_acquire_u64(&c->seq);
-    long long dif = (long long)(seq - (pos + 1));
-    if (dif == 0) {
-      if (atomicCAS(head, pos, pos + 1) == pos) {
-        const unsigned long long w0 = c->w[0], w1 = c->w[1], w2 = c->w[2];
-        const unsigned long long m54 = (1ull << 54) - 1;
-        q = c->q;
-        N.n0 = w0 & m54;
-        N.n1 = w1 & m54;
-        N.n2 = w2 & m54;
-        N.l0 = (int)(w0 >> 54);
-        N.l1 = (int)(w1 >> 54);
-        N.l2 = (int)(w2 >> 54);
-        st_release_u64(&c->seq, pos + mask + 1);
-        return true;
-      }
-      pos = ld_relaxed_u64(head);
-    } else if (dif < 0) {
-      return false;  // empty, or the next item is still being written
-    } else {
-      pos = ld_relaxed_u64(head);
-    }
-  }
-  return false;
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ void query_ids(int64_t q, int64_t n_vf, const int32_t *__restrict__ vfp,
@@ -343,9 +318,12 @@ k_narrow(NarrowArgs A) {
   unsigned flags = 0;
   long long n_eval = 0, n_exp = 0, n_cap = 0;
   int idle_rounds = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->t_start, 0ull, globaltimer());
 
   while (true) {
     // ---- 1. refill lanes without work: exported intervals, then queries ---
+    // One lane claims, with a single CAS, as many ready ring cells as the
+    // warp has idle lanes; each idle lane then copies out its own cell.
     if (__any_sync(FULL, !have)) {
       unsigned long long hd = 0, tl_ = 0;
       if (lane == 0) {
@@ -354,10 +332,40 @@ k_narrow(NarrowArgs A) {
       }
       hd = __shfl_sync(FULL, hd, 0);
       tl_ = __shfl_sync(FULL, tl_, 0);
-      if (!have && hd != tl_) {
-        uint32_t qq;
-        if (ring_pop(A.ring, A.ring_mask, &ctl->q_head, qq, N)) {
-          q = qq;
+      if (hd != tl_) {
+        const unsigned m = __ballot_sync(FULL, !have);
+        unsigned long long pos0 = 0;
+        int r = 0;
+        if (lane == 0) {
+          const int want = __popc(m);
+          for (int tries = 0; tries < 8 && r == 0; ++tries) {
+            const unsigned long long h = ld_relaxed_u64(&ctl->q_head);
+            int k = 0;
+            while (k < want && ld_acquire_u64(&A.ring[(h + k) & A.ring_mask].seq) == h + k + 1) ++k;
+            if (k == 0) break;
+            if (atomicCAS(&ctl->q_head, h, h + k) == h) {
+              pos0 = h;
+              r = k;
+            }
+          }
+        }
+        pos0 = __shfl_sync(FULL, pos0, 0);
+        r = __shfl_sync(FULL, r, 0);
+        const int rank = __popc(m & lt_mask);
+        if (!have && rank < r) {
+          const unsigned long long pos = pos0 + rank;
+          RingCell *c = &A.ring[pos & A.ring_mask];
+          (void)ld_acquire_u64(&c->seq);   // pairs with the writer's release
+          const unsigned long long w0 = c->w[0], w1 = c->w[1], w2 = c->w[2];
+          const unsigned long long m54 = (1ull << 54) - 1;
+          q = c->q;
+          N.n0 = w0 & m54;
+          N.n1 = w1 & m54;
+          N.n2 = w2 & m54;
+          N.l0 = (int)(w0 >> 54);
+          N.l1 = (int)(w1 >> 54);
+          N.l2 = (int)(w2 >> 54);
+          st_release_u64(&c->seq, pos + A.ring_mask + 1);   // free for the next lap
           have = fresh = true;
           whole = false;
         }
@@ -367,7 +375,11 @@ k_narrow(NarrowArgs A) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&ctl->q_next, (unsigned long long)__popc(m));
         base = __shfl_sync(FULL, base, 0);
-        if (base + __popc(m) >= (unsigned long long)nq) exhausted = true;
+        if (base + __popc(m) >= (unsigned long long)nq) {
+          exhausted = true;
+          if (lane == 0 && ld_relaxed_u64(&ctl->t_exhausted) == 0)
+            atomicCAS(&ctl->t_exhausted, 0ull, globaltimer());
+        }
         if (!have) {
           const unsigned long long mine = base + __popc(m & lt_mask);
           if ((int64_t)mine < nq) {
@@ -423,12 +435,15 @@ k_narrow(NarrowArgs A) {
 
     // ---- 4. ProcessInterval on the current node ---------------------------
     unsigned long long cut = tq;
-    if (A.mode == 1) {
-      unsigned long long g = 0;
-      if (lane == 0) g = ld_relaxed_u64(&ctl->toi_bits);
-      g = __shfl_sync(FULL, g, 0);
-      cut = g < cut ? g : cut;
+    unsigned long long g = 0, qn = 0;
+    if (lane == 0) {
+      g = ld_relaxed_u64(&ctl->toi_bits);
+      qn = ld_relaxed_u64(&ctl->q_next);
     }
+    g = __shfl_sync(FULL, g, 0);
+    // hand work out only once every query has been taken (idle lanes exist)
+    const bool tail_phase = __shfl_sync(FULL, qn, 0) >= (unsigned long long)nq;
+    if (A.mode == 1) cut = g < cut ? g : cut;
     bool node_done = true;     // false when the node was split (go to its left child)
     bool unit_end = false;
     bool evaluate = false;
@@ -513,7 +528,7 @@ k_narrow(NarrowArgs A) {
     }
 
     // ---- 6. hand out the live intervals after `budget` evaluations --------
-    if (have && !unit_end && cnt >= A.budget) {
+    if (have && !unit_end && cnt >= A.budget && tail_phase) {
       int nexp = 1;
       {
         Node W = N;
@@ -548,7 +563,8 @@ k_narrow(NarrowArgs A) {
           }
           W.up(a);
         }
-        const unsigned long long occ = pos + nexp - ld_relaxed_u64(&ctl->q_head);
+        const unsigned long long h = ld_relaxed_u64(&ctl->q_head), t = pos + nexp;
+        const unsigned long long occ = t > h ? t - h : 0;
         if (occ > ld_relaxed_u64(&ctl->queue_peak)) atomicMax(&ctl->queue_peak, occ);
         n_exp += nexp;
         unit_end = true;
@@ -575,6 +591,7 @@ k_narrow(NarrowArgs A) {
   if (n_eval) atomicAdd(&ctl->n_intervals, (unsigned long long)n_eval);
   if (n_exp) atomicAdd(&ctl->n_exported, (unsigned long long)n_exp);
   if (n_cap) atomicAdd(&ctl->n_capped, (unsigned long long)n_cap);
+  if (lane == 0) atomicMax(&ctl->t_end, globaltimer());
 }
 
 __global__ void k_ring_init(RingCell *ring, unsigned long long cap, unsigned long long base) {
