@@ -156,6 +156,28 @@ int ccd_step(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV,
              const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
              double delta, double min_sep, int64_t max_iter, double *toi_min, void *stream);
 
+/*
+ * Narrow phase without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc where they
+ * need the query (under an allocator they do not own, in hosts that forbid
+ * allocation, in loops that must not allocate).  Same computation and
+ * arguments as ccd_narrow, but no context: the scratch is one fixed array in
+ * the library's device memory (about 1.4 MB per GPU, kept until the process
+ * exits).  Limit: n_vf + n_ee <= 65536; larger calls return CCD_EINVAL.
+ * status: device int32 [1], receives the kernels' CCD_* status.
+ * The first call on a device sets the array up (looks up its device address,
+ * initialises the interval ring) on `stream` from the current device; make
+ * that first call before any stream capture.  Every call shares the array and
+ * it keeps the last call's contents (each call clears what must start at
+ * zero); calls that overlap on the GPU race.  Asynchronous.
+ */
+int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee,
+                       const double *V0, const double *V1, int64_t nV,
+                       const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
+                       double delta, double min_sep, int64_t max_iter, int32_t mode,
+                       double *toi_vf, double *toi_ee, uint8_t *flags_vf, uint8_t *flags_ee,
+                       double *toi_min, int32_t *status, void *stream);
+
 /* Synchronize the context's last stream and read its device status and
  * counters (stats may be NULL).  Returns the device status. */
 int ccd_get_status(ccd_ctx *ctx, ccd_stats *stats);

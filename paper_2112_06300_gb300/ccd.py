@@ -79,6 +79,9 @@ def lib():
     L.ccd_status_str.restype = ctypes.c_char_p
     L.ccd_measure_fp64_peak.argtypes = [ctypes.c_int, ctypes.POINTER(d)]
     L.ccd_stage_times.argtypes = [P, ctypes.POINTER(d)]
+    L.ccd_narrow_noalloc.argtypes = [P, i64, P, i64, P, P, i64, P, i64, P, i64, d, d, i64, i32,
+                                     P, P, P, P, P, P, P]
+    L.ccd_narrow_noalloc.restype = ctypes.c_int
     for f in ("ccd_create", "ccd_destroy", "ccd_broad", "ccd_narrow", "ccd_step", "ccd_get_status",
               "ccd_measure_fp64_peak", "ccd_stage_times"):
         getattr(L, f).restype = ctypes.c_int
@@ -150,6 +153,19 @@ def ccd_narrow(ctx, vf, ee, V0, V1, E, F, delta, min_sep, max_iter, mode,
                           _ptr(toi_vf), _ptr(toi_ee), _ptr(flags_vf), _ptr(flags_ee), _ptr(toi_min),
                           _stream(stream))
     _check(rc, "ccd_narrow")
+
+
+def ccd_narrow_noalloc(vf, ee, V0, V1, E, F, delta, min_sep, max_iter, mode,
+                       toi_vf, toi_ee, flags_vf, flags_ee, toi_min, status, stream=None) -> None:
+    """Narrow phase with no device allocation (fixed scratch inside the
+    library, at most 65536 pairs per call); `status` is a CUDA int32 tensor of
+    one element that receives the device status."""
+    nV, nE, nF = _mesh(V0, V1, E, F)
+    rc = lib().ccd_narrow_noalloc(_ptr(vf), vf.shape[0], _ptr(ee), ee.shape[0], _ptr(V0), _ptr(V1), nV,
+                                  _ptr(E), nE, _ptr(F), nF, float(delta), float(min_sep), int(max_iter),
+                                  int(mode), _ptr(toi_vf), _ptr(toi_ee), _ptr(flags_vf), _ptr(flags_ee),
+                                  _ptr(toi_min), _ptr(status), _stream(stream))
+    _check(rc, "ccd_narrow_noalloc")
 
 
 def ccd_step(ctx, V0, V1, E, F, delta, min_sep, max_iter, toi_min, stream=None) -> int:
