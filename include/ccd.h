@@ -74,6 +74,13 @@ typedef struct {
                                 remaining intervals to the queue (0 = auto) */
     int32_t profile_stages;  /* 1: record CUDA events around the stages of each
                                 call (read with ccd_stage_times); default 0 */
+    int32_t no_zero_toi;     /* 1: ccd_step applies the zero-TOI rule of the appendix
+                                "Zero time of impact and minimum separation": when
+                                the earliest time is 0, the narrow phase runs again
+                                with min_sep = 0, intervals starting at t = 0 are
+                                always split, and the result is scaled by 0.8
+                                (decided on the device); default 0 */
+    int32_t pad_opts;
 } ccd_opts;
 
 /* Work counters of the last broad/narrow/step call (see ccd_get_status). */
@@ -84,7 +91,7 @@ typedef struct {
     int64_t n_superset;      /* pairs passing the single-precision box test */
     int64_t n_vf, n_ee;      /* candidate pairs after the exact test */
     int64_t n_intervals;     /* narrow-phase intervals evaluated */
-    int64_t n_exported;      /* intervals handed to the queue */
+    int64_t n_exported;      /* subtrees handed to the queue (other warps) */
     int64_t n_capped;        /* queries that hit max_iter */
     int64_t queue_peak;      /* largest queue occupancy seen */
     int32_t device_status;   /* CCD_* status raised by the kernels */
@@ -92,6 +99,8 @@ typedef struct {
     int64_t n_launches;      /* kernels this context launched since creation */
     int64_t narrow_bulk_ns;  /* narrow kernel: start until every query was taken */
     int64_t narrow_tail_ns;  /* narrow kernel: from then until the last lane ended */
+    int64_t n_donated;       /* subtrees passed between lanes of one warp */
+    int64_t n_intervals_tail;  /* intervals evaluated after every query was taken */
 } ccd_stats;
 
 /* Fill *o with the defaults. */

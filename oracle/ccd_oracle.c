@@ -455,9 +455,13 @@ static int split_axis(const query *q, const interval *I)
  *   - collision if w(B) < delta (widest axis) or B inside C_eps: t* = I_t^l
  *   - otherwise split along split_axis(); if no axis can be split, accept as
  *     a collision and set FLAG_LEVEL_CAP.
+ * no_zero (appendix "Zero time of impact and minimum separation"): an
+ * interval with I_t^l = 0 is always split -- neither the stop rule, nor
+ * containment in C_eps, nor the iteration cap applies to it; it is accepted
+ * only when no axis can be split.
  */
 static double process_query(const query *q, double delta, int64_t max_iter, double tstar_in,
-                            const volatile uint64_t *global_bits,
+                            const volatile uint64_t *global_bits, int no_zero,
                             uint8_t *flags, int64_t *iters)
 {
     interval stack[STACK_MAX];
@@ -481,7 +485,8 @@ static double process_query(const query *q, double delta, int64_t max_iter, doub
          * 53 bits, so it and the comparison are exact in FP64 (the sum may
          * round at the deepest levels). */
         if (q->vf && dyadic(I.n[1], I.l[1]) > 1.0 - dyadic(I.n[2], I.l[2])) continue;
-        if (++count > max_iter) {
+        int at_zero = no_zero && I.n[0] == 0;
+        if (!at_zero && ++count > max_iter) {
             double m = tl;
             for (int s = 0; s < sp; ++s) {
                 double ts = dyadic(stack[s].n[0], stack[s].l[0]);
@@ -502,7 +507,7 @@ static double process_query(const query *q, double delta, int64_t max_iter, doub
             if (wx > w) w = wx;
         }
         if (miss) continue;
-        if (w < delta || inside) { tstar = tl; continue; }
+        if (!at_zero && (w < delta || inside)) { tstar = tl; continue; }
         int k = split_axis(q, &I);
         if (k < 0) { tstar = tl; *flags |= FLAG_LEVEL_CAP; continue; }
         interval left = I, right = I;
@@ -526,12 +531,12 @@ static uint64_t bits_of(double d) { uint64_t b; memcpy(&b, &d, sizeof b); return
  *   mode 1: earliest only: one t* shared by all queries (Algorithm 3 as
  *           printed); toi/flags/iters are still written but toi[i] is only an
  *           upper bound for pruned queries.
- * Returns the earliest t* over all queries in *toi_min.  nthreads <= 0 uses
- * the OpenMP default.
+ * no_zero: the zero-TOI rule of process_query.  Returns the earliest t* over
+ * all queries in *toi_min.  nthreads <= 0 uses the OpenMP default.
  */
 void oracle_narrow(int64_t nq, const uint8_t *qtype, const int64_t *qids,
                    const double *V0, const double *V1,
-                   double delta, double min_sep, int64_t max_iter, int mode, int nthreads,
+                   double delta, double min_sep, int64_t max_iter, int mode, int no_zero, int nthreads,
                    double *toi, uint8_t *flags, int64_t *iters, double *toi_min)
 {
     volatile uint64_t gbits = bits_of(INFINITY);
@@ -545,7 +550,7 @@ void oracle_narrow(int64_t nq, const uint8_t *qtype, const int64_t *qids,
         query q;
         setup_query(&q, qtype[i], V0, V1, &qids[4 * i], min_sep);
         double start = INFINITY;
-        double t = process_query(&q, delta, max_iter, start, mode == 1 ? &gbits : NULL,
+        double t = process_query(&q, delta, max_iter, start, mode == 1 ? &gbits : NULL, no_zero,
                                  &flags[i], &iters[i]);
         toi[i] = t;
         if (t < INFINITY) { /* min into the shared value */

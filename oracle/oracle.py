@@ -55,7 +55,7 @@ def _configure(L):
                        P, i64, P, P, i64, P]
         fn.restype = ctypes.c_int
     L.oracle_narrow.argtypes = [i64, P, P, P, P, ctypes.c_double,
-                                ctypes.c_double, i64, ctypes.c_int,
+                                ctypes.c_double, i64, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, P, P, P, P]
     L.oracle_narrow.restype = None
     L.oracle_inclusion.argtypes = [ctypes.c_int, P, P, P, ctypes.c_double, P, P, P, P, P]
@@ -160,7 +160,7 @@ def query_ids(vf, ee, E, F):
 
 
 def narrow_queries(qtype, ids, V0, V1, delta=1e-6, min_sep=0.0, max_iter=10**6,
-                   mode=0, nthreads=0):
+                   mode=0, nthreads=0, no_zero=False):
     """Conservative interval bisection (Algorithm 3) on explicit queries.
     Returns (toi, flags, iters, toi_min); toi = +inf where no collision."""
     V0 = np.ascontiguousarray(V0, dtype=np.float64).reshape(-1, 3)
@@ -171,27 +171,37 @@ def narrow_queries(qtype, ids, V0, V1, delta=1e-6, min_sep=0.0, max_iter=10**6,
     toi = np.empty(n); flags = np.zeros(n, np.uint8); iters = np.zeros(n, np.int64)
     tmin = np.empty(1)
     lib().oracle_narrow(n, _p(qtype), _p(ids), _p(V0), _p(V1), float(delta),
-                        float(min_sep), int(max_iter), int(mode), int(nthreads),
+                        float(min_sep), int(max_iter), int(mode), int(bool(no_zero)), int(nthreads),
                         _p(toi), _p(flags), _p(iters), _p(tmin))
     return toi, flags, iters, float(tmin[0])
 
 
 def narrow(vf, ee, V0, V1, E, F, delta=1e-6, min_sep=0.0, max_iter=10**6, mode=0,
-           nthreads=0):
+           nthreads=0, no_zero=False):
     """Narrow phase over pair lists; per-pair results are split back into the
     vertex-face and edge-edge parts: (toi_vf, toi_ee, flags_vf, flags_ee,
     toi_min)."""
     qtype, ids = query_ids(vf, ee, E, F)
     toi, flags, _, tmin = narrow_queries(qtype, ids, V0, V1, delta, min_sep,
-                                         max_iter, mode, nthreads)
+                                         max_iter, mode, nthreads, no_zero)
     nvf = len(np.asarray(vf).reshape(-1, 2))
     return toi[:nvf], toi[nvf:], flags[:nvf], flags[nvf:], tmin
 
 
-def step(V0, V1, E, F, delta=1e-6, min_sep=0.0, max_iter=10**6, nthreads=0):
-    """Whole CCD (Algorithm 1): boxes, broad phase, earliest-TOI narrow phase."""
+NO_ZERO_SCALE = 0.8
+
+
+def step(V0, V1, E, F, delta=1e-6, min_sep=0.0, max_iter=10**6, nthreads=0, no_zero_toi=False):
+    """Whole CCD (Algorithm 1): boxes, broad phase, earliest-TOI narrow phase.
+    no_zero_toi (appendix "Zero time of impact and minimum separation"): when
+    the earliest time is 0, run the narrow phase again with min_sep = 0 and
+    the zero-TOI rule, and return that time scaled by 0.8."""
     vf, ee = broad(V0, V1, E, F, "sweep")
-    return narrow(vf, ee, V0, V1, E, F, delta, min_sep, max_iter, 1, nthreads)[4]
+    t = narrow(vf, ee, V0, V1, E, F, delta, min_sep, max_iter, 1, nthreads)[4]
+    if no_zero_toi and t == 0.0:
+        t2 = narrow(vf, ee, V0, V1, E, F, delta, 0.0, max_iter, 1, nthreads, no_zero=True)[4]
+        t = NO_ZERO_SCALE * t2
+    return t
 
 
 def inclusion(vf, x0, x1, n, l, min_sep=0.0):

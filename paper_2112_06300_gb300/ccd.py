@@ -31,7 +31,8 @@ class ccd_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int64), ("broad_fp64", ctypes.c_int32),
                 ("sweep_kernel", ctypes.c_int32), ("pair_capacity", ctypes.c_int64),
                 ("queue_capacity", ctypes.c_int64), ("export_budget", ctypes.c_int32),
-                ("profile_stages", ctypes.c_int32)]
+                ("profile_stages", ctypes.c_int32), ("no_zero_toi", ctypes.c_int32),
+                ("pad_opts", ctypes.c_int32)]
 
 
 class ccd_stats(ctypes.Structure):
@@ -41,7 +42,8 @@ class ccd_stats(ctypes.Structure):
                 ("n_capped", ctypes.c_int64), ("queue_peak", ctypes.c_int64),
                 ("device_status", ctypes.c_int32), ("pad1", ctypes.c_int32),
                 ("n_launches", ctypes.c_int64), ("narrow_bulk_ns", ctypes.c_int64),
-                ("narrow_tail_ns", ctypes.c_int64)]
+                ("narrow_tail_ns", ctypes.c_int64), ("n_donated", ctypes.c_int64),
+                ("n_intervals_tail", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}

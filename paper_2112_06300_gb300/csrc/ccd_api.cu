@@ -28,6 +28,7 @@ struct ccd_ctx {
   int64_t cap_q = 0;
   uint32_t *qflags = nullptr;
   unsigned long long *qiters = nullptr;
+  unsigned long long *qrec = nullptr;          // query records, 24 x cap_q words
   RingCell *ring = nullptr;
   unsigned long long ring_cap = 0;
   cudaStream_t last_stream = nullptr;
@@ -71,6 +72,8 @@ __global__ void k_reset_narrow(DevCtl *c) {
   c->toi_bits = 0x7FF0000000000000ull;
   c->n_intervals = c->n_exported = c->n_capped = c->queue_peak = 0;
   c->t_start = c->t_exhausted = c->t_end = 0;
+  c->n_donated = 0;
+  c->n_intervals_tail = 0;
 }
 __global__ void k_reset_status(DevCtl *c) { c->status = CCD_OK; }
 
@@ -96,7 +99,7 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   size_t o_lo64 = take(3 * cap * sizeof(long long)), o_hi64 = take(3 * cap * sizeof(long long));
   size_t o_vid = take(cap * sizeof(int4));
   size_t o_k0 = take(cap * 8), o_k1 = take(cap * 8), o_v0 = take(cap * 4), o_v1 = take(cap * 4);
-  size_t o_hist = take(256 * ntiles * 4);
+  size_t o_hist = take((256 * ntiles + 256) * 4);
   size_t o_salo = take(cap * 4), o_sahi = take(cap * 4);
   size_t o_soth = take(cap * sizeof(float4)), o_svid = take(cap * sizeof(int4));
   size_t o_part = take(6 * nbuild * sizeof(float));
@@ -141,12 +144,15 @@ int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
   if (nq <= c->cap_q) return CCD_OK;
   if (c->qflags) CK(cudaFree(c->qflags));
   if (c->qiters) CK(cudaFree(c->qiters));
+  if (c->qrec) CK(cudaFree(c->qrec));
   c->qflags = nullptr;
   c->qiters = nullptr;
+  c->qrec = nullptr;
   c->cap_q = 0;
   int64_t cap = std::max<int64_t>(nq, 1024);
   CK(cudaMalloc(&c->qflags, cap * sizeof(uint32_t)));
   CK(cudaMalloc(&c->qiters, cap * sizeof(unsigned long long)));
+  CK(cudaMalloc(&c->qrec, cap * 24 * sizeof(unsigned long long)));
   c->cap_q = cap;
   return CCD_OK;
 }
@@ -230,7 +236,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   else if (c->opts.sweep_kernel == 1)
     k_sweep<<<sgrid, 256, 0, s>>>(A);
   else
-    k_sweep_tiled<<<(unsigned)cdiv(nB, 128), 128, 0, s>>>(A);
+    k_sweep_tiled<<<(unsigned)cdiv(nB, 256), 128, 0, s>>>(A);
   mark(c, CCD_STAGE_SWEEP, false, s);
   // reset, build, axis, keys, passes x (hist, scan, scatter), gather, sweep
   c->n_launches += 6 + 3 * (fp64 ? 8 : 4);
@@ -241,11 +247,15 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
 int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee,
                   int counts_from_ctl, const double *V0, const double *V1, int64_t nV, const int32_t *E,
                   const int32_t *F, double delta, double min_sep, int64_t max_iter, int mode,
-                  unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s) {
+                  unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s,
+                  bool zero_rule_pass = false) {
   const int64_t nq = n_vf + n_ee;
   int rc = ensure_narrow(c, nq, s);
   if (rc) return rc;
-  k_reset_narrow<<<1, 1, 0, s>>>(c->ctl);
+  if (zero_rule_pass)
+    k_nozero_prepare<<<1, 1, 0, s>>>(c->ctl);
+  else
+    k_reset_narrow<<<1, 1, 0, s>>>(c->ctl);
   NarrowArgs A;
   A.ctl = c->ctl;
   A.vf = vf;
@@ -263,16 +273,24 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   A.max_iter = max_iter;
   A.mode = mode;
   A.budget = c->opts.export_budget > 0 ? c->opts.export_budget : 64;
+  A.no_zero = zero_rule_pass ? 1 : 0;
+  A.only_if_rerun = zero_rule_pass ? 1 : 0;
   A.toi_vf_bits = toi_vf_bits;
   A.toi_ee_bits = toi_ee_bits;
   A.qflags = c->qflags;
   A.qiters = c->qiters;
   A.ring = c->ring;
   A.ring_mask = c->ring_cap - 1;
-  mark(c, CCD_STAGE_NARROW, true, s);
+  A.qrec = c->qrec;
+  A.rec_stride = c->cap_q;
+  if (!zero_rule_pass) mark(c, CCD_STAGE_NARROW, true, s);
+  // query records: one dense pass (the zero-TOI pass has min_sep = 0: redo it)
+  k_prepare_queries<<<(unsigned)std::min<int64_t>(cdiv(std::max<int64_t>(nq, 1), 256), (int64_t)c->sm_count * 16),
+                      256, 0, s>>>(A);
   k_narrow<<<c->narrow_blocks, kNarrowThreads, 0, s>>>(A);
+  if (zero_rule_pass) k_nozero_finish<<<1, 1, 0, s>>>(c->ctl);
   mark(c, CCD_STAGE_NARROW, false, s);
-  c->n_launches += 2;    // reset, narrow
+  c->n_launches += zero_rule_pass ? 4 : 3;    // reset/prepare, records, narrow, finish
   CK(cudaGetLastError());
   return CCD_OK;
 }
@@ -302,6 +320,7 @@ void ccd_default_opts(ccd_opts *o) {
   o->queue_capacity = 0;
   o->export_budget = 0;
   o->profile_stages = 0;
+  o->no_zero_toi = 0;
 }
 
 int ccd_create(ccd_ctx **out, const ccd_opts *o, int device) {
@@ -313,6 +332,7 @@ int ccd_create(ccd_ctx **out, const ccd_opts *o, int device) {
   if (!(opts.delta >= 0) || !(opts.min_sep >= 0) || opts.max_iter < 0) return CCD_EINVAL;
   if (opts.broad_fp64 != 0 && opts.broad_fp64 != 1) return CCD_EINVAL;
   if (opts.sweep_kernel != 0 && opts.sweep_kernel != 1) return CCD_EINVAL;
+  if (opts.no_zero_toi != 0 && opts.no_zero_toi != 1) return CCD_EINVAL;
   if (opts.profile_stages != 0 && opts.profile_stages != 1) return CCD_EINVAL;
   if (opts.queue_capacity < 0 || (opts.queue_capacity & (opts.queue_capacity - 1))) return CCD_EINVAL;
   int ndev = 0;
@@ -357,6 +377,7 @@ int ccd_destroy(ccd_ctx *c) {
   cudaFree(c->ee);
   cudaFree(c->qflags);
   cudaFree(c->qiters);
+  cudaFree(c->qrec);
   cudaFree(c->ring);
   cudaFree(c->ctl);
   for (int k = 0; k < 2 * CCD_NSTAGES; ++k)
@@ -444,6 +465,12 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     rc = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep,
                        max_iter, 1, nullptr, nullptr, s);
     if (rc) return rc;
+    if (c->opts.no_zero_toi) {
+      // second pass only when the first found t* = 0 (decided on the device)
+      rc = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, 0.0, max_iter,
+                         1, nullptr, nullptr, s, true);
+      if (rc) return rc;
+    }
     if (!host_out) {
       CK(cudaMemcpyAsync(toi_min, &c->ctl->toi_bits, sizeof(double), cudaMemcpyDeviceToDevice, s));
       return CCD_OK;
@@ -480,6 +507,8 @@ int ccd_get_status(ccd_ctx *c, ccd_stats *st) {
     st->n_ee = (int64_t)h.n_ee;
     st->n_intervals = (int64_t)h.n_intervals;
     st->n_exported = (int64_t)h.n_exported;
+    st->n_donated = (int64_t)h.n_donated;
+    st->n_intervals_tail = (int64_t)h.n_intervals_tail;
     st->n_capped = (int64_t)h.n_capped;
     st->queue_peak = (int64_t)h.queue_peak;
     st->device_status = h.status;

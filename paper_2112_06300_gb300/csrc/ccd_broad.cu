@@ -152,18 +152,19 @@ k_radix_hist(const K *__restrict__ keys, int64_t n, int shift, uint32_t *hist, i
   hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];   // digit-major
 }
 
-// Exclusive scan of the digit-major histogram, one block of 1024 threads:
-// consecutive chunks of 1024 entries (coalesced), warp-shuffle scan within a
-// chunk, carry across chunks.
-__global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int total) {
-  __shared__ uint32_t wsum[32];
+// Row scan of the digit-major histogram: block d turns row d (the counts of
+// digit d in every tile) into its exclusive prefix and stores the row total;
+// the scatter adds the exclusive prefix of the totals (the digit's base).
+__global__ void __launch_bounds__(256) k_radix_scan_rows(uint32_t *hist, int ntiles, uint32_t *totals) {
+  __shared__ uint32_t wsum[8];
   __shared__ uint32_t carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t *row = hist + (int64_t)blockIdx.x * ntiles;
   if (tid == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < total; base += 1024) {
+  for (int base = 0; base < ntiles; base += 256) {
     const int i = base + tid;
-    const uint32_t v = i < total ? hist[i] : 0u;
+    const uint32_t v = i < ntiles ? row[i] : 0u;
     uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -172,22 +173,15 @@ __global__ void __launch_bounds__(1024) k_radix_scan(uint32_t *hist, int total) 
     }
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-      uint32_t s = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
-        if (lane >= o) s += y;
-      }
-      wsum[lane] = s;
-    }
+    uint32_t before = carry;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    const uint32_t excl = before + x - v;
+    if (i < ntiles) row[i] = excl;
     __syncthreads();
-    const uint32_t excl = carry + (warp ? wsum[warp - 1] : 0u) + x - v;
-    if (i < total) hist[i] = excl;
-    __syncthreads();
-    if (tid == 1023) carry = excl + v;
+    if (tid == 255) carry = excl + v;
     __syncthreads();
   }
+  if (tid == 0) totals[blockIdx.x] = carry;
 }
 
 // Stable scatter of one tile: rounds of 256 consecutive keys; within a round
@@ -197,12 +191,27 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_scatter(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
                 uint32_t *__restrict__ vals_out, int64_t n, int shift, const uint32_t *__restrict__ offsets,
-                int ntiles) {
+                int ntiles, const uint32_t *__restrict__ totals) {
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t run[256];              // running position per digit
   __shared__ uint32_t wcnt[kWarps][256];     // per-warp digit counts of the round
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  run[threadIdx.x] = offsets[threadIdx.x * ntiles + blockIdx.x];
+  {
+    // digit base: exclusive scan of the 256 digit totals
+    const uint32_t tot = totals[threadIdx.x];
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wcnt[0][w] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int j = 0; j < w; ++j) before += wcnt[0][j];
+    run[threadIdx.x] = before + x - tot + offsets[threadIdx.x * ntiles + blockIdx.x];
+    __syncthreads();
+  }
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   for (int r = 0; r < kSortItems; ++r) {
     for (int j = 0; j < kWarps; ++j) wcnt[j][threadIdx.x] = 0;
@@ -244,12 +253,13 @@ k_radix_scatter(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
 template <typename K>
 int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, uint32_t *hist, cudaStream_t s) {
   const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
+  uint32_t *totals = hist + 256 * (int64_t)ntiles;
   int cur = 0;
   for (int shift = 0; shift < (int)(8 * sizeof(K)); shift += 8) {
     k_radix_hist<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, ntiles);
-    k_radix_scan<<<1, 1024, 0, s>>>(hist, 256 * ntiles);
+    k_radix_scan_rows<<<256, 256, 0, s>>>(hist, ntiles, totals);
     k_radix_scatter<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
-                                                       hist, ntiles);
+                                                       hist, ntiles, totals);
     cur ^= 1;
   }
   return cur;
@@ -391,55 +401,86 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs A) {
   }
 }
 
-// Tiled sweep (single-precision form).  A block owns kTI consecutive sorted
-// boxes, one per thread, and walks the union of their sweep ranges in tiles
-// of kTJ boxes staged in shared memory; at every step all lanes test their
-// own box i against the same box j, so the shared-memory reads are
-// broadcasts and each staged box is tested against kTI boxes.  Tests that
-// pass the three single-precision axes go through the candidate rule and the
-// exact FP64 test (box j's data is read once per hit, the same address for
-// every hitting lane of a warp).
-constexpr int kTI = 128;
+// Tiled sweep (single-precision form).  A block of 128 threads owns 256
+// consecutive sorted boxes, two per thread, and walks the union of their
+// sweep ranges in tiles of kTJ boxes staged in shared memory.  At every step
+// all lanes test their two boxes against the same box j, so the shared-memory
+// reads are broadcasts serving two tests each; the order test j > i is needed
+// only while the tile overlaps the block's own boxes; one warp vote covers
+// 4 j x 2 boxes.  Tests beyond a box's range fail by themselves (sorted
+// minima exceed its maximum).  Survivors of the three single-precision axes
+// go through the candidate rule and the exact FP64 test.
+constexpr int kSweepThreads = 128;
+constexpr int kTI = 2 * kSweepThreads;
 constexpr int kTJ = 256;
 
-__global__ void __launch_bounds__(kTI) k_sweep_tiled(SweepArgs A) {
+__device__ __forceinline__ void sweep_hit(const SweepArgs &A, bool hit, const int4 vi, int ki, const int4 vj,
+                                          int64_t nB) {
+  bool is_vf = false, is_ee = false, sup = false;
+  int p0 = 0, p1 = 0;
+  if (hit) {
+    bool vf;
+    if (candidate(vi, ki, vj, A.nV, A.nE, vf, p0, p1)) {
+      sup = true;
+      bool ov = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const long long ilo = A.lo64[a * nB + vi.w], ihi = A.hi64[a * nB + vi.w];
+        const long long jlo = A.lo64[a * nB + vj.w], jhi = A.hi64[a * nB + vj.w];
+        ov &= (jlo <= ihi) & (ilo <= jhi);
+      }
+      is_vf = ov && vf;
+      is_ee = ov && !vf;
+    }
+  }
+  const unsigned bs = __ballot_sync(0xFFFFFFFFu, sup);
+  if (bs && (threadIdx.x & 31) == 0) atomicAdd(&A.ctl->n_superset, (unsigned long long)__popc(bs));
+  emit(A, is_vf, is_ee, p0, p1);
+}
+
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_tiled(SweepArgs A) {
   __shared__ float sh_alo[kTJ];
   __shared__ float4 sh_oth[kTJ];
   __shared__ int4 sh_vid[kTJ];
-  __shared__ int64_t sh_end;
+  __shared__ unsigned long long sh_end;
   const int64_t nB = A.nB;
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x;
   for (int64_t i0 = (int64_t)blockIdx.x * kTI; i0 < nB; i0 += (int64_t)gridDim.x * kTI) {
-    const int64_t i = i0 + threadIdx.x;
-    const bool valid = i < nB;
-    float ahi = -__int_as_float(0x7F800000);
-    float4 oi = make_float4(0.f, 0.f, 0.f, 0.f);
-    int4 vi = make_int4(-1, -1, -1, 0);
-    int64_t end_i = i0;
-    if (valid) {
-      ahi = A.s_ahi[i];
-      oi = A.s_oth[i];
-      vi = A.s_vid[i];
-      // first sorted index whose minimum exceeds ahi (binary search, i < end)
-      int64_t lo = i + 1, hi = nB;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (A.s_alo[mid] <= ahi) lo = mid + 1; else hi = mid;
+    float ahi[2];
+    float4 oi[2];
+    int4 vi[2];
+    int ki[2];
+    int64_t end_max = i0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t i = i0 + r * kSweepThreads + tid;
+      ahi[r] = -__int_as_float(0x7F800000);   // no box: every test fails
+      oi[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      vi[r] = make_int4(-1, -1, -1, 0);
+      if (i < nB) {
+        ahi[r] = A.s_ahi[i];
+        oi[r] = A.s_oth[i];
+        vi[r] = A.s_vid[i];
+        // first sorted index whose minimum exceeds ahi (binary search)
+        int64_t lo = i + 1, hi = nB;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (A.s_alo[mid] <= ahi[r]) lo = mid + 1; else hi = mid;
+        }
+        end_max = lo > end_max ? lo : end_max;
       }
-      end_i = lo;
+      ki[r] = box_kind(vi[r].w, A.nV, A.nE);
     }
-    if (threadIdx.x == 0) sh_end = i0;
+    if (tid == 0) sh_end = (unsigned long long)i0;
     __syncthreads();
-    atomicMax((unsigned long long *)&sh_end, (unsigned long long)end_i);
+    atomicMax(&sh_end, (unsigned long long)end_max);
     __syncthreads();
-    const int64_t jend = sh_end;
-    const int ki = box_kind(vi.w, A.nV, A.nE);
-    long long ilo[3] = {0, 0, 0}, ihi[3] = {0, 0, 0};
-    bool have_exact = false;
+    const int64_t jend = (int64_t)sh_end;
+    const int li0 = tid, li1 = kSweepThreads + tid;   // local indices of the two boxes
     for (int64_t jt = i0 + 1; jt < jend; jt += kTJ) {
       __syncthreads();
-      for (int k = threadIdx.x; k < kTJ; k += kTI) {
-        int64_t j = jt + k;
+      for (int k = tid; k < kTJ; k += kSweepThreads) {
+        const int64_t j = jt + k;
         if (j < nB) {
           sh_alo[k] = A.s_alo[j];
           sh_oth[k] = A.s_oth[j];
@@ -450,42 +491,30 @@ __global__ void __launch_bounds__(kTI) k_sweep_tiled(SweepArgs A) {
       }
       __syncthreads();
       const int cnt = (int)min((int64_t)kTJ, jend - jt);
-      for (int k = 0; k < cnt; ++k) {
-        const int64_t j = jt + k;
-        const float alo = sh_alo[k];
-        const float4 oj = sh_oth[k];
-        const bool hit = valid & (j > i) & (alo <= ahi) & (oj.x <= oi.y) & (oi.x <= oj.y) & (oj.z <= oi.w) &
-                         (oi.z <= oj.w);
-        bool is_vf = false, is_ee = false, sup = false;
-        int p0 = 0, p1 = 0;
-        if (__any_sync(0xFFFFFFFFu, hit)) {
-          if (hit) {
-            bool vf;
-            const int4 vj = sh_vid[k];
-            if (candidate(vi, ki, vj, A.nV, A.nE, vf, p0, p1)) {
-              sup = true;
-              if (!have_exact) {
+      const int jl0 = (int)(jt - i0);      // local index of the tile's first box
+      const bool ordered = jl0 > kTI - 1;   // every j of the tile follows every i
+      for (int k = 0; k < cnt; k += 4) {
+        unsigned bits = 0;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                  ilo[a] = A.lo64[a * nB + vi.w];
-                  ihi[a] = A.hi64[a * nB + vi.w];
-                }
-                have_exact = true;
-              }
-              const int bj = vj.w;
-              bool ov = true;
+        for (int u = 0; u < 4; ++u) {
+          const float alo = sh_alo[k + u];
+          const float4 oj = sh_oth[k + u];
+          const int jl = jl0 + k + u;
+          const bool h0 = (alo <= ahi[0]) & (oj.x <= oi[0].y) & (oi[0].x <= oj.y) & (oj.z <= oi[0].w) &
+                          (oi[0].z <= oj.w) & (ordered | (jl > li0));
+          const bool h1 = (alo <= ahi[1]) & (oj.x <= oi[1].y) & (oi[1].x <= oj.y) & (oj.z <= oi[1].w) &
+                          (oi[1].z <= oj.w) & (ordered | (jl > li1));
+          bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
+        }
+        if (__any_sync(0xFFFFFFFFu, bits)) {
 #pragma unroll
-              for (int a = 0; a < 3; ++a) {
-                long long jlo = A.lo64[a * nB + bj], jhi = A.hi64[a * nB + bj];
-                ov &= (jlo <= ihi[a]) & (ilo[a] <= jhi);
-              }
-              is_vf = ov && vf;
-              is_ee = ov && !vf;
+          for (int bb = 0; bb < 8; ++bb) {
+            const bool hit = (bits >> bb) & 1u;
+            if (__any_sync(0xFFFFFFFFu, hit)) {
+              const int r = bb & 1;
+              sweep_hit(A, hit, vi[r], ki[r], sh_vid[k + (bb >> 1)], nB);
             }
           }
-          const unsigned bs = __ballot_sync(0xFFFFFFFFu, sup);
-          if (bs && lane == 0) atomicAdd(&A.ctl->n_superset, (unsigned long long)__popc(bs));
-          emit(A, is_vf, is_ee, p0, p1);
         }
       }
     }

@@ -24,6 +24,10 @@ struct DevCtl {
   unsigned long long n_intervals, n_exported, n_capped, queue_peak;
   long long pair_counts[2];      // ccd_step: pairs for the narrow phase (clamped)
   unsigned long long t_start, t_exhausted, t_end;  // %globaltimer stamps of the narrow kernel
+  unsigned long long n_donated;  // subtrees passed between lanes of a warp
+  unsigned long long n_intervals_tail;  // intervals evaluated after the query list ran out
+  int rerun;                     // zero-TOI rule: 1 when the second pass must run
+  int pad_;
 };
 
 struct RingCell {
@@ -48,15 +52,22 @@ struct NarrowArgs {
   long long max_iter;
   int mode;                      // 0 per pair, 1 earliest only
   int budget;                    // intervals before a lane hands out its work
+  int no_zero;                   // zero-TOI rule: intervals with t_lo = 0 are always split
+  int only_if_rerun;             // return at once unless ctl->rerun is set
   unsigned long long *toi_vf_bits, *toi_ee_bits;   // mode 0 outputs (bits of doubles)
   uint32_t *qflags;              // [n_vf + n_ee] scratch
   unsigned long long *qiters;    // [n_vf + n_ee] scratch
   RingCell *ring;
   unsigned long long ring_mask;  // capacity - 1
+  unsigned long long *qrec;      // query records, 24 words x rec_stride (NULL: set up in the kernel)
+  int64_t rec_stride;
 };
 
 __global__ void k_narrow(NarrowArgs A);
+__global__ void k_prepare_queries(NarrowArgs A);
 __global__ void k_ring_init(RingCell *ring, unsigned long long cap, unsigned long long base);
+__global__ void k_nozero_prepare(DevCtl *ctl);
+__global__ void k_nozero_finish(DevCtl *ctl);
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v);
 __global__ void k_flags_out(const uint32_t *qflags, int64_t n_vf, int64_t n_ee, uint8_t *flags_vf,
                             uint8_t *flags_ee, DevCtl *ctl);
@@ -75,7 +86,7 @@ struct BroadBufs {
   // sort (keys are 4 or 8 bytes: single-precision or FP64 form)
   void *keys[2];                 // [nB]
   uint32_t *vals[2];             // [nB]
-  uint32_t *hist;                // [256 * nTiles]
+  uint32_t *hist;                // [256 * nTiles + 256]: digit-major counts, then digit totals
   // sorted by the minimum on the sweep axis
   float *s_alo, *s_ahi;          // [nB]
   float4 *s_oth;                 // [nB] (lo1, hi1, lo2, hi2)

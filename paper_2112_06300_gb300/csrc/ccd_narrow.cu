@@ -164,6 +164,25 @@ __device__ __forceinline__ int last_axis(const unsigned long long K[3], const No
   return best;
 }
 
+// The shallowest pending right sibling on the path from the unit's root to
+// node N (depth `depth`): the largest subtree the lane still owes.  Returns its
+// depth (0 if none) and the sibling in S.
+__device__ __forceinline__ int shallowest_pending(const unsigned long long K[3], const Node &N, int depth,
+                                                  int root_depth, Node &S) {
+  Node W = N;
+  int found = 0;
+  for (int d = depth; d > root_depth; --d) {
+    int a = last_axis(K, W);
+    if ((W.n(a) & 1) == 0) {
+      S = W;
+      S.add(a, 1);
+      found = d;
+    }
+    W.up(a);
+  }
+  return found;
+}
+
 struct Box3 {
   double lo[3], hi[3];
 };
@@ -284,6 +303,56 @@ __device__ __forceinline__ void query_ids(int64_t q, int64_t n_vf, const int32_t
   }
 }
 
+// Query records (the paper's CD step, Section "Broad-Phase", computed once per
+// query in a dense pass): the set-up of setup_query stored as structure of
+// arrays, 24 words per query -- c0[3][3], dc[3][3], the error box e[3] (as a
+// double) and the split keys K[3]; bit 63 of K[0] marks a vertex-face query.
+constexpr int kRecWords = 24;
+
+__device__ __forceinline__ void store_record(const QueryData &Q, bool vf, unsigned long long *rec, int64_t stride,
+                                             int64_t q) {
+  int w = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) rec[(w++) * stride + q] = dbits(Q.c0[j][x]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) rec[(w++) * stride + q] = dbits(Q.dc[j][x]);
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    // ebox_p is the ordered key of a positive double: its bits
+    rec[(w++) * stride + q] = (unsigned long long)Q.ebox_p[x];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) rec[(w++) * stride + q] = Q.K[k] | (k == 0 && vf ? (1ull << 63) : 0ull);
+}
+
+__device__ __forceinline__ void load_record(QueryData &Q, bool &vf, const unsigned long long *__restrict__ rec,
+                                            int64_t stride, int64_t q) {
+  int w = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) Q.c0[j][x] = __longlong_as_double((long long)__ldg(&rec[(w++) * stride + q]));
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) Q.dc[j][x] = __longlong_as_double((long long)__ldg(&rec[(w++) * stride + q]));
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const long long e = (long long)__ldg(&rec[(w++) * stride + q]);
+    Q.ebox_p[x] = e;
+    Q.ebox_n[x] = f64_ord(-__longlong_as_double(e));
+  }
+  unsigned long long k0 = __ldg(&rec[(w++) * stride + q]);
+  vf = (k0 >> 63) != 0;
+  Q.K[0] = k0 & ~(1ull << 63);
+  Q.K[1] = __ldg(&rec[(w++) * stride + q]);
+  Q.K[2] = __ldg(&rec[(w++) * stride + q]);
+}
+
 }  // namespace
 
 constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a warp retires
@@ -292,9 +361,10 @@ constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a
 // decided for the whole warp (ballots and broadcasts), and the per-lane work
 // sits in structured branches, so the lanes of a warp reconverge every
 // iteration and the FP64 instructions of an interval issue once per warp.
-__global__ void __launch_bounds__(kNarrowThreads, 3)
+__global__ void __launch_bounds__(kNarrowThreads, 4)
 k_narrow(NarrowArgs A) {
   DevCtl *ctl = A.ctl;
+  if (A.only_if_rerun && ctl->rerun == 0) return;
   if (A.counts_from_ctl) {
     A.n_vf = ctl->pair_counts[0];
     A.n_ee = ctl->pair_counts[1];
@@ -314,10 +384,15 @@ k_narrow(NarrowArgs A) {
   Node N{0, 0, 0, 0, 0, 0};
   int depth = 0, root_depth = 0;
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
-  long long cnt = 0, cap_left = 0;
+  long long cnt = 0, cap_left = 0, since = 0;   // since: evaluations since the last hand-off
   unsigned flags = 0;
-  long long n_eval = 0, n_exp = 0, n_cap = 0;
+  long long n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0;
   int idle_rounds = 0;
+  unsigned long long pf_toi = kInfBits, pf_qnext = 0;   // lane 0: prefetched shared values
+  if (lane == 0) {
+    pf_toi = ld_relaxed_u64(&ctl->toi_bits);
+    pf_qnext = ld_relaxed_u64(&ctl->q_next);
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->t_start, 0ull, globaltimer());
 
   while (true) {
@@ -393,6 +468,75 @@ k_narrow(NarrowArgs A) {
                             : 0;
         if (lane == 0 && got) atomicAdd(&ctl->pending, (unsigned long long)got);
       }
+      // Intra-warp donation: lanes still idle (no query left, nothing ready in
+      // the ring) take the shallowest pending sibling of a busy lane of their
+      // own warp; the query data moves by shuffles, the donor keeps the rest
+      // of its subtree (its root moves down to the donated sibling's depth).
+      const unsigned idle = __ballot_sync(FULL, !have);
+      if (idle && exhausted) {
+        // candidate donors: the first busy lanes, one per idle lane; only they
+        // walk their path to find the shallowest pending sibling
+        const unsigned busy = __ballot_sync(FULL, have && !fresh);
+        const bool cand = have && !fresh && __popc(busy & lt_mask) < __popc(idle);
+        Node S{0, 0, 0, 0, 0, 0};
+        int dS = 0;
+        if (cand) dS = shallowest_pending(Q.K, N, depth, root_depth, S);
+        const unsigned donors = __ballot_sync(FULL, dS > 0);
+        const int pairs = min(__popc(donors), __popc(idle));
+        if (pairs > 0) {
+          // every donated subtree is a new unit for the termination count
+          if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)pairs);
+          const bool recv = !have && __popc(idle & lt_mask) < pairs;
+          const bool give = dS > 0 && __popc(donors & lt_mask) < pairs;
+          const int src = recv ? (int)__fns(donors, 0, __popc(idle & lt_mask) + 1) : lane;
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+              const double c0v = __shfl_sync(FULL, Q.c0[j][x], src);
+              const double dcv = __shfl_sync(FULL, Q.dc[j][x], src);
+              if (recv) {
+                Q.c0[j][x] = c0v;
+                Q.dc[j][x] = dcv;
+              }
+            }
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const long long ep = __shfl_sync(FULL, Q.ebox_p[x], src);
+            const long long en = __shfl_sync(FULL, Q.ebox_n[x], src);
+            const unsigned long long kk = __shfl_sync(FULL, Q.K[x], src);
+            if (recv) {
+              Q.ebox_p[x] = ep;
+              Q.ebox_n[x] = en;
+              Q.K[x] = kk;
+            }
+          }
+          const uint64_t s0 = __shfl_sync(FULL, S.n0, src), s1 = __shfl_sync(FULL, S.n1, src),
+                         s2 = __shfl_sync(FULL, S.n2, src);
+          const int l0 = __shfl_sync(FULL, S.l0, src), l1 = __shfl_sync(FULL, S.l1, src),
+                    l2 = __shfl_sync(FULL, S.l2, src);
+          const long long qv = __shfl_sync(FULL, (long long)q, src);
+          const int vfv = __shfl_sync(FULL, (int)vf, src);
+          const unsigned long long tqv = __shfl_sync(FULL, tq, src);
+          const long long capv = __shfl_sync(FULL, cap_left - cnt, src);
+          if (recv) {
+            q = qv;
+            vf = vfv != 0;
+            N = Node{s0, s1, s2, l0, l1, l2};
+            depth = root_depth = N.depth();
+            tq = tqv;
+            cap_left = capv;
+            cnt = since = 0;
+            flags = 0;
+            have = true;
+            whole = false;
+          }
+          if (give) {
+            root_depth = dS;   // the donated sibling is no longer ours
+            ++n_don;
+          }
+        }
+      }
     }
 
     // ---- 2. a warp with no work idles or retires (uniform) ----------------
@@ -410,11 +554,15 @@ k_narrow(NarrowArgs A) {
 
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
-      int ids[4];
-      query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
-      setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep);
+      if (A.qrec) {
+        load_record(Q, vf, A.qrec, A.rec_stride, q);
+      } else {
+        int ids[4];
+        query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
+        setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep);
+      }
       depth = root_depth = N.depth();
-      cnt = 0;
+      cnt = since = 0;
       flags = 0;
       tq = kInfBits;
       cap_left = A.max_iter;
@@ -434,15 +582,16 @@ k_narrow(NarrowArgs A) {
     }
 
     // ---- 4. ProcessInterval on the current node ---------------------------
+    // shared values loaded during the previous iteration (stale values only
+    // prune less or hand off later)
     unsigned long long cut = tq;
-    unsigned long long g = 0, qn = 0;
-    if (lane == 0) {
-      g = ld_relaxed_u64(&ctl->toi_bits);
-      qn = ld_relaxed_u64(&ctl->q_next);
-    }
-    g = __shfl_sync(FULL, g, 0);
+    const unsigned long long g = __shfl_sync(FULL, pf_toi, 0);
     // hand work out only once every query has been taken (idle lanes exist)
-    const bool tail_phase = __shfl_sync(FULL, qn, 0) >= (unsigned long long)nq;
+    const bool tail_phase = __shfl_sync(FULL, pf_qnext, 0) >= (unsigned long long)nq;
+    if (lane == 0) {
+      pf_toi = ld_relaxed_u64(&ctl->toi_bits);
+      pf_qnext = ld_relaxed_u64(&ctl->q_next);
+    }
     if (A.mode == 1) cut = g < cut ? g : cut;
     bool node_done = true;     // false when the node was split (go to its left child)
     bool unit_end = false;
@@ -453,7 +602,7 @@ k_narrow(NarrowArgs A) {
         // pruned: starts at or after the current t*
       } else if (vf && dbits(dyadic(N.n1, N.l1)) > dbits(dyadic((1ull << N.l2) - N.n2, N.l2))) {
         // vertex-face: u_lo > 1 - v_lo, the interval lies outside the simplex
-      } else if (++cnt > cap_left) {
+      } else if (!(A.no_zero && N.n0 == 0) && ++cnt > cap_left) {
         // iteration cap: t* = min(t*, earliest left end among the live intervals)
         unsigned long long m = dbits(tl);
         Node W = N;
@@ -476,6 +625,8 @@ k_narrow(NarrowArgs A) {
     }
     if (evaluate) {
       ++n_eval;
+      n_eval_tail += tail_phase;
+      ++since;
       const double tr = dyadic(N.n0 + 1, N.l0);
       const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
       const double vl = dyadic(N.n2, N.l2), vr = dyadic(N.n2 + 1, N.l2);
@@ -490,7 +641,8 @@ k_narrow(NarrowArgs A) {
         narrow &= dbits(__dsub_rn(B.hi[x], B.lo[x])) < delta_bits;
       }
       if (!miss) {
-        bool accept = narrow || inside;
+        // zero-TOI rule: an interval starting at t = 0 is always split
+        bool accept = (narrow || inside) && !(A.no_zero && N.n0 == 0);
         int a = -1;
         if (!accept) {
           a = split_axis(Q.K, N);
@@ -527,48 +679,33 @@ k_narrow(NarrowArgs A) {
       }
     }
 
-    // ---- 6. hand out the live intervals after `budget` evaluations --------
-    if (have && !unit_end && cnt >= A.budget && tail_phase) {
-      int nexp = 1;
-      {
-        Node W = N;
-        for (int d = depth; d > root_depth; --d) {
-          int a = last_axis(Q.K, W);
-          nexp += (W.n(a) & 1) == 0;
-          W.up(a);
-        }
-      }
-      const unsigned long long pos =
-          ring_reserve(&ctl->q_tail, &ctl->q_head, (unsigned long long)nexp, ring_cap >> 2);
-      if (pos != ~0ull) {
-        // publish what the takers read before any item becomes visible
-        if (tq != kInfBits) {
-          if (A.mode == 0)
-            atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
-          else
-            atomicMin(&ctl->toi_bits, tq);
-        }
-        atomicAdd(&A.qiters[q], (unsigned long long)cnt);
-        atomicAdd(&ctl->pending, (unsigned long long)nexp);
-        ring_write(A.ring, A.ring_mask, pos, (uint32_t)q, N, &ctl->status);
-        int k = 1;
-        Node W = N;
-        for (int d = depth; d > root_depth; --d) {
-          int a = last_axis(Q.K, W);
-          if ((W.n(a) & 1) == 0) {
-            Node S = W;
-            S.add(a, 1);
-            ring_write(A.ring, A.ring_mask, pos + k, (uint32_t)q, S, &ctl->status);
-            ++k;
+    // ---- 6. in the tail phase, hand the shallowest pending sibling to the
+    //         ring every `budget` evaluations (other warps take it) ----------
+    if (have && !unit_end && since >= A.budget && tail_phase) {
+      Node S{0, 0, 0, 0, 0, 0};
+      const int dS = shallowest_pending(Q.K, N, depth, root_depth, S);
+      since = 0;
+      if (dS > 0) {
+        const unsigned long long pos = ring_reserve(&ctl->q_tail, &ctl->q_head, 1ull, ring_cap >> 2);
+        if (pos != ~0ull) {
+          // publish what the taker reads before the item becomes visible
+          if (tq != kInfBits) {
+            if (A.mode == 0)
+              atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
+            else
+              atomicMin(&ctl->toi_bits, tq);
           }
-          W.up(a);
+          atomicAdd(&A.qiters[q], (unsigned long long)cnt);
+          cap_left -= cnt;
+          cnt = 0;
+          atomicAdd(&ctl->pending, 1ull);
+          ring_write(A.ring, A.ring_mask, pos, (uint32_t)q, S, &ctl->status);
+          root_depth = dS;
+          const unsigned long long h = ld_relaxed_u64(&ctl->q_head), t = pos + 1;
+          const unsigned long long occ = t > h ? t - h : 0;
+          if (occ > ld_relaxed_u64(&ctl->queue_peak)) atomicMax(&ctl->queue_peak, occ);
+          ++n_exp;
         }
-        const unsigned long long h = ld_relaxed_u64(&ctl->q_head), t = pos + nexp;
-        const unsigned long long occ = t > h ? t - h : 0;
-        if (occ > ld_relaxed_u64(&ctl->queue_peak)) atomicMax(&ctl->queue_peak, occ);
-        n_exp += nexp;
-        unit_end = true;
-        cnt = 0;   // already added to qiters
       }
     }
 
@@ -591,7 +728,48 @@ k_narrow(NarrowArgs A) {
   if (n_eval) atomicAdd(&ctl->n_intervals, (unsigned long long)n_eval);
   if (n_exp) atomicAdd(&ctl->n_exported, (unsigned long long)n_exp);
   if (n_cap) atomicAdd(&ctl->n_capped, (unsigned long long)n_cap);
+  if (n_don) atomicAdd(&ctl->n_donated, (unsigned long long)n_don);
+  if (n_eval_tail) atomicAdd(&ctl->n_intervals_tail, (unsigned long long)n_eval_tail);
   if (lane == 0) atomicMax(&ctl->t_end, globaltimer());
+}
+
+// One thread per query: gather the 4 vertices at t = 0 and t = 1 and store the
+// query's set-up as a record, so that the narrow kernel's lanes set up a unit
+// from 24 coalesced loads with no FP64 work.
+__global__ void k_prepare_queries(NarrowArgs A) {
+  if (A.only_if_rerun && A.ctl->rerun == 0) return;
+  if (A.counts_from_ctl) {
+    A.n_vf = A.ctl->pair_counts[0];
+    A.n_ee = A.ctl->pair_counts[1];
+  }
+  const int64_t nq = A.n_vf + A.n_ee;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+    int ids[4];
+    bool vf;
+    query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
+    QueryData Q;
+    setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep);
+    store_record(Q, vf, A.qrec, A.rec_stride, q);
+  }
+}
+
+// Zero-TOI rule (appendix "Zero time of impact and minimum separation"): when
+// the first pass found t* = 0, reset the narrow-phase state for a second
+// pass (min_sep = 0, intervals at t = 0 always split) ...
+__global__ void k_nozero_prepare(DevCtl *ctl) {
+  ctl->rerun = ctl->toi_bits == 0 ? 1 : 0;
+  if (ctl->rerun) {
+    ctl->q_next = 0;
+    ctl->pending = 0;
+    ctl->toi_bits = kInfBits;
+    ctl->t_start = ctl->t_exhausted = ctl->t_end = 0;
+  }
+}
+
+// ... and scale its result by 0.8.
+__global__ void k_nozero_finish(DevCtl *ctl) {
+  if (ctl->rerun && ctl->toi_bits != kInfBits)
+    ctl->toi_bits = dbits(__dmul_rn(0.8, __longlong_as_double((long long)ctl->toi_bits)));
 }
 
 __global__ void k_ring_init(RingCell *ring, unsigned long long cap, unsigned long long base) {

@@ -64,6 +64,8 @@ __global__ void k_noalloc_reset(DevCtl *ctl) {
   ctl->toi_bits = 0x7FF0000000000000ull;
   ctl->n_intervals = ctl->n_exported = ctl->n_capped = ctl->queue_peak = 0;
   ctl->t_start = ctl->t_exhausted = ctl->t_end = 0;
+  ctl->n_donated = 0;
+  ctl->n_intervals_tail = 0;
 }
 
 __global__ void k_noalloc_status(const DevCtl *ctl, int32_t *status) { *status = ctl->status; }
@@ -131,6 +133,10 @@ extern "C" int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t
   A.max_iter = max_iter;
   A.mode = mode;
   A.budget = 64;
+  A.no_zero = 0;
+  A.only_if_rerun = 0;
+  A.qrec = nullptr;   // no record buffer: lanes set their queries up themselves
+  A.rec_stride = 0;
   A.toi_vf_bits = mode == 0 ? (unsigned long long *)toi_vf : nullptr;
   A.toi_ee_bits = mode == 0 ? (unsigned long long *)toi_ee : nullptr;
   A.qflags = (uint32_t *)(base + kCtlBytes);

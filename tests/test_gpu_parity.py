@@ -241,3 +241,25 @@ def test_warp_per_box_sweep_matches_oracle(ccd, s):
         np.testing.assert_array_equal(sorted_pairs(ee), oee)
     finally:
         c.close()
+
+
+def test_no_zero_toi_rule_matches_oracle(ccd):
+    c = ccd.CCD(0, no_zero_toi=1)
+    try:
+        h = 2.0 ** -12
+        tri = [(0.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0)]
+        V0 = np.array([(0.25, 0.25, h)] + tri)
+        V1 = np.array([(0.25, 0.25, h - 1.0)] + tri)
+        E = np.array([[1, 2], [2, 3], [3, 1]], np.int32)
+        F = np.array([[1, 2, 3]], np.int32)
+        d = ccd.mesh_to_device(V0, V1, E, F)
+        t = c.step(*d, min_sep=0.01)
+        assert t == O.step(V0, V1, E, F, min_sep=0.01, no_zero_toi=True) and t > 0
+        # scenes whose first pass is 0 with a large min_sep (that pass ends as
+        # soon as one pair is within min_sep at t = 0), and one whose is not
+        for s, ms in ((SCENES[2], 0.05), (SCENES[0], 0.3), (SCENES[0], 0.0)):
+            d = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+            t = c.step(*d, min_sep=ms)
+            assert t == O.step(s.V0, s.V1, s.E, s.F, min_sep=ms, no_zero_toi=True)
+    finally:
+        c.close()

@@ -137,3 +137,39 @@ def test_touching_at_endpoints_and_degenerate():
     # a query touching at t = 0 must report 0 exactly
     zero = [q for q in touch if X.toi(bool(is_vf[q]), X0[q].tolist(), X1[q].tolist()) == 0]
     assert zero and all(toi[q] == 0.0 for q in zero)
+
+
+def test_no_zero_toi_rule():
+    # a point 2^-12 above a triangle moving down at speed 1: first contact at
+    # t = 2^-12; with min_sep = 0.01 the first pass reports 0, the rerun with
+    # min_sep = 0 and the zero-TOI rule must give 0 < t <= 2^-12 (scaled 0.8)
+    h = 2.0 ** -12
+    tri = [(0.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0)]
+    V0 = np.array([(0.25, 0.25, h)] + tri)
+    V1 = np.array([(0.25, 0.25, h - 1.0)] + tri)
+    E = np.array([[1, 2], [2, 3], [3, 1]], np.int32)
+    F = np.array([[1, 2, 3]], np.int32)
+    assert O.step(V0, V1, E, F, min_sep=0.01) == 0.0
+    t = O.step(V0, V1, E, F, min_sep=0.01, no_zero_toi=True)
+    assert 0.0 < t <= 0.8 * h
+    assert t >= 0.8 * (h - 2e-6)
+    # without a zero first pass the rule changes nothing
+    assert O.step(V0, V1, E, F, no_zero_toi=True) == O.step(V0, V1, E, F)
+    # touching at t = 0 stays 0 (the split reaches the level cap and accepts)
+    W0 = np.array([(0.25, 0.25, 0.0)] + tri)
+    W1 = np.array([(0.25, 0.25, -1.0)] + tri)
+    assert O.step(W0, W1, E, F, no_zero_toi=True) == 0.0
+    # conservative on the stress mix: never later than exact, positive when
+    # the exact time is positive
+    X0, X1, is_vf, kind = scenes.narrow_stress_queries(200, seed=13)
+    sc, vf, ee, order = scenes.pack_queries(X0, X1, is_vf)
+    toi_vf, toi_ee, *_ = O.narrow(vf, ee, sc.V0, sc.V1, sc.E, sc.F, no_zero=True)
+    toi = np.empty(len(is_vf))
+    toi[order] = np.concatenate([toi_vf, toi_ee])
+    for q in range(len(is_vf)):
+        r = X.toi(bool(is_vf[q]), X0[q].tolist(), X1[q].tolist())
+        if r is None:
+            continue
+        assert X.le_float(toi[q], r)
+        if X.compare(r, Q(0)) > 0:
+            assert toi[q] > 0.0
