@@ -101,6 +101,7 @@ typedef struct {
     int64_t narrow_tail_ns;  /* narrow kernel: from then until the last lane ended */
     int64_t n_donated;       /* subtrees passed between lanes of one warp */
     int64_t n_intervals_tail;  /* intervals evaluated after every query was taken */
+    int64_t n_intervals_fp64;  /* intervals the single-precision filter left to FP64 */
 } ccd_stats;
 
 /* Fill *o with the defaults. */

@@ -43,7 +43,7 @@ class ccd_stats(ctypes.Structure):
                 ("device_status", ctypes.c_int32), ("pad1", ctypes.c_int32),
                 ("n_launches", ctypes.c_int64), ("narrow_bulk_ns", ctypes.c_int64),
                 ("narrow_tail_ns", ctypes.c_int64), ("n_donated", ctypes.c_int64),
-                ("n_intervals_tail", ctypes.c_int64)]
+                ("n_intervals_tail", ctypes.c_int64), ("n_intervals_fp64", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}

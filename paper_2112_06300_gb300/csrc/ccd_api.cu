@@ -74,6 +74,7 @@ __global__ void k_reset_narrow(DevCtl *c) {
   c->t_start = c->t_exhausted = c->t_end = 0;
   c->n_donated = 0;
   c->n_intervals_tail = 0;
+  c->n_intervals_fp64 = 0;
 }
 __global__ void k_reset_status(DevCtl *c) { c->status = CCD_OK; }
 
@@ -152,7 +153,7 @@ int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
   int64_t cap = std::max<int64_t>(nq, 1024);
   CK(cudaMalloc(&c->qflags, cap * sizeof(uint32_t)));
   CK(cudaMalloc(&c->qiters, cap * sizeof(unsigned long long)));
-  CK(cudaMalloc(&c->qrec, cap * 24 * sizeof(unsigned long long)));
+  CK(cudaMalloc(&c->qrec, cap * (24 * sizeof(unsigned long long) + 28 * sizeof(float))));
   c->cap_q = cap;
   return CCD_OK;
 }
@@ -509,6 +510,7 @@ int ccd_get_status(ccd_ctx *c, ccd_stats *st) {
     st->n_exported = (int64_t)h.n_exported;
     st->n_donated = (int64_t)h.n_donated;
     st->n_intervals_tail = (int64_t)h.n_intervals_tail;
+    st->n_intervals_fp64 = (int64_t)h.n_intervals_fp64;
     st->n_capped = (int64_t)h.n_capped;
     st->queue_peak = (int64_t)h.queue_peak;
     st->device_status = h.status;

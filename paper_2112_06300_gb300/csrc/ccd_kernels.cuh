@@ -26,6 +26,7 @@ struct DevCtl {
   unsigned long long t_start, t_exhausted, t_end;  // %globaltimer stamps of the narrow kernel
   unsigned long long n_donated;  // subtrees passed between lanes of a warp
   unsigned long long n_intervals_tail;  // intervals evaluated after the query list ran out
+  unsigned long long n_intervals_fp64;  // intervals the FP32 filter could not decide
   int rerun;                     // zero-TOI rule: 1 when the second pass must run
   int pad_;
 };
@@ -59,7 +60,8 @@ struct NarrowArgs {
   unsigned long long *qiters;    // [n_vf + n_ee] scratch
   RingCell *ring;
   unsigned long long ring_mask;  // capacity - 1
-  unsigned long long *qrec;      // query records, 24 words x rec_stride (NULL: set up in the kernel)
+  unsigned long long *qrec;      // query records: 24 words then 27 floats, x rec_stride
+                                 // (NULL: lanes set their queries up themselves)
   int64_t rec_stride;
 };
 

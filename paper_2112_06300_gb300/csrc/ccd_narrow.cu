@@ -43,6 +43,10 @@ struct QueryData {
   double dc[3][3];   // value at t = 1 minus value at t = 0
   long long ebox_p[3], ebox_n[3];  // ordered keys of +ebox and -ebox
   unsigned long long K[3];         // split keys: bits of L_t, L_u, L_v (0: never)
+  // single-precision filter (see inclusion32): rounded c0, dc and, per axis,
+  // the FP32 error bound e32 and the decision thresholds tm and wn
+  float c0f[3][3], dcf[3][3];
+  float e32[3], tm[3], wn[3];
 };
 
 __device__ __forceinline__ unsigned long long dbits(double d) {
@@ -52,7 +56,7 @@ __device__ __forceinline__ unsigned long long dbits(double d) {
 // Per-query set-up; the reading of the error box and split weights matches the
 // oracle's setup_query.  ids: VF (P, T0, T1, T2), EE (A0, A1, B0, B1).
 __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const double *__restrict__ V0,
-                            const double *__restrict__ V1, int64_t nV, double min_sep) {
+                            const double *__restrict__ V1, int64_t nV, double min_sep, double delta) {
   double x0[4][3], x1[4][3];
 #pragma unroll
   for (int k = 0; k < 4; ++k)
@@ -92,6 +96,19 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     e = __longlong_as_double(__double_as_longlong(e) + 1);                   // one ulp up
     Q.ebox_p[x] = f64_ord(e);
     Q.ebox_n[x] = f64_ord(-e);
+    // FP32 filter bounds, all rounded upward.  e32 = 40 * 2^-24 * max(m, 2^-100)
+    // bounds the distance of every FP32 corner from the exact one (derivation
+    // at inclusion32).  A decision taken on the FP32 hull must hold for the
+    // FP64 hull, which is within eps of the exact one:
+    //   tm = e + eps + e32  (beyond it, the FP64 hull misses or sticks out of C)
+    //   wn = (delta (1 + 2^-50) + 2 eps + 2 e32)(1 + 2^-23)  (an FP32 width at or
+    //        above it means an FP64 width at or above delta)
+    const double m32 = fmax(__longlong_as_double((long long)m), 0x1p-100);
+    const double e32 = (double)__double2float_ru(__dmul_ru(m32, 40.0 * 0x1p-24));
+    Q.e32[x] = (float)e32;
+    Q.tm[x] = __double2float_ru(__dadd_ru(__dadd_ru(e, eps), e32));
+    const double wn = __dadd_ru(__dadd_ru(__dmul_ru(delta, 1.0 + 0x1p-50), __dmul_ru(2.0, eps)), __dmul_ru(2.0, e32));
+    Q.wn[x] = __double2float_ru(__dmul_ru(wn, 1.0 + 0x1p-23));
     double st = __dadd_rn(dabs_int(Q.dc[0][x]), dabs_int(Q.dc[1][x]));
     st = __dadd_rn(st, dabs_int(Q.dc[2][x]));
     unsigned long long sb = dbits(st);
@@ -105,6 +122,13 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     Lu = u0 > Lu ? u0 : Lu;
     Lv = v0 > Lv ? v0 : Lv;
   }
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Q.c0f[j][x] = __double2float_rn(Q.c0[j][x]);
+      Q.dcf[j][x] = __double2float_rn(Q.dc[j][x]);
+    }
   const unsigned long long kFloor = 0x0DF0000000000000ull;  // 2^-800
   Q.K[0] = Lt < kFloor ? 0 : Lt;
   Q.K[1] = Lu < kFloor ? 0 : Lu;
@@ -228,6 +252,111 @@ __device__ __forceinline__ void inclusion(const QueryData &Q, bool vf, double tl
   }
 }
 
+// Single-precision hull of F over an interval with every level <= 24 (its
+// ends are then exact floats), same expression tree and corner selection as
+// inclusion().  Error bound, with u = 2^-24, m the largest |coordinate| on the
+// axis and the FP64 set-up errors (O(2^-53 m)) included:
+//   rounding c0 and dc to float:      2 u m and 4 u m;
+//   c(t) = fma(t, dc, c0):            |c(t) - exact| <= 6 u m + 2 u m = 8 u m;
+//   inner term fma(-v, e2, w):        2 x 8 u m + 4 u m = 20 u m;
+//   corner fma(-u, e1, g):            20 u m + 8 u m + 6 u m = 34 u m;
+// e32 = 40 u m leaves room for second-order and FP64 terms.  Rounding is
+// monotone, so the selected corners are the extremes of the computed ones,
+// and the FP32 hull is within e32 of the exact hull on every axis.
+struct Box3f {
+  float lo[3], hi[3];
+};
+
+__device__ __forceinline__ void inclusion32(const float c0f[3][3], const float dcf[3][3], bool vf, float tl, float tr,
+                                            float ul, float ur, float vl, float vr, Box3f &B) {
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    float lo = 0.f, hi = 0.f;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const float tt = it ? tr : tl;
+      const float w = fmaf(tt, dcf[0][x], c0f[0][x]);
+      const float a = fmaf(tt, dcf[1][x], c0f[1][x]);
+      const float b = fmaf(tt, dcf[2][x], c0f[2][x]);
+      const bool ap = a > 0.f, bp = b > 0.f;
+      float fmin, fmax;
+      if (vf) {
+        const float gmin = fmaf(-(bp ? vr : vl), b, w);
+        const float gmax = fmaf(-(bp ? vl : vr), b, w);
+        fmin = fmaf(-(ap ? ur : ul), a, gmin);
+        fmax = fmaf(-(ap ? ul : ur), a, gmax);
+      } else {
+        const float gmin = fmaf(ap ? ul : ur, a, w);
+        const float gmax = fmaf(ap ? ur : ul, a, w);
+        fmin = fmaf(-(bp ? vr : vl), b, gmin);
+        fmax = fmaf(-(bp ? vl : vr), b, gmax);
+      }
+      lo = it ? fminf(lo, fmin) : fmin;
+      hi = it ? fmaxf(hi, fmax) : fmax;
+    }
+    B.lo[x] = lo;
+    B.hi[x] = hi;
+  }
+}
+
+// n / 2^l as a float, exact for n <= 2^24 and l <= 24, assembled from bits.
+__device__ __forceinline__ float dyadic32(uint64_t n, int l) {
+  if (n == 0) return 0.f;
+  const unsigned v = (unsigned)n;
+  const int msb = 31 - __clz((int)v);
+  const unsigned frac = (msb <= 23 ? (v << (23 - msb)) : (v >> (msb - 23))) & 0x7FFFFFu;
+  return __uint_as_float(((unsigned)(msb - l + 127) << 23) | frac);
+}
+
+// The FP64 part of a lane's query, kept in shared memory (structure of
+// arrays: consecutive lanes hit consecutive banks).
+struct SharedQuery {
+  double c0[9][kNarrowThreads];
+  double dc[9][kNarrowThreads];
+  long long ep[3][kNarrowThreads], en[3][kNarrowThreads];
+};
+
+__device__ __forceinline__ void put_shared(SharedQuery &S, int tid, const QueryData &Q) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      S.c0[3 * j + x][tid] = Q.c0[j][x];
+      S.dc[3 * j + x][tid] = Q.dc[j][x];
+    }
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    S.ep[x][tid] = Q.ebox_p[x];
+    S.en[x][tid] = Q.ebox_n[x];
+  }
+}
+
+__device__ __forceinline__ void copy_shared(SharedQuery &S, int dst, int src) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    S.c0[k][dst] = S.c0[k][src];
+    S.dc[k][dst] = S.dc[k][src];
+  }
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    S.ep[x][dst] = S.ep[x][src];
+    S.en[x][dst] = S.en[x][src];
+  }
+}
+
+__device__ __forceinline__ void inclusion_shared(const SharedQuery &S, int tid, bool vf, double tl, double tr,
+                                                 double ul, double ur, double vl, double vr, Box3 &B) {
+  QueryData Q;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Q.c0[j][x] = S.c0[3 * j + x][tid];
+      Q.dc[j][x] = S.dc[3 * j + x][tid];
+    }
+  inclusion(Q, vf, tl, tr, ul, ur, vl, vr, B);
+}
+
 // ---- bounded MPMC ring of exported intervals -------------------------------
 // Cell: sequence number + interval.  A cell at position p holds data when
 // seq == p + 1 and is free for position p + cap once its reader stores
@@ -327,6 +456,21 @@ __device__ __forceinline__ void store_record(const QueryData &Q, bool vf, unsign
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) rec[(w++) * stride + q] = Q.K[k] | (k == 0 && vf ? (1ull << 63) : 0ull);
+  float *r32 = (float *)(rec + kRecWords * stride);
+  int f = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      r32[(f++) * stride + q] = Q.c0f[j][x];
+      r32[(f++) * stride + q] = Q.dcf[j][x];
+    }
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    r32[(f++) * stride + q] = Q.e32[x];
+    r32[(f++) * stride + q] = Q.tm[x];
+    r32[(f++) * stride + q] = Q.wn[x];
+  }
 }
 
 __device__ __forceinline__ void load_record(QueryData &Q, bool &vf, const unsigned long long *__restrict__ rec,
@@ -351,6 +495,21 @@ __device__ __forceinline__ void load_record(QueryData &Q, bool &vf, const unsign
   Q.K[0] = k0 & ~(1ull << 63);
   Q.K[1] = __ldg(&rec[(w++) * stride + q]);
   Q.K[2] = __ldg(&rec[(w++) * stride + q]);
+  const float *r32 = (const float *)(rec + kRecWords * stride);
+  int f = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Q.c0f[j][x] = __ldg(&r32[(f++) * stride + q]);
+      Q.dcf[j][x] = __ldg(&r32[(f++) * stride + q]);
+    }
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    Q.e32[x] = __ldg(&r32[(f++) * stride + q]);
+    Q.tm[x] = __ldg(&r32[(f++) * stride + q]);
+    Q.wn[x] = __ldg(&r32[(f++) * stride + q]);
+  }
 }
 
 }  // namespace
@@ -361,7 +520,7 @@ constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a
 // decided for the whole warp (ballots and broadcasts), and the per-lane work
 // sits in structured branches, so the lanes of a warp reconverge every
 // iteration and the FP64 instructions of an interval issue once per warp.
-__global__ void __launch_bounds__(kNarrowThreads, 4)
+__global__ void __launch_bounds__(kNarrowThreads, 3)
 k_narrow(NarrowArgs A) {
   DevCtl *ctl = A.ctl;
   if (A.only_if_rerun && ctl->rerun == 0) return;
@@ -376,7 +535,11 @@ k_narrow(NarrowArgs A) {
   const unsigned long long delta_bits = dbits(A.delta);
   const unsigned long long ring_cap = A.ring_mask + 1;
 
-  QueryData Q;
+  __shared__ SharedQuery SQ;                 // FP64 part of each lane's query
+  const int tid = threadIdx.x;
+  // single-precision filter data and split keys of the lane's query
+  float c0f[3][3], dcf[3][3], e32[3], tm[3], wn[3];
+  unsigned long long K[3] = {0, 0, 0};
   bool vf = false;
   bool have = false, fresh = false, whole = false;
   bool exhausted = false;                    // warp-uniform
@@ -386,7 +549,7 @@ k_narrow(NarrowArgs A) {
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
   long long cnt = 0, cap_left = 0, since = 0;   // since: evaluations since the last hand-off
   unsigned flags = 0;
-  long long n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0;
+  long long n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0, n_eval64 = 0;
   int idle_rounds = 0;
   unsigned long long pf_toi = kInfBits, pf_qnext = 0;   // lane 0: prefetched shared values
   if (lane == 0) {
@@ -480,7 +643,7 @@ k_narrow(NarrowArgs A) {
         const bool cand = have && !fresh && __popc(busy & lt_mask) < __popc(idle);
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
-        if (cand) dS = shallowest_pending(Q.K, N, depth, root_depth, S);
+        if (cand) dS = shallowest_pending(K, N, depth, root_depth, S);
         const unsigned donors = __ballot_sync(FULL, dS > 0);
         const int pairs = min(__popc(donors), __popc(idle));
         if (pairs > 0) {
@@ -489,26 +652,30 @@ k_narrow(NarrowArgs A) {
           const bool recv = !have && __popc(idle & lt_mask) < pairs;
           const bool give = dS > 0 && __popc(donors & lt_mask) < pairs;
           const int src = recv ? (int)__fns(donors, 0, __popc(idle & lt_mask) + 1) : lane;
+          __syncwarp(FULL);
+          if (recv) copy_shared(SQ, tid, (tid & ~31) | src);   // the donor's FP64 data
 #pragma unroll
           for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
-              const double c0v = __shfl_sync(FULL, Q.c0[j][x], src);
-              const double dcv = __shfl_sync(FULL, Q.dc[j][x], src);
+              const float a = __shfl_sync(FULL, c0f[j][x], src);
+              const float b = __shfl_sync(FULL, dcf[j][x], src);
               if (recv) {
-                Q.c0[j][x] = c0v;
-                Q.dc[j][x] = dcv;
+                c0f[j][x] = a;
+                dcf[j][x] = b;
               }
             }
 #pragma unroll
           for (int x = 0; x < 3; ++x) {
-            const long long ep = __shfl_sync(FULL, Q.ebox_p[x], src);
-            const long long en = __shfl_sync(FULL, Q.ebox_n[x], src);
-            const unsigned long long kk = __shfl_sync(FULL, Q.K[x], src);
+            const float a = __shfl_sync(FULL, e32[x], src);
+            const float b = __shfl_sync(FULL, tm[x], src);
+            const float c = __shfl_sync(FULL, wn[x], src);
+            const unsigned long long kk = __shfl_sync(FULL, K[x], src);
             if (recv) {
-              Q.ebox_p[x] = ep;
-              Q.ebox_n[x] = en;
-              Q.K[x] = kk;
+              e32[x] = a;
+              tm[x] = b;
+              wn[x] = c;
+              K[x] = kk;
             }
           }
           const uint64_t s0 = __shfl_sync(FULL, S.n0, src), s1 = __shfl_sync(FULL, S.n1, src),
@@ -554,12 +721,28 @@ k_narrow(NarrowArgs A) {
 
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
+      QueryData Q;
       if (A.qrec) {
         load_record(Q, vf, A.qrec, A.rec_stride, q);
       } else {
         int ids[4];
         query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
-        setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep);
+        setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep, A.delta);
+      }
+      put_shared(SQ, tid, Q);
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          c0f[j][x] = Q.c0f[j][x];
+          dcf[j][x] = Q.dcf[j][x];
+        }
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        e32[x] = Q.e32[x];
+        tm[x] = Q.tm[x];
+        wn[x] = Q.wn[x];
+        K[x] = Q.K[x];
       }
       depth = root_depth = N.depth();
       cnt = since = 0;
@@ -607,7 +790,7 @@ k_narrow(NarrowArgs A) {
         unsigned long long m = dbits(tl);
         Node W = N;
         for (int d = depth; d > root_depth; --d) {
-          int a = last_axis(Q.K, W);
+          int a = last_axis(K, W);
           if ((W.n(a) & 1) == 0) {
             unsigned long long sb = dbits(a == 0 ? dyadic(W.n0 + 1, W.l0) : dyadic(W.n0, W.l0));
             m = sb < m ? sb : m;
@@ -627,25 +810,52 @@ k_narrow(NarrowArgs A) {
       ++n_eval;
       n_eval_tail += tail_phase;
       ++since;
-      const double tr = dyadic(N.n0 + 1, N.l0);
-      const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
-      const double vl = dyadic(N.n2, N.l2), vr = dyadic(N.n2 + 1, N.l2);
-      Box3 B;
-      inclusion(Q, vf, tl, tr, ul, ur, vl, vr, B);
-      bool miss = false, inside = true, narrow = true;
+      // Single-precision filter: when every level is <= 24 the interval's
+      // ends are exact floats and the FP32 hull is within e32 of the exact
+      // hull; a miss, or a split (no miss, not narrow, not inside), proven on
+      // it is certainly the FP64 decision, so FP64 runs only on the rest.
+      bool decided = false, miss = false, accept = false;
+      if (max(max(N.l0, N.l1), N.l2) <= 24) {
+        Box3f Bf;
+        inclusion32(c0f, dcf, vf, dyadic32(N.n0, N.l0), dyadic32(N.n0 + 1, N.l0), dyadic32(N.n1, N.l1),
+                    dyadic32(N.n1 + 1, N.l1), dyadic32(N.n2, N.l2), dyadic32(N.n2 + 1, N.l2), Bf);
+        bool cmiss = false, cnm = true, cni = false, cnn = false;
 #pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        long long lo = f64_ord(B.lo[x]), hi = f64_ord(B.hi[x]);
-        miss |= (lo > Q.ebox_p[x]) | (hi < Q.ebox_n[x]);
-        inside &= (lo >= Q.ebox_n[x]) & (hi <= Q.ebox_p[x]);
-        narrow &= dbits(__dsub_rn(B.hi[x], B.lo[x])) < delta_bits;
+        for (int x = 0; x < 3; ++x) {
+          cmiss |= (Bf.lo[x] > tm[x]) | (Bf.hi[x] < -tm[x]);
+          cnm &= (Bf.lo[x] <= -e32[x]) & (Bf.hi[x] >= e32[x]);
+          cni |= (Bf.lo[x] < -tm[x]) | (Bf.hi[x] > tm[x]);
+          cnn |= __fsub_rn(Bf.hi[x], Bf.lo[x]) >= wn[x];
+        }
+        if (cmiss) {
+          decided = miss = true;
+        } else if (cnm & cni & cnn) {
+          decided = true;   // split
+        }
+      }
+      if (!decided) {
+        ++n_eval64;
+        const double tr = dyadic(N.n0 + 1, N.l0);
+        const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
+        const double vl = dyadic(N.n2, N.l2), vr = dyadic(N.n2 + 1, N.l2);
+        Box3 B;
+        inclusion_shared(SQ, tid, vf, tl, tr, ul, ur, vl, vr, B);
+        bool inside = true, narrow = true;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const long long lo = f64_ord(B.lo[x]), hi = f64_ord(B.hi[x]);
+          const long long ep = SQ.ep[x][tid], en = SQ.en[x][tid];
+          miss |= (lo > ep) | (hi < en);
+          inside &= (lo >= en) & (hi <= ep);
+          narrow &= dbits(__dsub_rn(B.hi[x], B.lo[x])) < delta_bits;
+        }
+        // zero-TOI rule: an interval starting at t = 0 is always split
+        accept = (narrow || inside) && !(A.no_zero && N.n0 == 0);
       }
       if (!miss) {
-        // zero-TOI rule: an interval starting at t = 0 is always split
-        bool accept = (narrow || inside) && !(A.no_zero && N.n0 == 0);
         int a = -1;
         if (!accept) {
-          a = split_axis(Q.K, N);
+          a = split_axis(K, N);
           if (a < 0) {
             accept = true;
             flags |= CCD_FLAG_LEVEL_CAP;
@@ -669,7 +879,7 @@ k_narrow(NarrowArgs A) {
           unit_end = true;
           break;
         }
-        int a = last_axis(Q.K, N);
+        int a = last_axis(K, N);
         if ((N.n(a) & 1) == 0) {
           N.add(a, 1);
           break;
@@ -683,7 +893,7 @@ k_narrow(NarrowArgs A) {
     //         ring every `budget` evaluations (other warps take it) ----------
     if (have && !unit_end && since >= A.budget && tail_phase) {
       Node S{0, 0, 0, 0, 0, 0};
-      const int dS = shallowest_pending(Q.K, N, depth, root_depth, S);
+      const int dS = shallowest_pending(K, N, depth, root_depth, S);
       since = 0;
       if (dS > 0) {
         const unsigned long long pos = ring_reserve(&ctl->q_tail, &ctl->q_head, 1ull, ring_cap >> 2);
@@ -730,6 +940,7 @@ k_narrow(NarrowArgs A) {
   if (n_cap) atomicAdd(&ctl->n_capped, (unsigned long long)n_cap);
   if (n_don) atomicAdd(&ctl->n_donated, (unsigned long long)n_don);
   if (n_eval_tail) atomicAdd(&ctl->n_intervals_tail, (unsigned long long)n_eval_tail);
+  if (n_eval64) atomicAdd(&ctl->n_intervals_fp64, (unsigned long long)n_eval64);
   if (lane == 0) atomicMax(&ctl->t_end, globaltimer());
 }
 
@@ -748,7 +959,7 @@ __global__ void k_prepare_queries(NarrowArgs A) {
     bool vf;
     query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
     QueryData Q;
-    setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep);
+    setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep, A.delta);
     store_record(Q, vf, A.qrec, A.rec_stride, q);
   }
 }

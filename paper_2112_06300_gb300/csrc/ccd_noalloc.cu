@@ -66,6 +66,7 @@ __global__ void k_noalloc_reset(DevCtl *ctl) {
   ctl->t_start = ctl->t_exhausted = ctl->t_end = 0;
   ctl->n_donated = 0;
   ctl->n_intervals_tail = 0;
+  ctl->n_intervals_fp64 = 0;
 }
 
 __global__ void k_noalloc_status(const DevCtl *ctl, int32_t *status) { *status = ctl->status; }
