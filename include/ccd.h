@@ -80,7 +80,11 @@ typedef struct {
                                 with min_sep = 0, intervals starting at t = 0 are
                                 always split, and the result is scaled by 0.8
                                 (decided on the device); default 0 */
-    int32_t pad_opts;
+    int32_t use_graph;       /* 1: ccd_step with a device output and ccd_step_batch
+                                capture their launch sequence into a CUDA graph on
+                                the first call and replay it while the arguments
+                                (pointers, sizes, parameters) stay the same;
+                                default 0 */
 } ccd_opts;
 
 /* Work counters of the last broad/narrow/step call (see ccd_get_status). */
@@ -187,6 +191,27 @@ int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t *ee, int64
                        double delta, double min_sep, int64_t max_iter, int32_t mode,
                        double *toi_vf, double *toi_ee, uint8_t *flags_vf, uint8_t *flags_ee,
                        double *toi_min, int32_t *status, void *stream);
+
+/*
+ * Batched step: Algorithm 1 on many independent scenes (environments) of
+ * uneven size in one launch sequence -- one sort, one sweep, one narrow-phase
+ * launch for all of them.  The scenes are concatenated: scene s owns vertices
+ * [vert_off[s], vert_off[s+1]), edges [edge_off[s], edge_off[s+1]) and faces
+ * [face_off[s], face_off[s+1]) (device int64 arrays of n_scenes + 1 entries,
+ * each starting at 0); E and F hold global vertex ids, and every edge or face
+ * uses vertices of its own scene.  Pairs never cross scenes; each scene has
+ * its own sweep axis (largest centre variance) and its own earliest time.
+ * toi_out: device double [n_scenes], +inf for a scene without collision.
+ * Asynchronous and allocation-free once the context's buffers have grown to
+ * the sizes of a first call (it can then be captured in a CUDA graph); an
+ * overflow of the pair buffers is reported by ccd_get_status (CCD_ETRUNC).
+ * Requires the default single-precision broad phase and tiled sweep, and no
+ * zero-TOI rule.
+ */
+int ccd_step_batch(ccd_ctx *ctx, int32_t n_scenes, const int64_t *vert_off, const int64_t *edge_off,
+                   const int64_t *face_off, const double *V0, const double *V1, int64_t nV,
+                   const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
+                   double delta, double min_sep, int64_t max_iter, double *toi_out, void *stream);
 
 /* Synchronize the context's last stream and read its device status and
  * counters (stats may be NULL).  Returns the device status. */

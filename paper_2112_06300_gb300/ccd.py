@@ -32,7 +32,7 @@ class ccd_opts(ctypes.Structure):
                 ("sweep_kernel", ctypes.c_int32), ("pair_capacity", ctypes.c_int64),
                 ("queue_capacity", ctypes.c_int64), ("export_budget", ctypes.c_int32),
                 ("profile_stages", ctypes.c_int32), ("no_zero_toi", ctypes.c_int32),
-                ("pad_opts", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32)]
 
 
 class ccd_stats(ctypes.Structure):
@@ -81,6 +81,8 @@ def lib():
     L.ccd_status_str.restype = ctypes.c_char_p
     L.ccd_measure_fp64_peak.argtypes = [ctypes.c_int, ctypes.POINTER(d)]
     L.ccd_stage_times.argtypes = [P, ctypes.POINTER(d)]
+    L.ccd_step_batch.argtypes = [P, i32, P, P, P, P, P, i64, P, i64, P, i64, d, d, i64, P, P]
+    L.ccd_step_batch.restype = ctypes.c_int
     L.ccd_narrow_noalloc.argtypes = [P, i64, P, i64, P, P, i64, P, i64, P, i64, d, d, i64, i32,
                                      P, P, P, P, P, P, P]
     L.ccd_narrow_noalloc.restype = ctypes.c_int
@@ -184,6 +186,19 @@ def ccd_step(ctx, V0, V1, E, F, delta, min_sep, max_iter, toi_min, stream=None) 
     if rc not in (CCD_OK,):
         raise CCDError(rc, "ccd_step")
     return rc
+
+
+def ccd_step_batch(ctx, vert_off, edge_off, face_off, V0, V1, E, F, delta, min_sep, max_iter, toi_out,
+                   stream=None) -> None:
+    """Batched step; offsets are CUDA int64 tensors of n_scenes + 1 entries,
+    toi_out a CUDA float64 tensor of n_scenes entries (asynchronous)."""
+    nV, nE, nF = _mesh(V0, V1, E, F)
+    n = toi_out.shape[0]
+    assert vert_off.shape[0] == n + 1 and edge_off.shape[0] == n + 1 and face_off.shape[0] == n + 1
+    rc = lib().ccd_step_batch(ctx, n, _ptr(vert_off), _ptr(edge_off), _ptr(face_off), _ptr(V0), _ptr(V1), nV,
+                              _ptr(E), nE, _ptr(F), nF, float(delta), float(min_sep), int(max_iter), _ptr(toi_out),
+                              _stream(stream))
+    _check(rc, "ccd_step_batch")
 
 
 def ccd_get_status(ctx) -> Tuple[int, dict]:
@@ -292,6 +307,24 @@ class CCD:
                  self.opts.min_sep if min_sep is None else min_sep,
                  self.opts.max_iter if max_iter is None else max_iter, out, stream)
         return float(out[0])
+
+    def step_batch(self, scenes_list, delta=None, min_sep=None, max_iter=None, stream=None):
+        """Earliest time of every scene of a list (scenes.Scene), one batched
+        step; returns a numpy array and checks the device status."""
+        import torch
+        from . import scenes as S
+        V0, V1, E, F, vo, eo, fo = S.concat_scenes(scenes_list)
+        dev = f"cuda:{self.device}"
+        V0d, V1d, Ed, Fd = mesh_to_device(V0, V1, E, F, dev)
+        t = lambda a: torch.from_numpy(a).to(dev)
+        out = torch.empty(len(scenes_list), dtype=torch.float64, device=dev)
+        ccd_step_batch(self.ctx, t(vo), t(eo), t(fo), V0d, V1d, Ed, Fd,
+                       self.opts.delta if delta is None else delta,
+                       self.opts.min_sep if min_sep is None else min_sep,
+                       self.opts.max_iter if max_iter is None else max_iter, out, stream)
+        rc, _ = ccd_get_status(self.ctx)
+        _check(rc, "ccd_step_batch (device)")
+        return out.cpu().numpy()
 
     def status(self):
         return ccd_get_status(self.ctx)

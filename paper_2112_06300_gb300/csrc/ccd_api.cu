@@ -29,11 +29,27 @@ struct ccd_ctx {
   uint32_t *qflags = nullptr;
   unsigned long long *qiters = nullptr;
   unsigned long long *qrec = nullptr;          // query records, 24 x cap_q words
+  int *qsid = nullptr;                         // scene of each query (batched scenes)
+  // batched scenes
+  int64_t cap_bsid = 0, cap_scenes = 0;
+  int *bsid = nullptr, *saxis = nullptr;
+  float *ssum = nullptr;
   RingCell *ring = nullptr;
   unsigned long long ring_cap = 0;
   cudaStream_t last_stream = nullptr;
   int64_t last_nB = 0;
   long long n_launches = 0;
+  // CUDA graphs of ccd_step (device output) and ccd_step_batch, captured on a
+  // private stream and replayed on the caller's stream while the call's
+  // arguments stay the same
+  cudaStream_t cap_stream = nullptr;
+  bool capturing = false;
+  struct GraphEntry {
+    bool valid = false;
+    unsigned char key[256];
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+  } g_step, g_batch;
   // stage events: ev[2k] before stage k, ev[2k+1] after; ran[k] for the last call
   cudaEvent_t ev[2 * CCD_NSTAGES] = {};
   bool ran[CCD_NSTAGES] = {};
@@ -53,7 +69,7 @@ namespace {
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 inline void mark(ccd_ctx *c, int stage, bool begin, cudaStream_t s) {
-  if (!c->opts.profile_stages) return;
+  if (!c->opts.profile_stages || c->capturing) return;
   cudaEventRecord(c->ev[2 * stage + (begin ? 0 : 1)], s);
   if (!begin) c->ran[stage] = true;
 }
@@ -146,15 +162,39 @@ int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
   if (c->qflags) CK(cudaFree(c->qflags));
   if (c->qiters) CK(cudaFree(c->qiters));
   if (c->qrec) CK(cudaFree(c->qrec));
+  if (c->qsid) CK(cudaFree(c->qsid));
   c->qflags = nullptr;
   c->qiters = nullptr;
   c->qrec = nullptr;
+  c->qsid = nullptr;
   c->cap_q = 0;
   int64_t cap = std::max<int64_t>(nq, 1024);
   CK(cudaMalloc(&c->qflags, cap * sizeof(uint32_t)));
   CK(cudaMalloc(&c->qiters, cap * sizeof(unsigned long long)));
   CK(cudaMalloc(&c->qrec, cap * (24 * sizeof(unsigned long long) + 28 * sizeof(float))));
+  CK(cudaMalloc(&c->qsid, cap * sizeof(int)));
   c->cap_q = cap;
+  return CCD_OK;
+}
+
+int ensure_scenes(ccd_ctx *c, int64_t nB, int64_t n_scenes) {
+  if (nB > c->cap_bsid) {
+    if (c->bsid) CK(cudaFree(c->bsid));
+    c->bsid = nullptr;
+    c->cap_bsid = 0;
+    CK(cudaMalloc(&c->bsid, std::max<int64_t>(nB, 1024) * sizeof(int)));
+    c->cap_bsid = std::max<int64_t>(nB, 1024);
+  }
+  if (n_scenes > c->cap_scenes) {
+    if (c->ssum) CK(cudaFree(c->ssum));
+    if (c->saxis) CK(cudaFree(c->saxis));
+    c->ssum = nullptr;
+    c->saxis = nullptr;
+    c->cap_scenes = 0;
+    CK(cudaMalloc(&c->ssum, 6 * n_scenes * sizeof(float)));
+    CK(cudaMalloc(&c->saxis, n_scenes * sizeof(int)));
+    c->cap_scenes = n_scenes;
+  }
   return CCD_OK;
 }
 
@@ -181,12 +221,21 @@ bool mesh_args_ok(const double *V0, const double *V1, int64_t nV, const int32_t 
 
 // Launch sequence of the broad phase.  Outputs go to vf_out/ee_out (counts in
 // ctl->n_vf / n_ee, unclamped).
+struct SceneSpec {
+  int n;                            // number of scenes (0: one scene, no offsets)
+  const int64_t *voff, *eoff, *foff;
+};
+
 int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
                  const int32_t *F, int64_t nF, int32_t *vf_out, int64_t vf_cap, int32_t *ee_out, int64_t ee_cap,
-                 cudaStream_t s) {
+                 cudaStream_t s, const SceneSpec &sc = SceneSpec{0, nullptr, nullptr, nullptr}) {
   const int64_t nB = nV + nE + nF;
   int rc = ensure_broad(c, nB);
   if (rc) return rc;
+  if (sc.n > 0) {
+    rc = ensure_scenes(c, nB, sc.n);
+    if (rc) return rc;
+  }
   c->last_nB = nB;
   k_reset_broad<<<1, 1, 0, s>>>(c->ctl);
   if (nB == 0) {
@@ -194,15 +243,37 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ECUDA;
   }
   BroadBufs B = c->bb;
+  B.n_scenes = sc.n;
+  B.voff = sc.voff;
+  B.eoff = sc.eoff;
+  B.foff = sc.foff;
+  B.bsid = c->bsid;
+  B.ssum = c->ssum;
+  B.saxis = c->saxis;
   const int nbuild = (int)cdiv(nB, kBuildThreads);
   mark(c, CCD_STAGE_BOXES, true, s);
-  k_build_boxes<<<nbuild, kBuildThreads, 0, s>>>(nV, nE, nF, V0, V1, E, F, B);
-  k_axis_select<<<1, 1024, 0, s>>>(B.partials, nbuild, nB, c->ctl);
+  if (sc.n > 0) {
+    CK(cudaMemsetAsync(c->ssum, 0, 6 * sc.n * sizeof(float), s));
+    k_build_boxes<<<nbuild, kBuildThreads, 0, s>>>(nV, nE, nF, V0, V1, E, F, B);
+    k_axis_select_scenes<<<(unsigned)cdiv(sc.n, 256), 256, 0, s>>>(B);
+  } else {
+    k_build_boxes<<<nbuild, kBuildThreads, 0, s>>>(nV, nE, nF, V0, V1, E, F, B);
+    k_axis_select<<<1, 1024, 0, s>>>(B.partials, nbuild, nB, c->ctl);
+  }
   mark(c, CCD_STAGE_BOXES, false, s);
   mark(c, CCD_STAGE_SORT, true, s);
   const int grid = (int)std::min<int64_t>(cdiv(nB, 256), (int64_t)c->sm_count * 8);
   const bool fp64 = c->opts.broad_fp64 != 0;
-  if (!fp64) {
+  int sort_passes = fp64 ? 8 : 4;
+  if (sc.n > 0) {
+    // scene in the high word of the key: one sorted run per scene
+    int bits = 32;
+    while ((1ll << (bits - 32)) < sc.n) ++bits;
+    k_make_keys_scenes<<<grid, 256, 0, s>>>(nB, B, (unsigned long long *)B.keys[0], B.vals[0]);
+    const int cur = radix_sort(B.keys, B.vals, 8, nB, B.hist, s, bits);
+    k_gather_sorted<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
+    sort_passes = (bits + 7) / 8;
+  } else if (!fp64) {
     k_make_keys<<<grid, 256, 0, s>>>(nB, B.lo32, c->ctl, (uint32_t *)B.keys[0], B.vals[0]);
     const int cur = radix_sort(B.keys, B.vals, 4, nB, B.hist, s);
     k_gather_sorted<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
@@ -216,6 +287,11 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.nB = nB;
   A.nV = nV;
   A.nE = nE;
+  A.n_scenes = sc.n;
+  A.voff = sc.voff;
+  A.eoff = sc.eoff;
+  A.foff = sc.foff;
+  A.bsid = c->bsid;
   A.s_alo = B.s_alo;
   A.s_ahi = B.s_ahi;
   A.s_oth = B.s_oth;
@@ -232,15 +308,15 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.ctl = c->ctl;
   const int sgrid = (int)std::min<int64_t>(cdiv(nB * 32, 256), (int64_t)c->sm_count * 32);
   mark(c, CCD_STAGE_SWEEP, true, s);
-  if (fp64)
+  if (fp64 && sc.n == 0)
     k_sweep64<<<sgrid, 256, 0, s>>>(A);
-  else if (c->opts.sweep_kernel == 1)
+  else if (c->opts.sweep_kernel == 1 && sc.n == 0)
     k_sweep<<<sgrid, 256, 0, s>>>(A);
   else
     k_sweep_tiled<<<(unsigned)cdiv(nB, 256), 128, 0, s>>>(A);
   mark(c, CCD_STAGE_SWEEP, false, s);
   // reset, build, axis, keys, passes x (hist, scan, scatter), gather, sweep
-  c->n_launches += 6 + 3 * (fp64 ? 8 : 4);
+  c->n_launches += 6 + 3 * sort_passes;
   CK(cudaGetLastError());
   return CCD_OK;
 }
@@ -249,7 +325,8 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
                   int counts_from_ctl, const double *V0, const double *V1, int64_t nV, const int32_t *E,
                   const int32_t *F, double delta, double min_sep, int64_t max_iter, int mode,
                   unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s,
-                  bool zero_rule_pass = false) {
+                  bool zero_rule_pass = false, int n_scenes = 0, const int64_t *voff = nullptr,
+                  unsigned long long *toi_scene = nullptr) {
   const int64_t nq = n_vf + n_ee;
   int rc = ensure_narrow(c, nq, s);
   if (rc) return rc;
@@ -284,6 +361,10 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   A.ring_mask = c->ring_cap - 1;
   A.qrec = c->qrec;
   A.rec_stride = c->cap_q;
+  A.n_scenes = n_scenes;
+  A.voff = voff;
+  A.toi_scene = toi_scene;
+  A.qsid = c->qsid;
   if (!zero_rule_pass) mark(c, CCD_STAGE_NARROW, true, s);
   // query records: one dense pass (the zero-TOI pass has min_sep = 0: redo it)
   k_prepare_queries<<<(unsigned)std::min<int64_t>(cdiv(std::max<int64_t>(nq, 1), 256), (int64_t)c->sm_count * 16),
@@ -305,6 +386,44 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Replay the graph cached for `key`, or capture `enqueue` on the private
+// stream into a new one.  Buffers must already have their sizes: nothing may
+// allocate while a capture is open.
+template <class Enqueue>
+int run_graph(ccd_ctx *c, ccd_ctx::GraphEntry &g, const void *key, size_t key_len, cudaStream_t s,
+              Enqueue enqueue) {
+  if (g.valid && std::memcmp(g.key, key, key_len) == 0) {
+    CK(cudaGraphLaunch(g.exec, s));
+    c->n_launches += g.launches;
+    return CCD_OK;
+  }
+  if (g.valid) {
+    cudaGraphExecDestroy(g.exec);
+    g.valid = false;
+  }
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  const long long before = c->n_launches;
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+  c->capturing = true;
+  const int rc = enqueue(c->cap_stream);
+  c->capturing = false;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  if (rc != CCD_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc != CCD_OK ? rc : CCD_ECUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return CCD_ECUDA;
+  std::memcpy(g.key, key, key_len);
+  g.valid = true;
+  g.launches = c->n_launches - before;
+  CK(cudaGraphLaunch(g.exec, s));
+  return CCD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -322,6 +441,7 @@ void ccd_default_opts(ccd_opts *o) {
   o->export_budget = 0;
   o->profile_stages = 0;
   o->no_zero_toi = 0;
+  o->use_graph = 0;
 }
 
 int ccd_create(ccd_ctx **out, const ccd_opts *o, int device) {
@@ -334,6 +454,7 @@ int ccd_create(ccd_ctx **out, const ccd_opts *o, int device) {
   if (opts.broad_fp64 != 0 && opts.broad_fp64 != 1) return CCD_EINVAL;
   if (opts.sweep_kernel != 0 && opts.sweep_kernel != 1) return CCD_EINVAL;
   if (opts.no_zero_toi != 0 && opts.no_zero_toi != 1) return CCD_EINVAL;
+  if (opts.use_graph != 0 && opts.use_graph != 1) return CCD_EINVAL;
   if (opts.profile_stages != 0 && opts.profile_stages != 1) return CCD_EINVAL;
   if (opts.queue_capacity < 0 || (opts.queue_capacity & (opts.queue_capacity - 1))) return CCD_EINVAL;
   int ndev = 0;
@@ -379,7 +500,14 @@ int ccd_destroy(ccd_ctx *c) {
   cudaFree(c->qflags);
   cudaFree(c->qiters);
   cudaFree(c->qrec);
+  cudaFree(c->qsid);
+  cudaFree(c->bsid);
+  cudaFree(c->ssum);
+  cudaFree(c->saxis);
   cudaFree(c->ring);
+  if (c->g_step.valid) cudaGraphExecDestroy(c->g_step.exec);
+  if (c->g_batch.valid) cudaGraphExecDestroy(c->g_batch.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->ctl);
   for (int k = 0; k < 2 * CCD_NSTAGES; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
@@ -452,30 +580,51 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
   c->last_stream = s;
   const bool host_out = !is_device_ptr(toi_min);
   int64_t want = c->opts.pair_capacity > 0 ? c->opts.pair_capacity : std::max<int64_t>(1 << 20, 8 * (nV + nE + nF));
+  auto enqueue = [&](cudaStream_t st) -> int {
+    clear_marks(c);
+    k_reset_status<<<1, 1, 0, st>>>(c->ctl);
+    int r = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, st);
+    if (r) return r;
+    k_counts_from_broad<<<1, 1, 0, st>>>(c->ctl, c->pair_cap, c->pair_cap);
+    c->n_launches += 2;
+    r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep, max_iter, 1,
+                      nullptr, nullptr, st);
+    if (r) return r;
+    if (c->opts.no_zero_toi) {
+      // second pass only when the first found t* = 0 (decided on the device)
+      r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, 0.0, max_iter, 1,
+                        nullptr, nullptr, st, true);
+      if (r) return r;
+    }
+    if (!host_out && cudaMemcpyAsync(toi_min, &c->ctl->toi_bits, sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+                         cudaSuccess)
+      return CCD_ECUDA;
+    return CCD_OK;
+  };
   for (int attempt = 0; attempt < 3; ++attempt) {
     int rc = ensure_pairs(c, want);
     if (rc) return rc;
     rc = ensure_narrow(c, 2 * c->pair_cap, s);
     if (rc) return rc;
-    clear_marks(c);
-    k_reset_status<<<1, 1, 0, s>>>(c->ctl);
-    rc = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, s);
+    rc = ensure_broad(c, nV + nE + nF);
     if (rc) return rc;
-    k_counts_from_broad<<<1, 1, 0, s>>>(c->ctl, c->pair_cap, c->pair_cap);
-    c->n_launches += 2;
-    rc = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep,
-                       max_iter, 1, nullptr, nullptr, s);
-    if (rc) return rc;
-    if (c->opts.no_zero_toi) {
-      // second pass only when the first found t* = 0 (decided on the device)
-      rc = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, 0.0, max_iter,
-                         1, nullptr, nullptr, s, true);
-      if (rc) return rc;
-    }
     if (!host_out) {
-      CK(cudaMemcpyAsync(toi_min, &c->ctl->toi_bits, sizeof(double), cudaMemcpyDeviceToDevice, s));
-      return CCD_OK;
+      if (!c->opts.use_graph) return enqueue(s);
+      struct {
+        const void *p[6];
+        int64_t n[4];
+        double d[2];
+        int64_t mi;
+      } key;
+      std::memset(&key, 0, sizeof(key));
+      key.p[0] = V0; key.p[1] = V1; key.p[2] = E; key.p[3] = F; key.p[4] = toi_min; key.p[5] = c->vf;
+      key.n[0] = nV; key.n[1] = nE; key.n[2] = nF; key.n[3] = c->pair_cap;
+      key.d[0] = delta; key.d[1] = min_sep;
+      key.mi = max_iter;
+      return run_graph(c, c->g_step, &key, sizeof(key), s, enqueue);
     }
+    rc = enqueue(s);
+    if (rc) return rc;
     struct {
       unsigned long long nvf, nee, toi;
       int status;
@@ -491,6 +640,56 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     want = (int64_t)std::max(h.nvf, h.nee) + (int64_t)(std::max(h.nvf, h.nee) / 8) + 1024;
   }
   return CCD_ETRUNC;
+}
+
+int ccd_step_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const int64_t *edge_off,
+                   const int64_t *face_off, const double *V0, const double *V1, int64_t nV, const int32_t *E,
+                   int64_t nE, const int32_t *F, int64_t nF, double delta, double min_sep, int64_t max_iter,
+                   double *toi_out, void *stream) {
+  if (!c || n_scenes < 1 || !vert_off || !edge_off || !face_off || !toi_out) return CCD_EINVAL;
+  if (!(delta >= 0) || !(min_sep >= 0) || max_iter < 0) return CCD_EINVAL;
+  if (!mesh_args_ok(V0, V1, nV, E, nE, F, nF)) return CCD_EINVAL;
+  if (c->opts.broad_fp64 != 0 || c->opts.sweep_kernel != 0 || c->opts.no_zero_toi != 0) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  clear_marks(c);
+  const int64_t nB = nV + nE + nF;
+  int rc = ensure_pairs(c, c->opts.pair_capacity > 0 ? c->opts.pair_capacity : std::max<int64_t>(1 << 20, 8 * nB));
+  if (rc) return rc;
+  rc = ensure_narrow(c, 2 * c->pair_cap, s);
+  if (rc) return rc;
+  rc = ensure_broad(c, nB);
+  if (rc) return rc;
+  rc = ensure_scenes(c, nB, n_scenes);
+  if (rc) return rc;
+  auto enqueue = [&](cudaStream_t st) -> int {
+    clear_marks(c);
+    k_reset_status<<<1, 1, 0, st>>>(c->ctl);
+    const SceneSpec sc{n_scenes, vert_off, edge_off, face_off};
+    int r = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, st, sc);
+    if (r) return r;
+    k_counts_from_broad<<<1, 1, 0, st>>>(c->ctl, c->pair_cap, c->pair_cap);
+    k_fill_u64<<<(unsigned)std::min<int64_t>(cdiv(n_scenes, 256), 1024), 256, 0, st>>>(
+        (unsigned long long *)toi_out, n_scenes, 0x7FF0000000000000ull);
+    c->n_launches += 3;
+    return launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep, max_iter,
+                         2, nullptr, nullptr, st, false, n_scenes, vert_off, (unsigned long long *)toi_out);
+  };
+  if (!c->opts.use_graph) return enqueue(s);
+  struct {
+    const void *p[9];
+    int64_t n[5];
+    double d[2];
+    int64_t mi;
+  } key;
+  std::memset(&key, 0, sizeof(key));
+  key.p[0] = V0; key.p[1] = V1; key.p[2] = E; key.p[3] = F; key.p[4] = toi_out;
+  key.p[5] = vert_off; key.p[6] = edge_off; key.p[7] = face_off; key.p[8] = c->vf;
+  key.n[0] = nV; key.n[1] = nE; key.n[2] = nF; key.n[3] = n_scenes; key.n[4] = c->pair_cap;
+  key.d[0] = delta; key.d[1] = min_sep;
+  key.mi = max_iter;
+  return run_graph(c, c->g_batch, &key, sizeof(key), s, enqueue);
 }
 
 int ccd_get_status(ccd_ctx *c, ccd_stats *st) {

@@ -68,6 +68,29 @@ k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *__restrict__ V0,
     }
     B.vid[b] = make_int4(ids[0], ids[1], ids[2], (int)b);
   }
+  if (B.n_scenes > 0) {
+    // batched scenes: the box's scene, and centre sums per scene (one atomic
+    // per warp when the warp's boxes share a scene, which is the usual case)
+    int sid = 0;
+    if (b < nB)
+      sid = b < nV ? scene_of(B.voff, B.n_scenes, b)
+                   : (b < nV + nE ? scene_of(B.eoff, B.n_scenes, b - nV) : scene_of(B.foff, B.n_scenes, b - nV - nE));
+    if (b < nB) B.bsid[b] = sid;
+    const float v[6] = {c[0], c[1], c[2], c[0] * c[0], c[1] * c[1], c[2] * c[2]};
+    const unsigned valid = __ballot_sync(0xFFFFFFFFu, b < nB);
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, b < nB ? sid : -1);
+    if (peers == 0xFFFFFFFFu && valid == 0xFFFFFFFFu) {
+      float s6[6] = {v[0], v[1], v[2], v[3], v[4], v[5]};
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+        for (int o = 16; o; o >>= 1) s6[i] += __shfl_xor_sync(0xFFFFFFFFu, s6[i], o);
+      if ((threadIdx.x & 31) == 0)
+        for (int i = 0; i < 6; ++i) atomicAdd(&B.ssum[i * B.n_scenes + sid], s6[i]);
+    } else if (b < nB) {
+      for (int i = 0; i < 6; ++i) atomicAdd(&B.ssum[i * B.n_scenes + sid], v[i]);
+    }
+    return;
+  }
   // per-block sums of centres and squared centres (axis choice only)
   float s[6] = {c[0], c[1], c[2], c[0] * c[0], c[1] * c[1], c[2] * c[2]};
 #pragma unroll
@@ -119,6 +142,33 @@ __global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, ui
   const int a = ctl->axis;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nB; i += (int64_t)gridDim.x * blockDim.x) {
     keys[i] = f32_sort_key(lo32[a * nB + i]);
+    vals[i] = (uint32_t)i;
+  }
+}
+
+// Batched scenes: axis of largest centre variance per scene.
+__global__ void k_axis_select_scenes(BroadBufs B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B.n_scenes) return;
+  const double n = (double)((B.voff[s + 1] - B.voff[s]) + (B.eoff[s + 1] - B.eoff[s]) + (B.foff[s + 1] - B.foff[s]));
+  const double inv = n > 0 ? 1.0 / n : 0.0;
+  int best = 0;
+  double bv = -1.0;
+  for (int a = 0; a < 3; ++a) {
+    const double mean = (double)B.ssum[a * B.n_scenes + s] * inv;
+    const double var = (double)B.ssum[(3 + a) * B.n_scenes + s] * inv - mean * mean;
+    if (var > bv) { bv = var; best = a; }
+  }
+  B.saxis[s] = best;
+}
+
+// Batched scenes: key = scene << 32 | ordered bits of the minimum on the
+// scene's axis, so that every scene is one contiguous, sorted run.
+__global__ void k_make_keys_scenes(int64_t nB, BroadBufs B, unsigned long long *keys, uint32_t *vals) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nB; i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = B.bsid[i];
+    const int a = B.saxis[s];
+    keys[i] = ((unsigned long long)s << 32) | f32_sort_key(B.lo32[a * nB + i]);
     vals[i] = (uint32_t)i;
   }
 }
@@ -251,11 +301,12 @@ k_radix_scatter(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
 }
 
 template <typename K>
-int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, uint32_t *hist, cudaStream_t s) {
+int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, uint32_t *hist, cudaStream_t s, int key_bits) {
   const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
   uint32_t *totals = hist + 256 * (int64_t)ntiles;
   int cur = 0;
-  for (int shift = 0; shift < (int)(8 * sizeof(K)); shift += 8) {
+  const int bits = key_bits > 0 ? key_bits : (int)(8 * sizeof(K));
+  for (int shift = 0; shift < bits; shift += 8) {
     k_radix_hist<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, ntiles);
     k_radix_scan_rows<<<256, 256, 0, s>>>(hist, ntiles, totals);
     k_radix_scatter<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
@@ -265,13 +316,14 @@ int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, uint32_t *hist, cudaS
   return cur;
 }
 
-int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s) {
+int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s,
+               int key_bits) {
   if (key_bytes == 4) {
     uint32_t *k[2] = {(uint32_t *)keys[0], (uint32_t *)keys[1]};
-    return radix_sort_t<uint32_t>(k, vals, n, hist, s);
+    return radix_sort_t<uint32_t>(k, vals, n, hist, s, key_bits);
   }
   unsigned long long *k[2] = {(unsigned long long *)keys[0], (unsigned long long *)keys[1]};
-  return radix_sort_t<unsigned long long>(k, vals, n, hist, s);
+  return radix_sort_t<unsigned long long>(k, vals, n, hist, s, key_bits);
 }
 
 __global__ void k_gather_sorted64(int64_t nB, const uint32_t *__restrict__ perm, const DevCtl *ctl, BroadBufs B) {
@@ -287,9 +339,9 @@ __global__ void k_gather_sorted64(int64_t nB, const uint32_t *__restrict__ perm,
 }
 
 __global__ void k_gather_sorted(int64_t nB, const uint32_t *__restrict__ perm, const DevCtl *ctl, BroadBufs B) {
-  const int a = ctl->axis, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nB; s += (int64_t)gridDim.x * blockDim.x) {
     int64_t b = perm[s];
+    const int a = B.n_scenes > 0 ? B.saxis[B.bsid[b]] : ctl->axis, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
     B.s_alo[s] = B.lo32[a * nB + b];
     B.s_ahi[s] = B.hi32[a * nB + b];
     B.s_oth[s] = make_float4(B.lo32[a1 * nB + b], B.hi32[a1 * nB + b], B.lo32[a2 * nB + b], B.hi32[a2 * nB + b]);
@@ -439,7 +491,6 @@ __device__ __forceinline__ void sweep_hit(const SweepArgs &A, bool hit, const in
 }
 
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_tiled(SweepArgs A) {
-  __shared__ float sh_alo[kTJ];
   __shared__ float4 sh_oth[kTJ];
   __shared__ int4 sh_vid[kTJ];
   __shared__ unsigned long long sh_end;
@@ -450,6 +501,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_tiled(SweepArgs A) {
     float4 oi[2];
     int4 vi[2];
     int ki[2];
+    // end of each box's sweep range relative to i0 (no box: empty range)
+    int endl[2] = {tid + 1, kSweepThreads + tid + 1};
     int64_t end_max = i0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -461,12 +514,19 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_tiled(SweepArgs A) {
         ahi[r] = A.s_ahi[i];
         oi[r] = A.s_oth[i];
         vi[r] = A.s_vid[i];
-        // first sorted index whose minimum exceeds ahi (binary search)
-        int64_t lo = i + 1, hi = nB;
+        // first sorted index whose minimum exceeds ahi (binary search),
+        // within the box's scene (batched scenes are contiguous runs)
+        int64_t hi = nB;
+        if (A.n_scenes > 0) {
+          const int sid = A.bsid[vi[r].w];
+          hi = A.voff[sid + 1] + A.eoff[sid + 1] + A.foff[sid + 1];
+        }
+        int64_t lo = i + 1;
         while (lo < hi) {
           const int64_t mid = (lo + hi) >> 1;
           if (A.s_alo[mid] <= ahi[r]) lo = mid + 1; else hi = mid;
         }
+        endl[r] = (int)(lo - i0);
         end_max = lo > end_max ? lo : end_max;
       }
       ki[r] = box_kind(vi[r].w, A.nV, A.nE);
@@ -482,28 +542,26 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_tiled(SweepArgs A) {
       for (int k = tid; k < kTJ; k += kSweepThreads) {
         const int64_t j = jt + k;
         if (j < nB) {
-          sh_alo[k] = A.s_alo[j];
           sh_oth[k] = A.s_oth[j];
           sh_vid[k] = A.s_vid[j];
-        } else {
-          sh_alo[k] = __int_as_float(0x7F800000);
         }
       }
       __syncthreads();
       const int cnt = (int)min((int64_t)kTJ, jend - jt);
       const int jl0 = (int)(jt - i0);      // local index of the tile's first box
-      const bool ordered = jl0 > kTI - 1;   // every j of the tile follows every i
+      // box r tests j when li_r < jl < endl_r: in one sorted scene, j < end_r
+      // is the same as min_a(j) <= max_a(i); unsigned form of the two tests
+      const unsigned span0 = (unsigned)(endl[0] - li0 - 1), span1 = (unsigned)(endl[1] - li1 - 1);
       for (int k = 0; k < cnt; k += 4) {
         unsigned bits = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float alo = sh_alo[k + u];
           const float4 oj = sh_oth[k + u];
           const int jl = jl0 + k + u;
-          const bool h0 = (alo <= ahi[0]) & (oj.x <= oi[0].y) & (oi[0].x <= oj.y) & (oj.z <= oi[0].w) &
-                          (oi[0].z <= oj.w) & (ordered | (jl > li0));
-          const bool h1 = (alo <= ahi[1]) & (oj.x <= oi[1].y) & (oi[1].x <= oj.y) & (oj.z <= oi[1].w) &
-                          (oi[1].z <= oj.w) & (ordered | (jl > li1));
+          const bool h0 = ((unsigned)(jl - li0 - 1) < span0) & (oj.x <= oi[0].y) & (oi[0].x <= oj.y) &
+                          (oj.z <= oi[0].w) & (oi[0].z <= oj.w);
+          const bool h1 = ((unsigned)(jl - li1 - 1) < span1) & (oj.x <= oi[1].y) & (oi[1].x <= oj.y) &
+                          (oj.z <= oi[1].w) & (oi[1].z <= oj.w);
           bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
         }
         if (__any_sync(0xFFFFFFFFu, bits)) {

@@ -51,7 +51,7 @@ struct NarrowArgs {
   const int32_t *E, *F;
   double delta, min_sep;
   long long max_iter;
-  int mode;                      // 0 per pair, 1 earliest only
+  int mode;                      // 0 per pair, 1 earliest only, 2 earliest per scene
   int budget;                    // intervals before a lane hands out its work
   int no_zero;                   // zero-TOI rule: intervals with t_lo = 0 are always split
   int only_if_rerun;             // return at once unless ctl->rerun is set
@@ -60,6 +60,11 @@ struct NarrowArgs {
   unsigned long long *qiters;    // [n_vf + n_ee] scratch
   RingCell *ring;
   unsigned long long ring_mask;  // capacity - 1
+  // batched scenes (mode 2): per-scene earliest time, scene of each query
+  int n_scenes;
+  const int64_t *voff;
+  unsigned long long *toi_scene; // [n_scenes] bits of each scene's t* (+inf initialised)
+  int *qsid;                     // [n_vf + n_ee] scene of each query
   unsigned long long *qrec;      // query records: 24 words then 27 floats, x rec_stride
                                  // (NULL: lanes set their queries up themselves)
   int64_t rec_stride;
@@ -97,23 +102,46 @@ struct BroadBufs {
   // FP64 form: sorted ordered-int64 extents
   long long *s_alo64, *s_ahi64;  // [nB]
   longlong2 *s_oth64;            // [2 * nB]: (lo1, hi1), (lo2, hi2)
+  // batched scenes (n_scenes = 0: one scene): scene s owns vertices
+  // [voff[s], voff[s+1]), edges [eoff[s], ...), faces [foff[s], ...)
+  int n_scenes;
+  const int64_t *voff, *eoff, *foff;   // device [n_scenes + 1], starting at 0
+  int *bsid;                     // [nB] scene of each box
+  float *ssum;                   // [6][n_scenes] centre sums per scene
+  int *saxis;                    // [n_scenes] sweep axis per scene
 };
+
+// Scene of a primitive (batched scenes): largest s with off[s] <= id.
+__device__ __forceinline__ int scene_of(const int64_t *off, int n_scenes, int64_t id) {
+  int lo = 0, hi = n_scenes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= id) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 __global__ void k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *V0, const double *V1,
                               const int32_t *E, const int32_t *F, BroadBufs B);
 __global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl);
 __global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, uint32_t *keys, uint32_t *vals);
+__global__ void k_axis_select_scenes(BroadBufs B);
+__global__ void k_make_keys_scenes(int64_t nB, BroadBufs B, unsigned long long *keys, uint32_t *vals);
 __global__ void k_make_keys64(int64_t nB, const long long *lo64, const DevCtl *ctl, unsigned long long *keys,
                               uint32_t *vals);
 // Stable LSD radix sort of (key, value) pairs, 8 bits per pass, on stream s;
 // keys[0]/vals[0] hold the input; returns the index (0 or 1) of the buffers
 // holding the sorted output.  key_bytes = 4 or 8.  Launches 3 kernels per pass.
-int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s);
+int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s,
+               int key_bits = 0);
 __global__ void k_gather_sorted(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 __global__ void k_gather_sorted64(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 
 struct SweepArgs {
   int64_t nB, nV, nE;
+  int n_scenes;                  // 0: one scene
+  const int64_t *voff, *eoff, *foff;
+  const int *bsid;
   const float *s_alo, *s_ahi;
   const float4 *s_oth;
   const long long *s_alo64, *s_ahi64;

@@ -541,6 +541,8 @@ k_narrow(NarrowArgs A) {
   float c0f[3][3], dcf[3][3], e32[3], tm[3], wn[3];
   unsigned long long K[3] = {0, 0, 0};
   bool vf = false;
+  int sid = 0;                               // scene of the lane's query (mode 2)
+  unsigned long long pf_scene = kInfBits;    // its t*, loaded one iteration ahead
   bool have = false, fresh = false, whole = false;
   bool exhausted = false;                    // warp-uniform
   int64_t q = 0;
@@ -683,11 +685,14 @@ k_narrow(NarrowArgs A) {
           const int l0 = __shfl_sync(FULL, S.l0, src), l1 = __shfl_sync(FULL, S.l1, src),
                     l2 = __shfl_sync(FULL, S.l2, src);
           const long long qv = __shfl_sync(FULL, (long long)q, src);
+          const int sidv = __shfl_sync(FULL, sid, src);
           const int vfv = __shfl_sync(FULL, (int)vf, src);
           const unsigned long long tqv = __shfl_sync(FULL, tq, src);
           const long long capv = __shfl_sync(FULL, cap_left - cnt, src);
           if (recv) {
             q = qv;
+            sid = sidv;
+            pf_scene = kInfBits;
             vf = vfv != 0;
             N = Node{s0, s1, s2, l0, l1, l2};
             depth = root_depth = N.depth();
@@ -730,6 +735,8 @@ k_narrow(NarrowArgs A) {
         setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep, A.delta);
       }
       put_shared(SQ, tid, Q);
+      sid = A.mode == 2 ? A.qsid[q] : 0;
+      pf_scene = kInfBits;   // the prefetched value belonged to the previous query
 #pragma unroll
       for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -776,6 +783,10 @@ k_narrow(NarrowArgs A) {
       pf_qnext = ld_relaxed_u64(&ctl->q_next);
     }
     if (A.mode == 1) cut = g < cut ? g : cut;
+    if (A.mode == 2) {
+      cut = pf_scene < cut ? pf_scene : cut;
+      if (have) pf_scene = ld_relaxed_u64(&A.toi_scene[sid]);
+    }
     bool node_done = true;     // false when the node was split (go to its left child)
     bool unit_end = false;
     bool evaluate = false;
@@ -864,6 +875,7 @@ k_narrow(NarrowArgs A) {
         if (accept) {
           tq = dbits(tl);
           if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);
+          if (A.mode == 2) atomicMin(&A.toi_scene[sid], tq);
         } else {
           N.down_left(a);
           depth += 1;
@@ -902,6 +914,8 @@ k_narrow(NarrowArgs A) {
           if (tq != kInfBits) {
             if (A.mode == 0)
               atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
+            else if (A.mode == 2)
+              atomicMin(&A.toi_scene[sid], tq);
             else
               atomicMin(&ctl->toi_bits, tq);
           }
@@ -924,6 +938,7 @@ k_narrow(NarrowArgs A) {
       if (tq != kInfBits) {
         if (A.mode == 0)
           atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
+        if (A.mode == 2) atomicMin(&A.toi_scene[sid], tq);
         atomicMin(&ctl->toi_bits, tq);
       }
       if (flags) atomicOr(&A.qflags[q], flags);
@@ -961,6 +976,7 @@ __global__ void k_prepare_queries(NarrowArgs A) {
     QueryData Q;
     setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep, A.delta);
     store_record(Q, vf, A.qrec, A.rec_stride, q);
+    if (A.n_scenes > 0) A.qsid[q] = scene_of(A.voff, A.n_scenes, ids[0]);
   }
 }
 

@@ -138,6 +138,10 @@ extern "C" int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t
   A.only_if_rerun = 0;
   A.qrec = nullptr;   // no record buffer: lanes set their queries up themselves
   A.rec_stride = 0;
+  A.n_scenes = 0;
+  A.voff = nullptr;
+  A.toi_scene = nullptr;
+  A.qsid = nullptr;
   A.toi_vf_bits = mode == 0 ? (unsigned long long *)toi_vf : nullptr;
   A.toi_ee_bits = mode == 0 ? (unsigned long long *)toi_ee : nullptr;
   A.qflags = (uint32_t *)(base + kCtlBytes);

@@ -264,3 +264,90 @@ def pack_queries(X0, X1, is_vf):
     ee = np.stack([2 * np.arange(len(iee)), 2 * np.arange(len(iee)) + 1], 1).astype(np.int32)
     order = np.concatenate([ivf, iee])
     return Scene(V0, V1, E, F, {"name": "standalone-queries", "n": n}), vf, ee, order
+
+
+# ---------------------------------------------------------------------------
+# Batched rigid-body environments.
+# ---------------------------------------------------------------------------
+
+def torus(nu: int, nv: int, R: float = 1.0, r: float = 0.35):
+    """Torus with nu x nv quads (2 * nu * nv triangles)."""
+    u = np.arange(nu) * 2 * np.pi / nu
+    v = np.arange(nv) * 2 * np.pi / nv
+    U, W = np.meshgrid(u, v, indexing="ij")
+    V = np.stack([(R + r * np.cos(W)) * np.cos(U), (R + r * np.cos(W)) * np.sin(U), r * np.sin(W)], -1).reshape(-1, 3)
+    i, j = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+    a = (i * nv + j).ravel()
+    b = (((i + 1) % nu) * nv + j).ravel()
+    c = (((i + 1) % nu) * nv + (j + 1) % nv).ravel()
+    d = (i * nv + (j + 1) % nv).ravel()
+    F = np.concatenate([np.stack([a, b, c], 1), np.stack([a, c, d], 1)], 0).astype(np.int32)
+    return V, F
+
+
+def _random_rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def rigid_environment(seed: int, tri_lo: float = 500, tri_hi: float = 50000, vmax: float = 0.05) -> Scene:
+    """One environment: rigid icospheres (levels 1-3) and tori added until a
+    total triangle count drawn log-uniformly from [tri_lo, tri_hi] is reached,
+    randomly placed, rotated and scaled (0.2-0.5) in a cube sized for about one
+    body diameter between neighbours, each translated by a random velocity of
+    norm <= vmax over the step."""
+    rng = np.random.default_rng(seed)
+    target = float(np.exp(rng.uniform(np.log(tri_lo), np.log(tri_hi))))
+    bodies = []
+    total = 0
+    while total < target or not bodies:
+        if rng.random() < 0.5:
+            Vb, Fb = icosphere(int(rng.integers(1, 4)))
+        else:
+            n = int(rng.integers(6, 25))
+            Vb, Fb = torus(n, max(4, n // 2))
+            Vb = Vb / 1.35
+        bodies.append((Vb, Fb))
+        total += len(Fb)
+    nb = len(bodies)
+    side = max(1.0, 1.1 * nb ** (1.0 / 3.0))
+    Vs0, Vs1, Fs = [], [], []
+    off = 0
+    for Vb, Fb in bodies:
+        Rm = _random_rotation(rng)
+        sc = rng.uniform(0.2, 0.5)
+        pos = rng.uniform(0, side, 3)
+        vel = rng.normal(size=3)
+        vel *= rng.uniform(0, vmax) / max(np.linalg.norm(vel), 1e-12)
+        P = (Vb @ Rm.T) * sc + pos
+        Vs0.append(P)
+        Vs1.append(P + vel)
+        Fs.append(Fb + off)
+        off += len(Vb)
+    V0 = np.concatenate(Vs0, 0)
+    V1 = np.concatenate(Vs1, 0)
+    F = np.concatenate(Fs, 0).astype(np.int32)
+    return Scene(V0, V1, edges_of(F), F, {"name": "rigid-environment", "seed": seed, "bodies": nb,
+                                           "triangles": len(F)})
+
+
+def concat_scenes(scs):
+    """Concatenate scenes for a batched step: vertex ids of edges and faces are
+    shifted to global ids; returns (V0, V1, E, F, vert_off, edge_off,
+    face_off) with the offsets as int64 arrays of len(scs) + 1."""
+    voff = np.zeros(len(scs) + 1, np.int64)
+    eoff = np.zeros(len(scs) + 1, np.int64)
+    foff = np.zeros(len(scs) + 1, np.int64)
+    for k, s in enumerate(scs):
+        voff[k + 1] = voff[k] + len(s.V0)
+        eoff[k + 1] = eoff[k] + len(s.E)
+        foff[k + 1] = foff[k] + len(s.F)
+    V0 = np.concatenate([s.V0 for s in scs], 0) if scs else np.zeros((0, 3))
+    V1 = np.concatenate([s.V1 for s in scs], 0) if scs else np.zeros((0, 3))
+    E = np.concatenate([s.E.astype(np.int64) + voff[k] for k, s in enumerate(scs)], 0).astype(np.int32)
+    F = np.concatenate([s.F.astype(np.int64) + voff[k] for k, s in enumerate(scs)], 0).astype(np.int32)
+    return V0, V1, E.reshape(-1, 2), F.reshape(-1, 3), voff, eoff, foff
