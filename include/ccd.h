@@ -64,9 +64,13 @@ typedef struct {
     int64_t max_iter;        /* per-query cap on processed intervals; default 1e6 */
     int32_t broad_fp64;      /* 0 (default): single-precision outward-rounded boxes
                                 then an exact FP64 filter; 1: FP64 boxes throughout */
-    int32_t sweep_kernel;    /* 0 (default): tiled sweep (a block walks the sweep
-                                ranges of 128 boxes through shared memory);
-                                1: one warp per box */
+    int32_t sweep_kernel;    /* 0 (default): strip sweep (boxes are also binned
+                                into strips along a second axis and swept per
+                                strip, each pair reported in one strip only);
+                                1: one warp per box, one sorted list (Algorithm 2
+                                as printed); 2: tiled sweep over one sorted list
+                                (a block walks the sweep ranges of 256 boxes
+                                through shared memory) */
     int64_t pair_capacity;   /* initial pair-buffer capacity used by ccd_step
                                 (0 = auto); grows on demand in synchronous calls */
     int64_t queue_capacity;  /* interval-queue slots, a power of two (0 = auto) */
@@ -85,6 +89,11 @@ typedef struct {
                                 the first call and replay it while the arguments
                                 (pointers, sizes, parameters) stay the same;
                                 default 0 */
+    int32_t pad0;
+    double strip_width;      /* strip sweep: strip width as a multiple of the mean
+                                box width on the strip axis (0 = auto: 2); more
+                                strips mean fewer comparisons but more copies of
+                                boxes that straddle strip borders */
 } ccd_opts;
 
 /* Work counters of the last broad/narrow/step call (see ccd_get_status). */
@@ -106,6 +115,8 @@ typedef struct {
     int64_t n_donated;       /* subtrees passed between lanes of one warp */
     int64_t n_intervals_tail;  /* intervals evaluated after every query was taken */
     int64_t n_intervals_fp64;  /* intervals the single-precision filter left to FP64 */
+    int64_t n_box_copies;    /* strip sweep: boxes placed in strips, counting each
+                                strip a box overlaps (n_boxes for the other sweeps) */
 } ccd_stats;
 
 /* Fill *o with the defaults. */
@@ -205,13 +216,41 @@ int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t *ee, int64
  * Asynchronous and allocation-free once the context's buffers have grown to
  * the sizes of a first call (it can then be captured in a CUDA graph); an
  * overflow of the pair buffers is reported by ccd_get_status (CCD_ETRUNC).
- * Requires the default single-precision broad phase and tiled sweep, and no
- * zero-TOI rule.
+ * Each scene has its own strip layout under the strip sweep (more than
+ * 65,536 scenes take the tiled sweep).  Requires the single-precision broad
+ * phase, the strip or tiled sweep (sweep_kernel 0 or 2), and no zero-TOI rule.
  */
 int ccd_step_batch(ccd_ctx *ctx, int32_t n_scenes, const int64_t *vert_off, const int64_t *edge_off,
                    const int64_t *face_off, const double *V0, const double *V1, int64_t nV,
                    const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
                    double delta, double min_sep, int64_t max_iter, double *toi_out, void *stream);
+
+/* Settings chosen by ccd_autotune. */
+typedef struct {
+    int32_t sweep_kernel;    /* 0 strips or 2 tiled */
+    int32_t export_budget;   /* intervals between hand-offs in the tail phase */
+    double strip_width;      /* strip width in mean box widths (strip sweep) */
+    int64_t queue_capacity;  /* interval-queue slots */
+    double broad_ms;         /* median broad-phase time with the chosen settings */
+    double narrow_ms;        /* median narrow-phase time with the chosen settings */
+    double default_ms;       /* median broad + narrow time with the previous settings */
+    int32_t n_trials;        /* settings timed */
+    int32_t pad;
+} ccd_tuning;
+
+/*
+ * Autotuner: times the broad phase with the strip sweep at strip widths of
+ * 0.5-8 mean box widths and with the tiled sweep, then the narrow phase with
+ * hand-off budgets of 16-256 intervals, each as the median of `reps` runs on
+ * this mesh, and keeps the fastest settings in the context (later calls use
+ * them; captured graphs are dropped).  The interval queue then shrinks to the
+ * smallest power of two at least 16 times the peak occupancy seen (and at
+ * least 1024 slots) unless that slows the narrow phase by more than 2%.
+ * Synchronous; not for use under stream capture.  Requires the
+ * single-precision broad phase.  On an error the previous settings stay.
+ */
+int ccd_autotune(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+                 const int32_t *F, int64_t nF, int32_t reps, ccd_tuning *out, void *stream);
 
 /* Synchronize the context's last stream and read its device status and
  * counters (stats may be NULL).  Returns the device status. */
@@ -222,7 +261,8 @@ enum { CCD_STAGE_BOXES = 0, CCD_STAGE_SORT = 1, CCD_STAGE_SWEEP = 2, CCD_STAGE_N
 
 /* Milliseconds spent in each stage by the last ccd_broad / ccd_narrow /
  * ccd_step call (CUDA events on its stream; boxes = box build and axis
- * choice, sort = keys, radix sort and gather, sweep = sweep with the exact
+ * choice, sort = keys (strip sweep: copies per strip), radix sort and
+ * gather, sweep = sweep with the exact
  * filter, narrow = narrow-phase kernel); stages the call did not run read 0.
  * Synchronizes the stream.  Returns CCD_EINVAL unless profile_stages was set. */
 int ccd_stage_times(ccd_ctx *ctx, double ms[CCD_NSTAGES]);

@@ -32,7 +32,8 @@ class ccd_opts(ctypes.Structure):
                 ("sweep_kernel", ctypes.c_int32), ("pair_capacity", ctypes.c_int64),
                 ("queue_capacity", ctypes.c_int64), ("export_budget", ctypes.c_int32),
                 ("profile_stages", ctypes.c_int32), ("no_zero_toi", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("strip_width", ctypes.c_double)]
 
 
 class ccd_stats(ctypes.Structure):
@@ -43,7 +44,18 @@ class ccd_stats(ctypes.Structure):
                 ("device_status", ctypes.c_int32), ("pad1", ctypes.c_int32),
                 ("n_launches", ctypes.c_int64), ("narrow_bulk_ns", ctypes.c_int64),
                 ("narrow_tail_ns", ctypes.c_int64), ("n_donated", ctypes.c_int64),
-                ("n_intervals_tail", ctypes.c_int64), ("n_intervals_fp64", ctypes.c_int64)]
+                ("n_intervals_tail", ctypes.c_int64), ("n_intervals_fp64", ctypes.c_int64),
+                ("n_box_copies", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
+
+
+class ccd_tuning(ctypes.Structure):
+    _fields_ = [("sweep_kernel", ctypes.c_int32), ("export_budget", ctypes.c_int32),
+                ("strip_width", ctypes.c_double), ("queue_capacity", ctypes.c_int64),
+                ("broad_ms", ctypes.c_double), ("narrow_ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double), ("n_trials", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
@@ -86,6 +98,8 @@ def lib():
     L.ccd_narrow_noalloc.argtypes = [P, i64, P, i64, P, P, i64, P, i64, P, i64, d, d, i64, i32,
                                      P, P, P, P, P, P, P]
     L.ccd_narrow_noalloc.restype = ctypes.c_int
+    L.ccd_autotune.argtypes = [P, P, P, i64, P, i64, P, i64, i32, ctypes.POINTER(ccd_tuning), P]
+    L.ccd_autotune.restype = ctypes.c_int
     for f in ("ccd_create", "ccd_destroy", "ccd_broad", "ccd_narrow", "ccd_step", "ccd_get_status",
               "ccd_measure_fp64_peak", "ccd_stage_times"):
         getattr(L, f).restype = ctypes.c_int
@@ -199,6 +213,17 @@ def ccd_step_batch(ctx, vert_off, edge_off, face_off, V0, V1, E, F, delta, min_s
                               _ptr(E), nE, _ptr(F), nF, float(delta), float(min_sep), int(max_iter), _ptr(toi_out),
                               _stream(stream))
     _check(rc, "ccd_step_batch")
+
+
+def ccd_autotune(ctx, V0, V1, E, F, reps=3, stream=None) -> dict:
+    """Run the autotuner on one mesh (synchronous); returns the chosen
+    settings and the median times."""
+    nV, nE, nF = _mesh(V0, V1, E, F)
+    out = ccd_tuning()
+    rc = lib().ccd_autotune(ctx, _ptr(V0), _ptr(V1), nV, _ptr(E), nE, _ptr(F), nF, int(reps), ctypes.byref(out),
+                            _stream(stream))
+    _check(rc, "ccd_autotune")
+    return out.as_dict()
 
 
 def ccd_get_status(ctx) -> Tuple[int, dict]:
@@ -325,6 +350,11 @@ class CCD:
         rc, _ = ccd_get_status(self.ctx)
         _check(rc, "ccd_step_batch (device)")
         return out.cpu().numpy()
+
+    def autotune(self, V0, V1, E, F, reps=3, stream=None):
+        """Pick the sweep, strip width, hand-off budget and queue capacity for
+        this mesh (kept in the context)."""
+        return ccd_autotune(self.ctx, V0, V1, E, F, reps, stream)
 
     def status(self):
         return ccd_get_status(self.ctx)

@@ -24,6 +24,9 @@ struct ccd_ctx {
   // pair buffers of ccd_step
   int64_t pair_cap = 0;
   int32_t *vf = nullptr, *ee = nullptr;
+  // single-precision candidates of the strip sweep
+  int64_t sup_cap = 0;
+  uint2 *sup = nullptr;
   // narrow-phase scratch, sized for cap_q queries
   int64_t cap_q = 0;
   uint32_t *qflags = nullptr;
@@ -34,6 +37,8 @@ struct ccd_ctx {
   int64_t cap_bsid = 0, cap_scenes = 0;
   int *bsid = nullptr, *saxis = nullptr;
   float *ssum = nullptr;
+  uint32_t *smm = nullptr;
+  StripParam *sparam_sc = nullptr;             // strip layout per scene (batched scenes)
   RingCell *ring = nullptr;
   unsigned long long ring_cap = 0;
   cudaStream_t last_stream = nullptr;
@@ -79,6 +84,9 @@ inline void clear_marks(ccd_ctx *c) {
 
 __global__ void k_reset_broad(DevCtl *c) {
   c->n_vf = c->n_ee = c->n_superset = 0;
+  c->n_copies = 0;
+  c->strip_fallback = 0;
+  c->sup_overflow = 0;
   for (int i = 0; i < 6; ++i) c->var_sum[i] = 0;
   c->axis = 0;
 }
@@ -96,10 +104,13 @@ __global__ void k_reset_status(DevCtl *c) { c->status = CCD_OK; }
 
 // Pair counts of the broad phase clamped to the buffer capacities (ccd_step:
 // the narrow phase reads them on the device, no host round trip).
+// Pairs that did not fit raise CCD_ETRUNC (the first error wins).
 __global__ void k_counts_from_broad(DevCtl *c, int64_t vf_cap, int64_t ee_cap) {
   unsigned long long a = c->n_vf, b = c->n_ee;
   c->pair_counts[0] = (long long)min(a, (unsigned long long)vf_cap);
   c->pair_counts[1] = (long long)min(b, (unsigned long long)ee_cap);
+  if (a > (unsigned long long)vf_cap || b > (unsigned long long)ee_cap || c->sup_overflow)
+    atomicCAS(&c->status, CCD_OK, CCD_ETRUNC);
 }
 
 int ensure_broad(ccd_ctx *c, int64_t nB) {
@@ -108,19 +119,27 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   c->broad_mem = nullptr;
   c->cap_boxes = 0;
   int64_t cap = std::max<int64_t>(nB, 1024);
-  int64_t ntiles = cdiv(cap, kSortTile);
+  // box copies of the strip sweep: a box lands in at most (its width / the
+  // strip width) + 2 strips, +1 for rounding, so strips two mean widths wide
+  // bound the total by 3.5 nB (typically about 1.5 nB); the buffers hold
+  // 3 nB + 4096 copies, and past that the device falls back to one strip per
+  // scene (the plain sweep)
+  const int64_t capc = 3 * cap + 4096;
+  int64_t ntiles = cdiv(capc, kSortTile);
   int64_t nbuild = cdiv(cap, kBuildThreads);
   size_t bytes = 0;
   auto take = [&](size_t n) { size_t off = bytes; bytes += (n + 255) & ~size_t(255); return off; };
   size_t o_lo32 = take(3 * cap * sizeof(float)), o_hi32 = take(3 * cap * sizeof(float));
   size_t o_lo64 = take(3 * cap * sizeof(long long)), o_hi64 = take(3 * cap * sizeof(long long));
   size_t o_vid = take(cap * sizeof(int4));
-  size_t o_k0 = take(cap * 8), o_k1 = take(cap * 8), o_v0 = take(cap * 4), o_v1 = take(cap * 4);
+  size_t o_k0 = take(capc * 8), o_k1 = take(capc * 8), o_v0 = take(capc * 4), o_v1 = take(capc * 4);
   size_t o_hist = take((256 * ntiles + 256) * 4);
-  size_t o_salo = take(cap * 4), o_sahi = take(cap * 4);
-  size_t o_soth = take(cap * sizeof(float4)), o_svid = take(cap * sizeof(int4));
-  size_t o_part = take(6 * nbuild * sizeof(float));
+  size_t o_salo = take(cap * 4), o_sahi = take(capc * 4);
+  size_t o_soth = take(capc * sizeof(float4)), o_svid = take(capc * sizeof(int4));
+  size_t o_part = take(kStatWords * nbuild * sizeof(float));
   size_t o_salo64 = take(cap * 8), o_sahi64 = take(cap * 8), o_soth64 = take(2 * cap * sizeof(longlong2));
+  size_t o_clocal = take(cap * 4), o_cblk = take((cdiv(cap, kCopyBlock) + 1) * 8);
+  size_t o_sp1 = take(sizeof(StripParam));
   char *m = nullptr;
   CK(cudaMalloc(&m, bytes));
   c->broad_mem = m;
@@ -144,6 +163,10 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   B.s_alo64 = (long long *)(m + o_salo64);
   B.s_ahi64 = (long long *)(m + o_sahi64);
   B.s_oth64 = (longlong2 *)(m + o_soth64);
+  B.cap_copies = capc;
+  B.c_local = (uint32_t *)(m + o_clocal);
+  B.c_blk = (unsigned long long *)(m + o_cblk);
+  B.sparam = (StripParam *)(m + o_sp1);
   return CCD_OK;
 }
 
@@ -188,17 +211,36 @@ int ensure_scenes(ccd_ctx *c, int64_t nB, int64_t n_scenes) {
   if (n_scenes > c->cap_scenes) {
     if (c->ssum) CK(cudaFree(c->ssum));
     if (c->saxis) CK(cudaFree(c->saxis));
+    if (c->smm) CK(cudaFree(c->smm));
+    if (c->sparam_sc) CK(cudaFree(c->sparam_sc));
     c->ssum = nullptr;
     c->saxis = nullptr;
+    c->smm = nullptr;
+    c->sparam_sc = nullptr;
     c->cap_scenes = 0;
-    CK(cudaMalloc(&c->ssum, 6 * n_scenes * sizeof(float)));
+    CK(cudaMalloc(&c->ssum, 9 * n_scenes * sizeof(float)));
     CK(cudaMalloc(&c->saxis, n_scenes * sizeof(int)));
+    CK(cudaMalloc(&c->smm, 6 * n_scenes * sizeof(uint32_t)));
+    CK(cudaMalloc(&c->sparam_sc, n_scenes * sizeof(StripParam)));
     c->cap_scenes = n_scenes;
   }
   return CCD_OK;
 }
 
+int ensure_sup(ccd_ctx *c, int64_t cap) {
+  cap = std::max<int64_t>(cap, 1 << 20);
+  if (cap <= c->sup_cap) return CCD_OK;
+  if (c->sup) CK(cudaFree(c->sup));
+  c->sup = nullptr;
+  c->sup_cap = 0;
+  CK(cudaMalloc(&c->sup, cap * sizeof(uint2)));
+  c->sup_cap = cap;
+  return CCD_OK;
+}
+
 int ensure_pairs(ccd_ctx *c, int64_t cap) {
+  int rc = ensure_sup(c, 2 * cap);
+  if (rc) return rc;
   if (cap <= c->pair_cap) return CCD_OK;
   if (c->vf) CK(cudaFree(c->vf));
   if (c->ee) CK(cudaFree(c->ee));
@@ -232,6 +274,10 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   const int64_t nB = nV + nE + nF;
   int rc = ensure_broad(c, nB);
   if (rc) return rc;
+  if (!c->capturing) {
+    rc = ensure_sup(c, std::max<int64_t>(vf_cap + ee_cap, 8 * nB));
+    if (rc) return rc;
+  }
   if (sc.n > 0) {
     rc = ensure_scenes(c, nB, sc.n);
     if (rc) return rc;
@@ -249,26 +295,49 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   B.foff = sc.foff;
   B.bsid = c->bsid;
   B.ssum = c->ssum;
+  B.smm = c->smm;
   B.saxis = c->saxis;
+  if (sc.n > 0) B.sparam = c->sparam_sc;
+  B.strip_factor = c->opts.strip_width > 0 ? (float)c->opts.strip_width : 2.0f;
+  const bool fp64 = c->opts.broad_fp64 != 0;
+  // sweep: 0 strips, 1 warp per box, 2 tiled over one sorted list
+  // (the strip keys hold 16 bits of scene index: more scenes take the tiled sweep)
+  const int sweep = fp64 ? 1 : (c->opts.sweep_kernel == 0 && sc.n > 65536 ? 2 : c->opts.sweep_kernel);
   const int nbuild = (int)cdiv(nB, kBuildThreads);
   mark(c, CCD_STAGE_BOXES, true, s);
   if (sc.n > 0) {
-    CK(cudaMemsetAsync(c->ssum, 0, 6 * sc.n * sizeof(float), s));
+    CK(cudaMemsetAsync(c->ssum, 0, 9 * sc.n * sizeof(float), s));
+    CK(cudaMemsetAsync(c->smm, 0xFF, 3 * sc.n * sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(c->smm + 3 * sc.n, 0, 3 * sc.n * sizeof(uint32_t), s));
     k_build_boxes<<<nbuild, kBuildThreads, 0, s>>>(nV, nE, nF, V0, V1, E, F, B);
     k_axis_select_scenes<<<(unsigned)cdiv(sc.n, 256), 256, 0, s>>>(B);
   } else {
     k_build_boxes<<<nbuild, kBuildThreads, 0, s>>>(nV, nE, nF, V0, V1, E, F, B);
-    k_axis_select<<<1, 1024, 0, s>>>(B.partials, nbuild, nB, c->ctl);
+    k_axis_select<<<1, 1024, 0, s>>>(B.partials, nbuild, nB, c->ctl, B.sparam, B.strip_factor);
   }
   mark(c, CCD_STAGE_BOXES, false, s);
   mark(c, CCD_STAGE_SORT, true, s);
   const int grid = (int)std::min<int64_t>(cdiv(nB, 256), (int64_t)c->sm_count * 8);
-  const bool fp64 = c->opts.broad_fp64 != 0;
   int sort_passes = fp64 ? 8 : 4;
-  if (sc.n > 0) {
+  int extra = 0;
+  int sbits = 0;   // bits of the scene index in the keys of batched scenes
+  while ((1ll << sbits) < sc.n) ++sbits;
+  const unsigned long long *s_key = nullptr;
+  if (sweep == 0) {
+    const int nblk = (int)cdiv(nB, kCopyBlock);
+    k_count_copies<<<nblk, kCopyBlock, 0, s>>>(nB, B);
+    k_scan_copies<<<1, 1024, 0, s>>>(nblk, nB, B, c->ctl);
+    k_expand_copies<<<grid, 256, 0, s>>>(nB, B, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
+    const int bits = 48 + (sc.n > 0 ? sbits : 0);
+    const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, B.hist, s, bits, &c->ctl->n_copies);
+    const int cgrid = (int)std::min<int64_t>(cdiv(B.cap_copies, 256), (int64_t)c->sm_count * 8);
+    k_gather_copies<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, (const unsigned long long *)B.keys[cur], B.vals[cur]);
+    s_key = (const unsigned long long *)B.keys[cur];
+    sort_passes = (bits + 7) / 8;
+    extra = 2;
+  } else if (sc.n > 0) {
     // scene in the high word of the key: one sorted run per scene
-    int bits = 32;
-    while ((1ll << (bits - 32)) < sc.n) ++bits;
+    const int bits = 32 + sbits;
     k_make_keys_scenes<<<grid, 256, 0, s>>>(nB, B, (unsigned long long *)B.keys[0], B.vals[0]);
     const int cur = radix_sort(B.keys, B.vals, 8, nB, B.hist, s, bits);
     k_gather_sorted<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
@@ -306,17 +375,27 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.vf_cap = vf_cap;
   A.ee_cap = ee_cap;
   A.ctl = c->ctl;
+  A.s_key = s_key;
+  A.n_dev = &c->ctl->n_copies;
+  A.sup = c->sup;
+  A.sup_cap = c->sup_cap;
   const int sgrid = (int)std::min<int64_t>(cdiv(nB * 32, 256), (int64_t)c->sm_count * 32);
   mark(c, CCD_STAGE_SWEEP, true, s);
-  if (fp64 && sc.n == 0)
+  if (fp64)
     k_sweep64<<<sgrid, 256, 0, s>>>(A);
-  else if (c->opts.sweep_kernel == 1 && sc.n == 0)
+  else if (sweep == 1)
     k_sweep<<<sgrid, 256, 0, s>>>(A);
-  else
+  else if (sweep == 2)
     k_sweep_tiled<<<(unsigned)cdiv(nB, 256), 128, 0, s>>>(A);
+  else {
+    k_sweep_strips<<<(unsigned)std::min<int64_t>(cdiv(B.cap_copies, 256), (int64_t)c->sm_count * 16), 128, 0, s>>>(A);
+    k_exact_filter<<<(unsigned)std::min<int64_t>(cdiv(c->sup_cap, 2048), (int64_t)c->sm_count * 8), 256, 0, s>>>(A);
+    extra += 1;
+  }
   mark(c, CCD_STAGE_SWEEP, false, s);
-  // reset, build, axis, keys, passes x (hist, scan, scatter), gather, sweep
-  c->n_launches += 6 + 3 * sort_passes;
+  // reset, build, axis, keys (or count, scan, expand), passes x (hist, scan,
+  // scatter), gather, sweep (and exact filter)
+  c->n_launches += 6 + extra + 3 * sort_passes;
   CK(cudaGetLastError());
   return CCD_OK;
 }
@@ -452,7 +531,7 @@ int ccd_create(ccd_ctx **out, const ccd_opts *o, int device) {
   if (o) opts = *o;
   if (!(opts.delta >= 0) || !(opts.min_sep >= 0) || opts.max_iter < 0) return CCD_EINVAL;
   if (opts.broad_fp64 != 0 && opts.broad_fp64 != 1) return CCD_EINVAL;
-  if (opts.sweep_kernel != 0 && opts.sweep_kernel != 1) return CCD_EINVAL;
+  if (opts.sweep_kernel < 0 || opts.sweep_kernel > 2 || !(opts.strip_width >= 0)) return CCD_EINVAL;
   if (opts.no_zero_toi != 0 && opts.no_zero_toi != 1) return CCD_EINVAL;
   if (opts.use_graph != 0 && opts.use_graph != 1) return CCD_EINVAL;
   if (opts.profile_stages != 0 && opts.profile_stages != 1) return CCD_EINVAL;
@@ -497,6 +576,7 @@ int ccd_destroy(ccd_ctx *c) {
   cudaFree(c->broad_mem);
   cudaFree(c->vf);
   cudaFree(c->ee);
+  cudaFree(c->sup);
   cudaFree(c->qflags);
   cudaFree(c->qiters);
   cudaFree(c->qrec);
@@ -504,6 +584,8 @@ int ccd_destroy(ccd_ctx *c) {
   cudaFree(c->bsid);
   cudaFree(c->ssum);
   cudaFree(c->saxis);
+  cudaFree(c->smm);
+  cudaFree(c->sparam_sc);
   cudaFree(c->ring);
   if (c->g_step.valid) cudaGraphExecDestroy(c->g_step.exec);
   if (c->g_batch.valid) cudaGraphExecDestroy(c->g_batch.exec);
@@ -529,11 +611,19 @@ int ccd_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const 
   c->n_launches += 1;
   int rc = launch_broad(c, V0, V1, nV, E, nE, F, nF, vf_out, vf_cap, ee_out, ee_cap, s);
   if (rc) return rc;
-  unsigned long long h[2];
+  unsigned long long h[3];
+  int ovf = 0;
   CK(cudaMemcpyAsync(h, &c->ctl->n_vf, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&ovf, &c->ctl->sup_overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *n_vf = (int64_t)h[0];
   *n_ee = (int64_t)h[1];
+  if (ovf) {
+    // the candidates did not all fit: their count bounds both lists
+    *n_vf = std::max<int64_t>(*n_vf, (int64_t)h[2]);
+    *n_ee = std::max<int64_t>(*n_ee, (int64_t)h[2]);
+    return CCD_ETRUNC;
+  }
   return ((int64_t)h[0] > vf_cap || (int64_t)h[1] > ee_cap) ? CCD_ETRUNC : CCD_OK;
 }
 
@@ -626,18 +716,21 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     rc = enqueue(s);
     if (rc) return rc;
     struct {
-      unsigned long long nvf, nee, toi;
-      int status;
+      unsigned long long nvf, nee, nsup, toi;
+      int status, ovf;
     } h;
-    CK(cudaMemcpyAsync(&h.nvf, &c->ctl->n_vf, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&h.nvf, &c->ctl->n_vf, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&h.toi, &c->ctl->toi_bits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&h.status, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&h.ovf, &c->ctl->sup_overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if ((int64_t)h.nvf <= c->pair_cap && (int64_t)h.nee <= c->pair_cap) {
+    if (!h.ovf && (int64_t)h.nvf <= c->pair_cap && (int64_t)h.nee <= c->pair_cap) {
       std::memcpy(toi_min, &h.toi, sizeof(double));
       return h.status;
     }
-    want = (int64_t)std::max(h.nvf, h.nee) + (int64_t)(std::max(h.nvf, h.nee) / 8) + 1024;
+    unsigned long long need = std::max(h.nvf, h.nee);
+    if (h.ovf) need = std::max(need, h.nsup);
+    want = (int64_t)need + (int64_t)(need / 8) + 1024;
   }
   return CCD_ETRUNC;
 }
@@ -649,7 +742,7 @@ int ccd_step_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const 
   if (!c || n_scenes < 1 || !vert_off || !edge_off || !face_off || !toi_out) return CCD_EINVAL;
   if (!(delta >= 0) || !(min_sep >= 0) || max_iter < 0) return CCD_EINVAL;
   if (!mesh_args_ok(V0, V1, nV, E, nE, F, nF)) return CCD_EINVAL;
-  if (c->opts.broad_fp64 != 0 || c->opts.sweep_kernel != 0 || c->opts.no_zero_toi != 0) return CCD_EINVAL;
+  if (c->opts.broad_fp64 != 0 || c->opts.sweep_kernel == 1 || c->opts.no_zero_toi != 0) return CCD_EINVAL;
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
@@ -692,6 +785,145 @@ int ccd_step_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const 
   return run_graph(c, c->g_batch, &key, sizeof(key), s, enqueue);
 }
 
+int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+                 const int32_t *F, int64_t nF, int32_t reps, ccd_tuning *out, void *stream) {
+  if (!c || !out || reps < 1 || c->opts.broad_fp64 != 0) return CCD_EINVAL;
+  if (!mesh_args_ok(V0, V1, nV, E, nE, F, nF)) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const ccd_opts saved = c->opts;
+  const bool graph = c->opts.use_graph != 0;
+  c->opts.use_graph = 0;
+  std::memset(out, 0, sizeof(*out));
+  // one synchronous step sizes every buffer (pairs grow to fit)
+  double t0 = 0.0;
+  int rc = ccd_step(c, V0, V1, nV, E, nE, F, nF, c->opts.delta, c->opts.min_sep, c->opts.max_iter, &t0, stream);
+  if (rc) {
+    c->opts = saved;
+    return rc;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int err = CCD_OK;
+  int trials = 0;
+  // median of `reps` timings of one phase; the broad phase leaves its pairs
+  // in the context's buffers for the narrow phase
+  auto timed = [&](bool narrow) -> double {
+    double v[16];
+    const int n = std::min(reps, 16);
+    for (int r = 0; r < n; ++r) {
+      if (narrow) {
+        k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+        k_counts_from_broad<<<1, 1, 0, s>>>(c->ctl, c->pair_cap, c->pair_cap);
+      }
+      cudaEventRecord(e0, s);
+      int r2 = narrow ? launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F,
+                                      c->opts.delta, c->opts.min_sep, c->opts.max_iter, 1, nullptr, nullptr, s)
+                      : launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, s);
+      cudaEventRecord(e1, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) r2 = CCD_ECUDA;
+      int st = CCD_OK;
+      if (cudaMemcpy(&st, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) r2 = CCD_ECUDA;
+      if (r2 || st) {
+        err = r2 ? r2 : st;
+        return 1e30;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      v[r] = ms;
+    }
+    ++trials;
+    std::sort(v, v + n);
+    return v[n / 2];
+  };
+  // 1. sweep: strips of several widths, or one sorted list
+  const double widths[] = {0.5, 1.0, 2.0, 4.0, 8.0};
+  double best_b = 1e30;
+  int best_sweep = 0;
+  double best_w = 2.0;
+  c->opts.sweep_kernel = saved.sweep_kernel;
+  c->opts.strip_width = saved.strip_width;
+  const double base_b = timed(false);
+  for (double w : widths) {
+    c->opts.sweep_kernel = 0;
+    c->opts.strip_width = w;
+    const double t = timed(false);
+    if (t < best_b) { best_b = t; best_sweep = 0; best_w = w; }
+  }
+  c->opts.sweep_kernel = 2;
+  {
+    const double t = timed(false);
+    if (t < best_b) { best_b = t; best_sweep = 2; best_w = 0.0; }
+  }
+  c->opts.sweep_kernel = best_sweep;
+  c->opts.strip_width = best_w;
+  timed(false);   // pairs of the chosen sweep for the narrow trials
+  // 2. narrow: intervals between hand-offs in the tail phase
+  const int budgets[] = {16, 32, 64, 128, 256};
+  c->opts.export_budget = saved.export_budget;
+  const double base_n = timed(true);
+  double best_n = 1e30;
+  int best_budget = 64;
+  long long peak = 0;
+  for (int b : budgets) {
+    c->opts.export_budget = b;
+    const double t = timed(true);
+    unsigned long long qp = 0;
+    cudaMemcpy(&qp, &c->ctl->queue_peak, sizeof(qp), cudaMemcpyDeviceToHost);
+    peak = std::max<long long>(peak, (long long)qp);
+    if (t < best_n) { best_n = t; best_budget = b; }
+  }
+  c->opts.export_budget = best_budget;
+  // 3. queue: the smallest power of two with 16x headroom over the peak
+  // occupancy seen (hand-offs stop at a quarter of the capacity), kept if the
+  // narrow phase is not slower by more than 2%
+  unsigned long long qcap = 1024;
+  while (qcap < 16ull * (unsigned long long)peak) qcap <<= 1;
+  if (err == CCD_OK && qcap < c->ring_cap) {
+    const unsigned long long old_cap = c->ring_cap;
+    auto regrow = [&](unsigned long long cap) -> int {
+      CK(cudaStreamSynchronize(s));
+      CK(cudaFree(c->ring));
+      c->ring = nullptr;
+      c->ring_cap = 0;
+      c->opts.queue_capacity = (int64_t)cap;
+      return ensure_narrow(c, 0, s);
+    };
+    rc = regrow(qcap);
+    if (rc) err = rc;
+    const double t = err ? 1e30 : timed(true);
+    if (t <= 1.02 * best_n) {
+      best_n = std::min(best_n, t);
+    } else if (err == CCD_OK) {
+      rc = regrow(old_cap);
+      if (rc) err = rc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // launch configurations changed: captured graphs are stale
+  if (c->g_step.valid) { cudaGraphExecDestroy(c->g_step.exec); c->g_step.valid = false; }
+  if (c->g_batch.valid) { cudaGraphExecDestroy(c->g_batch.exec); c->g_batch.valid = false; }
+  c->opts.use_graph = graph ? 1 : 0;
+  if (err) {
+    const ccd_opts keep = c->opts;
+    c->opts = saved;
+    c->opts.queue_capacity = keep.queue_capacity;   // the ring as it stands
+    return err;
+  }
+  c->opts.queue_capacity = (int64_t)c->ring_cap;
+  out->sweep_kernel = c->opts.sweep_kernel;
+  out->export_budget = c->opts.export_budget;
+  out->strip_width = c->opts.strip_width;
+  out->queue_capacity = (int64_t)c->ring_cap;
+  out->broad_ms = best_b;
+  out->narrow_ms = best_n;
+  out->default_ms = base_b + base_n;
+  out->n_trials = trials;
+  return CCD_OK;
+}
+
 int ccd_get_status(ccd_ctx *c, ccd_stats *st) {
   if (!c) return CCD_EINVAL;
   CK(cudaSetDevice(c->device));
@@ -714,6 +946,7 @@ int ccd_get_status(ccd_ctx *c, ccd_stats *st) {
     st->queue_peak = (int64_t)h.queue_peak;
     st->device_status = h.status;
     st->n_launches = c->n_launches;
+    st->n_box_copies = h.n_copies ? (int64_t)h.n_copies : c->last_nB;
     if (h.t_end > h.t_start && h.t_start) {
       const unsigned long long tx = h.t_exhausted ? h.t_exhausted : h.t_end;
       st->narrow_bulk_ns = (int64_t)(tx - h.t_start);

@@ -28,7 +28,11 @@ k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *__restrict__ V0,
               const int32_t *__restrict__ F, BroadBufs B) {
   const int64_t nB = nV + nE + nF;
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  float c[3] = {0.f, 0.f, 0.f};
+  // statistics for the axis choice and the strip layout: centre, squared
+  // centre, width, minimum and maximum per axis (neutral values for no box)
+  float c[3] = {0.f, 0.f, 0.f}, wd[3] = {0.f, 0.f, 0.f};
+  float mn[3] = {__int_as_float(0x7F800000), __int_as_float(0x7F800000), __int_as_float(0x7F800000)};
+  float mx[3] = {-__int_as_float(0x7F800000), -__int_as_float(0x7F800000), -__int_as_float(0x7F800000)};
   if (b < nB) {
     int ids[3] = {-1, -1, -1};
     int k;
@@ -65,76 +69,160 @@ k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *__restrict__ V0,
       B.lo64[a * nB + b] = f64_ord(lo);
       B.hi64[a * nB + b] = f64_ord(hi);
       c[a] = 0.5f * (lo32 + hi32);
+      wd[a] = hi32 - lo32;
+      mn[a] = lo32;
+      mx[a] = hi32;
     }
     B.vid[b] = make_int4(ids[0], ids[1], ids[2], (int)b);
   }
+  const float v[9] = {c[0], c[1], c[2], c[0] * c[0], c[1] * c[1], c[2] * c[2], wd[0], wd[1], wd[2]};
   if (B.n_scenes > 0) {
-    // batched scenes: the box's scene, and centre sums per scene (one atomic
-    // per warp when the warp's boxes share a scene, which is the usual case)
+    // batched scenes: the box's scene, and the statistics per scene (one
+    // atomic per warp and word when the warp's boxes share a scene, which is
+    // the usual case)
     int sid = 0;
     if (b < nB)
       sid = b < nV ? scene_of(B.voff, B.n_scenes, b)
                    : (b < nV + nE ? scene_of(B.eoff, B.n_scenes, b - nV) : scene_of(B.foff, B.n_scenes, b - nV - nE));
     if (b < nB) B.bsid[b] = sid;
-    const float v[6] = {c[0], c[1], c[2], c[0] * c[0], c[1] * c[1], c[2] * c[2]};
+    uint32_t kmn[3], kmx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      kmn[a] = f32_sort_key(mn[a]);
+      kmx[a] = f32_sort_key(mx[a]);
+    }
+    const int ns = B.n_scenes;
     const unsigned valid = __ballot_sync(0xFFFFFFFFu, b < nB);
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, b < nB ? sid : -1);
     if (peers == 0xFFFFFFFFu && valid == 0xFFFFFFFFu) {
-      float s6[6] = {v[0], v[1], v[2], v[3], v[4], v[5]};
+      float s9[9];
 #pragma unroll
-      for (int i = 0; i < 6; ++i)
-        for (int o = 16; o; o >>= 1) s6[i] += __shfl_xor_sync(0xFFFFFFFFu, s6[i], o);
-      if ((threadIdx.x & 31) == 0)
-        for (int i = 0; i < 6; ++i) atomicAdd(&B.ssum[i * B.n_scenes + sid], s6[i]);
+      for (int i = 0; i < 9; ++i) {
+        s9[i] = v[i];
+        for (int o = 16; o; o >>= 1) s9[i] += __shfl_xor_sync(0xFFFFFFFFu, s9[i], o);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        kmn[a] = __reduce_min_sync(0xFFFFFFFFu, kmn[a]);
+        kmx[a] = __reduce_max_sync(0xFFFFFFFFu, kmx[a]);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        for (int i = 0; i < 9; ++i) atomicAdd(&B.ssum[i * ns + sid], s9[i]);
+        for (int a = 0; a < 3; ++a) {
+          atomicMin(&B.smm[a * ns + sid], kmn[a]);
+          atomicMax(&B.smm[(3 + a) * ns + sid], kmx[a]);
+        }
+      }
     } else if (b < nB) {
-      for (int i = 0; i < 6; ++i) atomicAdd(&B.ssum[i * B.n_scenes + sid], v[i]);
+      for (int i = 0; i < 9; ++i) atomicAdd(&B.ssum[i * ns + sid], v[i]);
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&B.smm[a * ns + sid], kmn[a]);
+        atomicMax(&B.smm[(3 + a) * ns + sid], kmx[a]);
+      }
     }
     return;
   }
-  // per-block sums of centres and squared centres (axis choice only)
-  float s[6] = {c[0], c[1], c[2], c[0] * c[0], c[1] * c[1], c[2] * c[2]};
+  // per-block statistics
+  float st[kStatWords];
 #pragma unroll
-  for (int i = 0; i < 6; ++i)
-    for (int o = 16; o; o >>= 1) s[i] += __shfl_xor_sync(0xFFFFFFFFu, s[i], o);
-  __shared__ float red[kBuildThreads / 32][6];
+  for (int i = 0; i < 9; ++i) {
+    st[i] = v[i];
+    for (int o = 16; o; o >>= 1) st[i] += __shfl_xor_sync(0xFFFFFFFFu, st[i], o);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    st[9 + a] = mn[a];
+    st[12 + a] = mx[a];
+    for (int o = 16; o; o >>= 1) {
+      st[9 + a] = fminf(st[9 + a], __shfl_xor_sync(0xFFFFFFFFu, st[9 + a], o));
+      st[12 + a] = fmaxf(st[12 + a], __shfl_xor_sync(0xFFFFFFFFu, st[12 + a], o));
+    }
+  }
+  __shared__ float red[kBuildThreads / 32][kStatWords];
   int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0)
-    for (int i = 0; i < 6; ++i) red[w][i] = s[i];
+    for (int i = 0; i < kStatWords; ++i) red[w][i] = st[i];
   __syncthreads();
-  if (threadIdx.x < 6) {
-    float t = 0.f;
-    for (int j = 0; j < kBuildThreads / 32; ++j) t += red[j][threadIdx.x];
-    B.partials[6 * blockIdx.x + threadIdx.x] = t;
+  if (threadIdx.x < kStatWords) {
+    const int i = threadIdx.x;
+    float t = red[0][i];
+    for (int j = 1; j < kBuildThreads / 32; ++j)
+      t = i < 9 ? t + red[j][i] : (i < 12 ? fminf(t, red[j][i]) : fmaxf(t, red[j][i]));
+    B.partials[kStatWords * blockIdx.x + i] = t;
   }
 }
 
-__global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl) {
-  __shared__ double acc[6][32];
-  double s[6] = {0, 0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x)
-    for (int j = 0; j < 6; ++j) s[j] += (double)partials[6 * i + j];
-  for (int j = 0; j < 6; ++j)
-    for (int o = 16; o; o >>= 1) s[j] += __shfl_xor_sync(0xFFFFFFFFu, s[j], o);
+// Strip layout of one scene from its statistics: the strip axis is the axis
+// of second-largest centre variance; strips are strip_factor mean box widths
+// wide (at most kMaxStrips strips).
+__device__ StripParam make_strip_param(int a, int a1, double n, double wsum, float org, float top,
+                                       float strip_factor) {
+  StripParam p;
+  p.axes = a | (a1 << 2) | ((3 - a - a1) << 4);
+  p.org = 0.f;
+  p.inv_w = 0.f;
+  p.nstrips = 1;
+  const double range = (double)top - (double)org;
+  const double mw = n > 0 ? wsum / n : 0.0;
+  const double w = fmax((double)strip_factor * mw, range / kMaxStrips * (1.0 + 1.0 / 1024));
+  if (!(range > 0) || !(w > 0) || !isfinite(range) || !isfinite(w)) return p;
+  const float inv = (float)(1.0 / w);
+  if (!(inv > 0.f) || !isfinite(inv)) return p;
+  p.org = org;
+  p.inv_w = inv;
+  p.nstrips = (int)fmin((double)kMaxStrips, floor(range * (double)inv) + 1.0);
+  if (p.nstrips < 1) p.nstrips = 1;
+  return p;
+}
+
+__device__ __forceinline__ void pick_axes(const double var[3], int &a, int &a1) {
+  a = 0;
+  for (int k = 1; k < 3; ++k)
+    if (var[k] > var[a]) a = k;
+  a1 = a == 0 ? 1 : 0;
+  for (int k = 0; k < 3; ++k)
+    if (k != a && var[k] > var[a1]) a1 = k;
+}
+
+__global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl, StripParam *sp,
+                              float strip_factor) {
+  __shared__ double acc[kStatWords][32];
+  double s[kStatWords];
+  for (int j = 0; j < 9; ++j) s[j] = 0.0;
+  for (int j = 9; j < 12; ++j) s[j] = __int_as_float(0x7F800000);
+  for (int j = 12; j < 15; ++j) s[j] = -__int_as_float(0x7F800000);
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    for (int j = 0; j < 9; ++j) s[j] += (double)partials[kStatWords * i + j];
+    for (int j = 9; j < 12; ++j) s[j] = fmin(s[j], (double)partials[kStatWords * i + j]);
+    for (int j = 12; j < 15; ++j) s[j] = fmax(s[j], (double)partials[kStatWords * i + j]);
+  }
+  for (int j = 0; j < kStatWords; ++j)
+    for (int o = 16; o; o >>= 1) {
+      const double y = __shfl_xor_sync(0xFFFFFFFFu, s[j], o);
+      s[j] = j < 9 ? s[j] + y : (j < 12 ? fmin(s[j], y) : fmax(s[j], y));
+    }
   if ((threadIdx.x & 31) == 0)
-    for (int j = 0; j < 6; ++j) acc[j][threadIdx.x >> 5] = s[j];
+    for (int j = 0; j < kStatWords; ++j) acc[j][threadIdx.x >> 5] = s[j];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t[6];
-    for (int j = 0; j < 6; ++j) {
-      t[j] = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[j] += acc[j][w];
+    double t[kStatWords];
+    for (int j = 0; j < kStatWords; ++j) {
+      t[j] = acc[j][0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        t[j] = j < 9 ? t[j] + acc[j][w] : (j < 12 ? fmin(t[j], acc[j][w]) : fmax(t[j], acc[j][w]));
     }
     double inv = nB > 0 ? 1.0 / (double)nB : 0.0;
-    int best = 0;
-    double bv = -1.0;
+    double var[3];
     for (int a = 0; a < 3; ++a) {
       double mean = t[a] * inv;
-      double var = t[3 + a] * inv - mean * mean;
+      var[a] = t[3 + a] * inv - mean * mean;
       ctl->var_sum[a] = t[a];
       ctl->var_sum[3 + a] = t[3 + a];
-      if (var > bv) { bv = var; best = a; }
     }
-    ctl->axis = best;
+    int a, b;
+    pick_axes(var, a, b);
+    ctl->axis = a;
+    sp[0] = make_strip_param(a, b, (double)nB, t[6 + b], (float)t[9 + b], (float)t[12 + b], strip_factor);
   }
 }
 
@@ -146,20 +234,32 @@ __global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, ui
   }
 }
 
-// Batched scenes: axis of largest centre variance per scene.
+// Batched scenes: axis of largest centre variance and strip layout per scene.
+__device__ __forceinline__ float f32_from_sort_key(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
 __global__ void k_axis_select_scenes(BroadBufs B) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B.n_scenes) return;
+  const int ns = B.n_scenes;
   const double n = (double)((B.voff[s + 1] - B.voff[s]) + (B.eoff[s + 1] - B.eoff[s]) + (B.foff[s + 1] - B.foff[s]));
   const double inv = n > 0 ? 1.0 / n : 0.0;
-  int best = 0;
-  double bv = -1.0;
+  double var[3];
   for (int a = 0; a < 3; ++a) {
-    const double mean = (double)B.ssum[a * B.n_scenes + s] * inv;
-    const double var = (double)B.ssum[(3 + a) * B.n_scenes + s] * inv - mean * mean;
-    if (var > bv) { bv = var; best = a; }
+    const double mean = (double)B.ssum[a * ns + s] * inv;
+    var[a] = (double)B.ssum[(3 + a) * ns + s] * inv - mean * mean;
   }
-  B.saxis[s] = best;
+  int a, b;
+  pick_axes(var, a, b);
+  B.saxis[s] = a;
+  StripParam p;
+  if (n > 0)
+    p = make_strip_param(a, b, n, (double)B.ssum[(6 + b) * ns + s], f32_from_sort_key(B.smm[b * ns + s]),
+                         f32_from_sort_key(B.smm[(3 + b) * ns + s]), B.strip_factor);
+  else
+    p = make_strip_param(a, b, 0.0, 0.0, 0.f, 0.f, B.strip_factor);
+  B.sparam[s] = p;
 }
 
 // Batched scenes: key = scene << 32 | ordered bits of the minimum on the
@@ -188,8 +288,10 @@ __global__ void k_make_keys64(int64_t nB, const long long *lo64, const DevCtl *c
 
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const K *__restrict__ keys, int64_t n, int shift, uint32_t *hist, int ntiles) {
+k_radix_hist(const K *__restrict__ keys, int64_t n, int shift, uint32_t *hist, int ntiles,
+             const unsigned long long *n_dev) {
   __shared__ uint32_t h[256];
+  if (n_dev) n = min(n, (int64_t)*n_dev);
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -241,8 +343,10 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_scatter(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
                 uint32_t *__restrict__ vals_out, int64_t n, int shift, const uint32_t *__restrict__ offsets,
-                int ntiles, const uint32_t *__restrict__ totals) {
+                int ntiles, const uint32_t *__restrict__ totals, const unsigned long long *n_dev) {
   constexpr int kWarps = kSortThreads / 32;
+  if (n_dev) n = min(n, (int64_t)*n_dev);
+  if ((int64_t)blockIdx.x * kSortTile >= n) return;   // whole tile beyond the count (uniform)
   __shared__ uint32_t run[256];              // running position per digit
   __shared__ uint32_t wcnt[kWarps][256];     // per-warp digit counts of the round
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -301,29 +405,30 @@ k_radix_scatter(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
 }
 
 template <typename K>
-int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, uint32_t *hist, cudaStream_t s, int key_bits) {
+int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, uint32_t *hist, cudaStream_t s, int key_bits,
+                 const unsigned long long *n_dev) {
   const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
   uint32_t *totals = hist + 256 * (int64_t)ntiles;
   int cur = 0;
   const int bits = key_bits > 0 ? key_bits : (int)(8 * sizeof(K));
   for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, ntiles);
+    k_radix_hist<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, ntiles, n_dev);
     k_radix_scan_rows<<<256, 256, 0, s>>>(hist, ntiles, totals);
     k_radix_scatter<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
-                                                       hist, ntiles, totals);
+                                                       hist, ntiles, totals, n_dev);
     cur ^= 1;
   }
   return cur;
 }
 
 int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s,
-               int key_bits) {
+               int key_bits, const unsigned long long *n_dev) {
   if (key_bytes == 4) {
     uint32_t *k[2] = {(uint32_t *)keys[0], (uint32_t *)keys[1]};
-    return radix_sort_t<uint32_t>(k, vals, n, hist, s, key_bits);
+    return radix_sort_t<uint32_t>(k, vals, n, hist, s, key_bits, n_dev);
   }
   unsigned long long *k[2] = {(unsigned long long *)keys[0], (unsigned long long *)keys[1]};
-  return radix_sort_t<unsigned long long>(k, vals, n, hist, s, key_bits);
+  return radix_sort_t<unsigned long long>(k, vals, n, hist, s, key_bits, n_dev);
 }
 
 __global__ void k_gather_sorted64(int64_t nB, const uint32_t *__restrict__ perm, const DevCtl *ctl, BroadBufs B) {
@@ -346,6 +451,136 @@ __global__ void k_gather_sorted(int64_t nB, const uint32_t *__restrict__ perm, c
     B.s_ahi[s] = B.hi32[a * nB + b];
     B.s_oth[s] = make_float4(B.lo32[a1 * nB + b], B.hi32[a1 * nB + b], B.lo32[a2 * nB + b], B.hi32[a2 * nB + b]);
     B.s_vid[s] = B.vid[b];
+  }
+}
+
+// ---- strip layout: copies of boxes per strip -------------------------------
+
+__device__ __forceinline__ int box_scene(const BroadBufs &B, int64_t b) { return B.n_scenes > 0 ? B.bsid[b] : 0; }
+
+// Strips [s0, s1] of box b on its scene's strip axis.
+__device__ __forceinline__ void box_strips(const BroadBufs &B, int64_t nB, int64_t b, const StripParam &p, int &s0,
+                                           int &s1) {
+  const int a1 = (p.axes >> 2) & 3;
+  s0 = strip_of(B.lo32[a1 * nB + b], p);
+  s1 = strip_of(B.hi32[a1 * nB + b], p);
+}
+
+// Copies per box and their exclusive prefix within each block of kCopyBlock
+// boxes; the block totals go to c_blk.
+__global__ void __launch_bounds__(kCopyBlock) k_count_copies(int64_t nB, BroadBufs B) {
+  __shared__ uint32_t wsum[kCopyBlock / 32];
+  const int64_t b = (int64_t)blockIdx.x * kCopyBlock + threadIdx.x;
+  uint32_t n = 0;
+  if (b < nB) {
+    const StripParam p = B.sparam[box_scene(B, b)];
+    int s0, s1;
+    box_strips(B, nB, b, p, s0, s1);
+    n = (uint32_t)(s1 - s0 + 1);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t v = wsum[lane];
+    uint32_t z = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+      if (lane >= o) z += y;
+    }
+    wsum[lane] = z - v;
+    if (lane == 31) B.c_blk[blockIdx.x] = z;
+  }
+  __syncthreads();
+  if (b < nB) B.c_local[b] = wsum[w] + x - n;
+}
+
+// Exclusive prefix of the block totals (one block); the total number of
+// copies, or the fallback to one strip per scene when they do not fit.
+__global__ void __launch_bounds__(1024) k_scan_copies(int nblk, int64_t nB, BroadBufs B, DevCtl *ctl) {
+  __shared__ unsigned long long wsum[32];
+  __shared__ unsigned long long carry;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nblk; base += 1024) {
+    const int i = base + tid;
+    const unsigned long long v = i < nblk ? B.c_blk[i] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    unsigned long long before = carry;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    if (i < nblk) B.c_blk[i] = before + x - v;
+    __syncthreads();
+    if (tid == 1023) carry = before + x;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const bool fit = carry <= (unsigned long long)B.cap_copies;
+    ctl->strip_fallback = fit ? 0 : 1;
+    ctl->n_copies = fit ? carry : (unsigned long long)nB;
+  }
+}
+
+// Sort keys of the copies: (scene << 16 | strip) << 32 | ordered minimum on
+// the scene's sweep axis.  Under the fallback every box has one copy, in
+// strip 0 of its scene.
+__global__ void k_expand_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, unsigned long long *keys,
+                                uint32_t *vals) {
+  const bool fallback = ctl->strip_fallback != 0;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nB; b += (int64_t)gridDim.x * blockDim.x) {
+    const int sid = box_scene(B, b);
+    const StripParam p = B.sparam[sid];
+    const unsigned long long seg = B.n_scenes > 0 ? ((unsigned long long)sid << 16) : 0ull;
+    const uint32_t k = f32_sort_key(B.lo32[(p.axes & 3) * nB + b]);
+    if (fallback) {
+      keys[b] = (seg << 32) | k;
+      vals[b] = (uint32_t)b;
+      continue;
+    }
+    int s0, s1;
+    box_strips(B, nB, b, p, s0, s1);
+    const unsigned long long o = B.c_blk[b / kCopyBlock] + B.c_local[b];
+    for (int t = s0; t <= s1; ++t) {
+      keys[o + (t - s0)] = ((seg | (unsigned)t) << 32) | k;
+      vals[o + (t - s0)] = (uint32_t)b;
+    }
+  }
+}
+
+// Copies in sorted order: maximum on the sweep axis, extents on the strip
+// axis and the third axis, vertex ids and box id; bit 31 of the box id marks
+// the copy in the box's first strip (the reporting rule of the sweep).
+__global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, const unsigned long long *keys,
+                                const uint32_t *perm) {
+  const int64_t n = (int64_t)ctl->n_copies;
+  const bool fallback = ctl->strip_fallback != 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = perm[i];
+    const unsigned long long key = keys[i];
+    const int sid = B.n_scenes > 0 ? (int)(key >> 48) : 0;
+    const int strip = (int)((key >> 32) & 0xFFFFu);
+    const StripParam p = B.sparam[sid];
+    const int a = p.axes & 3, a1 = (p.axes >> 2) & 3, a2 = (p.axes >> 4) & 3;
+    const float lo1 = B.lo32[a1 * nB + b];
+    B.s_ahi[i] = B.hi32[a * nB + b];
+    B.s_oth[i] = make_float4(lo1, B.hi32[a1 * nB + b], B.lo32[a2 * nB + b], B.hi32[a2 * nB + b]);
+    const bool first = fallback || strip == strip_of(lo1, p);
+    const int4 v = B.vid[b];
+    B.s_vid[i] = make_int4(v.x, v.y, v.z, (int)((uint32_t)b | (first ? 0x80000000u : 0u)));
   }
 }
 
@@ -574,6 +809,226 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_tiled(SweepArgs A) {
             }
           }
         }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Strip sweep (single-precision form).  Tiled like k_sweep_tiled, over the
+// sorted box copies: a copy's sweep range ends at the first copy whose key
+// exceeds (its strip segment, its maximum on the sweep axis), so it never
+// leaves its strip, and a pair is kept only when one of its two copies lies
+// in its box's first strip.  A thread owns two adjacent copies, so a warp's
+// 64 copies and their short in-strip ranges cover a narrow window of each
+// shared tile, and the warp walks only that window.  Candidates (vertex-face
+// or edge-edge, no shared vertex) collect in a per-warp shared buffer that is
+// flushed with one atomic per 256 pairs; the exact FP64 test runs afterwards
+// over the whole list (k_exact_filter).  The grid is persistent: the number
+// of copies is known only on the device.
+constexpr int kSupBuf = 256;
+
+__device__ __forceinline__ void sup_flush(const SweepArgs &A, uint2 *buf, int &cnt) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&A.ctl->n_superset, (unsigned long long)cnt);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  for (int k = lane; k < cnt; k += 32)
+    if ((int64_t)(base + k) < A.sup_cap) A.sup[base + k] = buf[k];
+  __syncwarp();
+  cnt = 0;
+}
+
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
+  __shared__ float4 sh_oth[kTJ];
+  __shared__ int4 sh_vid[kTJ];
+  __shared__ uint2 sh_sup[kSweepThreads / 32][kSupBuf];
+  __shared__ unsigned long long sh_end;
+  const int64_t n = (int64_t)*A.n_dev;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint2 *buf = sh_sup[wid];
+  int nbuf = 0;   // warp-uniform
+  for (int64_t i0 = (int64_t)blockIdx.x * kTI; i0 < n; i0 += (int64_t)gridDim.x * kTI) {
+    float ahi[2];
+    float4 oi[2];
+    int4 vi[2];
+    int ki[2];
+    bool fi[2];
+    const int li[2] = {2 * tid, 2 * tid + 1};   // local indices of the thread's two copies
+    int endl[2] = {li[0] + 1, li[1] + 1};      // no copy: empty range
+    int64_t end_max = i0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t i = i0 + li[r];
+      ahi[r] = -__int_as_float(0x7F800000);
+      oi[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      vi[r] = make_int4(-1, -1, -1, 0);
+      fi[r] = false;
+      if (i < n) {
+        ahi[r] = A.s_ahi[i];
+        oi[r] = A.s_oth[i];
+        vi[r] = A.s_vid[i];
+        fi[r] = vi[r].w < 0;
+        vi[r].w &= 0x7FFFFFFF;
+        const unsigned long long target = (A.s_key[i] & 0xFFFFFFFF00000000ull) | f32_sort_key(ahi[r]);
+        int64_t lo = i + 1, hi = n;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (A.s_key[mid] <= target) lo = mid + 1; else hi = mid;
+        }
+        endl[r] = (int)(lo - i0);
+        end_max = lo > end_max ? lo : end_max;
+      }
+      ki[r] = box_kind(vi[r].w, A.nV, A.nE);
+    }
+    // the warp's window of local j indices: [64 w + 1, largest end)
+    int wend = max(endl[0], endl[1]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wend = max(wend, __shfl_xor_sync(0xFFFFFFFFu, wend, o));
+    const int wbeg = 64 * wid + 1;
+    if (tid == 0) sh_end = (unsigned long long)i0;
+    __syncthreads();
+    atomicMax(&sh_end, (unsigned long long)end_max);
+    __syncthreads();
+    const int64_t jend = (int64_t)sh_end;
+    const unsigned span0 = (unsigned)(endl[0] - li[0] - 1), span1 = (unsigned)(endl[1] - li[1] - 1);
+    for (int64_t jt = i0 + 1; jt < jend; jt += kTJ) {
+      __syncthreads();
+      for (int k = tid; k < kTJ; k += kSweepThreads) {
+        const int64_t j = jt + k;
+        if (j < n) {
+          sh_oth[k] = A.s_oth[j];
+          sh_vid[k] = A.s_vid[j];
+        }
+      }
+      __syncthreads();
+      const int jl0 = (int)(jt - i0);
+      const int kb = max(0, wbeg - jl0) & ~3;
+      const int ke = (int)min((int64_t)min(kTJ, wend - jl0), jend - jt);
+      for (int k = kb; k < ke; k += 4) {
+        unsigned bits = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 oj = sh_oth[k + u];
+          const bool fj = sh_vid[k + u].w < 0;
+          const int jl = jl0 + k + u;
+          const bool h0 = ((unsigned)(jl - li[0] - 1) < span0) & (fi[0] | fj) & (oj.x <= oi[0].y) &
+                          (oi[0].x <= oj.y) & (oj.z <= oi[0].w) & (oi[0].z <= oj.w);
+          const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & (fi[1] | fj) & (oj.x <= oi[1].y) &
+                          (oi[1].x <= oj.y) & (oj.z <= oi[1].w) & (oi[1].z <= oj.w);
+          bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
+        }
+        if (__any_sync(0xFFFFFFFFu, bits)) {
+#pragma unroll
+          for (int bb = 0; bb < 8; ++bb) {
+            bool keep = false;
+            uint2 pr = make_uint2(0u, 0u);
+            if ((bits >> bb) & 1u) {
+              const int r = bb & 1;
+              int4 vj = sh_vid[k + (bb >> 1)];
+              vj.w &= 0x7FFFFFFF;
+              bool vf;
+              int p0, p1;
+              if (candidate(vi[r], ki[r], vj, A.nV, A.nE, vf, p0, p1)) {
+                keep = true;
+                pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)p1);
+              }
+            }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+            if (m) {
+              if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
+              if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
+              nbuf += __popc(m);
+              __syncwarp();
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (nbuf) sup_flush(A, buf, nbuf);
+}
+
+// Exact test of the strip sweep's candidates on the FP64 extents (ordered
+// int64 keys), compacted into the vertex-face and edge-edge lists with one
+// atomic per block and list.
+constexpr int kFilterThreads = 256;
+constexpr int kFilterItems = 8;
+
+__global__ void __launch_bounds__(kFilterThreads) k_exact_filter(SweepArgs A) {
+  __shared__ uint32_t wsum[2][kFilterThreads / 32];
+  __shared__ unsigned long long sbase[2];
+  const unsigned long long ns = A.ctl->n_superset;
+  const int64_t n = (int64_t)min(ns, (unsigned long long)A.sup_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && ns > (unsigned long long)A.sup_cap) {
+    A.ctl->sup_overflow = 1;
+    atomicCAS(&A.ctl->status, CCD_OK, CCD_ETRUNC);
+  }
+  const int64_t nB = A.nB;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int64_t c0 = (int64_t)blockIdx.x * kFilterThreads * kFilterItems; c0 < n;
+       c0 += (int64_t)gridDim.x * kFilterThreads * kFilterItems) {
+    uint2 pr[kFilterItems];
+    unsigned keep = 0, isvf = 0;
+#pragma unroll
+    for (int r = 0; r < kFilterItems; ++r) {
+      const int64_t k = c0 + r * kFilterThreads + tid;
+      pr[r] = make_uint2(0u, 0u);
+      if (k < n) {
+        pr[r] = A.sup[k];
+        const bool vf = (pr[r].x >> 31) != 0;
+        const int64_t a = pr[r].x & 0x7FFFFFFFu, b = pr[r].y;
+        const int64_t bi = vf ? a : A.nV + a;
+        const int64_t bj = vf ? A.nV + A.nE + b : A.nV + b;
+        bool ov = true;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const long long ilo = A.lo64[x * nB + bi], ihi = A.hi64[x * nB + bi];
+          const long long jlo = A.lo64[x * nB + bj], jhi = A.hi64[x * nB + bj];
+          ov &= (jlo <= ihi) & (ilo <= jhi);
+        }
+        keep |= (unsigned)ov << r;
+        isvf |= (unsigned)vf << r;
+      }
+    }
+    // block-wide exclusive prefix of the kept vertex-face / edge-edge counts
+    uint32_t cnt[2] = {(uint32_t)__popc(keep & isvf), (uint32_t)__popc(keep & ~isvf)};
+    uint32_t incl[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      uint32_t x = cnt[t];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      incl[t] = x;
+      if (lane == 31) wsum[t][w] = x;
+    }
+    __syncthreads();
+    uint32_t before[2] = {0u, 0u};
+    if (tid < 2) {
+      uint32_t tot = 0;
+      for (int k = 0; k < kFilterThreads / 32; ++k) tot += wsum[tid][k];
+      sbase[tid] = tot ? atomicAdd(tid == 0 ? &A.ctl->n_vf : &A.ctl->n_ee, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+      for (int k = 0; k < w; ++k) before[t] += wsum[t][k];
+    unsigned long long at[2] = {sbase[0] + before[0] + incl[0] - cnt[0], sbase[1] + before[1] + incl[1] - cnt[1]};
+#pragma unroll
+    for (int r = 0; r < kFilterItems; ++r) {
+      if ((keep >> r) & 1u) {
+        const int t = (isvf >> r) & 1u ? 0 : 1;
+        int32_t *out = t == 0 ? A.vf_out : A.ee_out;
+        const int64_t cap = t == 0 ? A.vf_cap : A.ee_cap;
+        if ((int64_t)at[t] < cap) {
+          out[2 * at[t]] = (int32_t)(pr[r].x & 0x7FFFFFFFu);
+          out[2 * at[t] + 1] = (int32_t)pr[r].y;
+        }
+        ++at[t];
       }
     }
     __syncthreads();

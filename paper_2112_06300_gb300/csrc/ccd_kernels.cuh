@@ -29,6 +29,10 @@ struct DevCtl {
   unsigned long long n_intervals_fp64;  // intervals the FP32 filter could not decide
   int rerun;                     // zero-TOI rule: 1 when the second pass must run
   int pad_;
+  // strip sweep
+  unsigned long long n_copies;   // boxes placed in strips (with repeats)
+  int strip_fallback;            // 1: the copies did not fit; one strip per scene
+  int sup_overflow;              // 1: the candidate buffer of the strip sweep overflowed
 };
 
 struct RingCell {
@@ -85,6 +89,27 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;                  // keys per thread per tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 
+// Strip sweep.  Per scene, the boxes are binned into strips of equal width
+// along a second axis (a box goes into every strip it overlaps) and the sweep
+// runs inside each strip; a pair is reported only in the strip where the
+// later of the two minima on the strip axis falls, so it is reported once.
+constexpr int kMaxStrips = 65535;
+struct StripParam {
+  float org;                     // smallest box minimum on the strip axis
+  float inv_w;                   // 1 / strip width (0: a single strip)
+  int nstrips;                   // 1 .. kMaxStrips
+  int axes;                      // sweep axis | strip axis << 2 | third axis << 4
+};
+
+// Strip of a coordinate x >= org: monotone non-decreasing in x, which is all
+// the reporting rule needs (two boxes that overlap on the strip axis share
+// the strip of the larger of their minima).
+__device__ __forceinline__ int strip_of(float x, const StripParam &p) {
+  if (p.nstrips <= 1) return 0;
+  const float t = __fmul_rn(__fsub_rn(x, p.org), p.inv_w);
+  return t >= (float)(p.nstrips - 1) ? p.nstrips - 1 : (t > 0.f ? (int)t : 0);
+}
+
 struct BroadBufs {
   // by box id
   float *lo32, *hi32;            // [3][nB]
@@ -98,7 +123,7 @@ struct BroadBufs {
   float *s_alo, *s_ahi;          // [nB]
   float4 *s_oth;                 // [nB] (lo1, hi1, lo2, hi2)
   int4 *s_vid;                   // [nB]
-  float *partials;               // [6 * nBuildBlocks]
+  float *partials;               // [kStatWords * nBuildBlocks]
   // FP64 form: sorted ordered-int64 extents
   long long *s_alo64, *s_ahi64;  // [nB]
   longlong2 *s_oth64;            // [2 * nB]: (lo1, hi1), (lo2, hi2)
@@ -107,9 +132,19 @@ struct BroadBufs {
   int n_scenes;
   const int64_t *voff, *eoff, *foff;   // device [n_scenes + 1], starting at 0
   int *bsid;                     // [nB] scene of each box
-  float *ssum;                   // [6][n_scenes] centre sums per scene
+  float *ssum;                   // [9][n_scenes] sums of centres, squared centres, widths
+  uint32_t *smm;                 // [6][n_scenes] ordered keys: min of minima, max of maxima
   int *saxis;                    // [n_scenes] sweep axis per scene
+  // strip sweep
+  StripParam *sparam;            // [max(1, n_scenes)]
+  float strip_factor;            // strip width / mean box width on the strip axis
+  int64_t cap_copies;            // capacity of the sorted arrays and sort buffers
+  uint32_t *c_local;             // [nB] offset of a box's copies within its block
+  unsigned long long *c_blk;     // [nB / kCopyBlock + 1] copies per block, then their prefix
 };
+
+constexpr int kStatWords = 15;   // per block: 3 centre sums, 3 squares, 3 widths, 3 min, 3 max
+constexpr int kCopyBlock = 1024; // boxes per block of the copy count
 
 // Scene of a primitive (batched scenes): largest s with off[s] <= id.
 __device__ __forceinline__ int scene_of(const int64_t *off, int n_scenes, int64_t id) {
@@ -123,7 +158,14 @@ __device__ __forceinline__ int scene_of(const int64_t *off, int n_scenes, int64_
 
 __global__ void k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *V0, const double *V1,
                               const int32_t *E, const int32_t *F, BroadBufs B);
-__global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl);
+__global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl, StripParam *sp,
+                              float strip_factor);
+__global__ void k_count_copies(int64_t nB, BroadBufs B);
+__global__ void k_scan_copies(int nblk, int64_t nB, BroadBufs B, DevCtl *ctl);
+__global__ void k_expand_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, unsigned long long *keys,
+                                uint32_t *vals);
+__global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, const unsigned long long *keys,
+                                const uint32_t *perm);
 __global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, uint32_t *keys, uint32_t *vals);
 __global__ void k_axis_select_scenes(BroadBufs B);
 __global__ void k_make_keys_scenes(int64_t nB, BroadBufs B, unsigned long long *keys, uint32_t *vals);
@@ -132,8 +174,10 @@ __global__ void k_make_keys64(int64_t nB, const long long *lo64, const DevCtl *c
 // Stable LSD radix sort of (key, value) pairs, 8 bits per pass, on stream s;
 // keys[0]/vals[0] hold the input; returns the index (0 or 1) of the buffers
 // holding the sorted output.  key_bytes = 4 or 8.  Launches 3 kernels per pass.
+// n_dev (optional): device count, read by the kernels, of the keys to sort
+// (at most n; grids are sized for n).
 int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s,
-               int key_bits = 0);
+               int key_bits = 0, const unsigned long long *n_dev = nullptr);
 __global__ void k_gather_sorted(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 __global__ void k_gather_sorted64(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 
@@ -151,8 +195,18 @@ struct SweepArgs {
   int32_t *vf_out, *ee_out;
   int64_t vf_cap, ee_cap;
   DevCtl *ctl;
+  // strip sweep: sorted keys (strip segment << 32 | minimum on the sweep
+  // axis) and the number of box copies, both on the device
+  const unsigned long long *s_key;
+  const unsigned long long *n_dev;
+  // strip sweep: single-precision candidates (vertex-face: bit 31 of x set),
+  // tested against the FP64 extents by k_exact_filter
+  uint2 *sup;
+  int64_t sup_cap;
 };
 __global__ void k_sweep(SweepArgs A);
+__global__ void k_sweep_strips(SweepArgs A);
+__global__ void k_exact_filter(SweepArgs A);
 __global__ void k_sweep_tiled(SweepArgs A);
 __global__ void k_sweep64(SweepArgs A);
 

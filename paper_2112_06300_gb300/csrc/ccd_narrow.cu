@@ -515,6 +515,7 @@ __device__ __forceinline__ void load_record(QueryData &Q, bool &vf, const unsign
 }  // namespace
 
 constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a warp retires
+constexpr int kRefresh = 8;            // iterations between reads of the shared values
 
 // Control flow is warp-uniform at the loop level: refill, idling and exit are
 // decided for the whole warp (ballots and broadcasts), and the per-lane work
@@ -553,10 +554,17 @@ k_narrow(NarrowArgs A) {
   unsigned flags = 0;
   long long n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0, n_eval64 = 0;
   int idle_rounds = 0;
-  unsigned long long pf_toi = kInfBits, pf_qnext = 0;   // lane 0: prefetched shared values
+  // Shared values (global t*, next query, the scene's t*) are read from L2
+  // every kRefresh iterations into a second register and used from the
+  // first, so that no iteration waits for an L2 round trip; stale values
+  // only prune less or hand work out later.
+  unsigned long long pf_toi = kInfBits, pf_qnext = 0;          // lane 0: values in use
+  unsigned long long nx_toi = kInfBits, nx_qnext = 0;          // lane 0: loads in flight
+  unsigned long long nx_scene = kInfBits;                      // per lane
+  int pf_age = 0;
   if (lane == 0) {
-    pf_toi = ld_relaxed_u64(&ctl->toi_bits);
-    pf_qnext = ld_relaxed_u64(&ctl->q_next);
+    nx_toi = ld_relaxed_u64(&ctl->toi_bits);
+    nx_qnext = ld_relaxed_u64(&ctl->q_next);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->t_start, 0ull, globaltimer());
 
@@ -692,7 +700,7 @@ k_narrow(NarrowArgs A) {
           if (recv) {
             q = qv;
             sid = sidv;
-            pf_scene = kInfBits;
+            pf_scene = nx_scene = kInfBits;
             vf = vfv != 0;
             N = Node{s0, s1, s2, l0, l1, l2};
             depth = root_depth = N.depth();
@@ -736,7 +744,7 @@ k_narrow(NarrowArgs A) {
       }
       put_shared(SQ, tid, Q);
       sid = A.mode == 2 ? A.qsid[q] : 0;
-      pf_scene = kInfBits;   // the prefetched value belonged to the previous query
+      pf_scene = nx_scene = kInfBits;   // the loaded values belonged to the previous query
 #pragma unroll
       for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -774,19 +782,25 @@ k_narrow(NarrowArgs A) {
     // ---- 4. ProcessInterval on the current node ---------------------------
     // shared values loaded during the previous iteration (stale values only
     // prune less or hand off later)
+    if (++pf_age == kRefresh) {
+      pf_age = 0;
+      if (lane == 0) {
+        pf_toi = nx_toi;
+        pf_qnext = nx_qnext;
+        nx_toi = ld_relaxed_u64(&ctl->toi_bits);
+        nx_qnext = ld_relaxed_u64(&ctl->q_next);
+      }
+      if (A.mode == 2) {
+        pf_scene = nx_scene;
+        if (have) nx_scene = ld_relaxed_u64(&A.toi_scene[sid]);
+      }
+    }
     unsigned long long cut = tq;
     const unsigned long long g = __shfl_sync(FULL, pf_toi, 0);
     // hand work out only once every query has been taken (idle lanes exist)
     const bool tail_phase = __shfl_sync(FULL, pf_qnext, 0) >= (unsigned long long)nq;
-    if (lane == 0) {
-      pf_toi = ld_relaxed_u64(&ctl->toi_bits);
-      pf_qnext = ld_relaxed_u64(&ctl->q_next);
-    }
     if (A.mode == 1) cut = g < cut ? g : cut;
-    if (A.mode == 2) {
-      cut = pf_scene < cut ? pf_scene : cut;
-      if (have) pf_scene = ld_relaxed_u64(&A.toi_scene[sid]);
-    }
+    if (A.mode == 2) cut = pf_scene < cut ? pf_scene : cut;
     bool node_done = true;     // false when the node was split (go to its left child)
     bool unit_end = false;
     bool evaluate = false;

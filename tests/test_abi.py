@@ -53,18 +53,25 @@ def test_every_declared_function_is_exported(libpath):
 
 
 def test_struct_layouts_match_binding():
+    """Size and every field offset of each struct the binding mirrors."""
     from paper_2112_06300_gb300 import ccd
     d = tempfile.mkdtemp()
     src = os.path.join(d, "s.c")
-    open(src, "w").write(
-        '#include <stdio.h>\n#include <stddef.h>\n#include "ccd.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(ccd_opts), sizeof(ccd_stats),'
-        ' offsetof(ccd_opts, profile_stages), offsetof(ccd_stats, n_launches)); return 0;}\n')
+    structs = (ccd.ccd_opts, ccd.ccd_stats, ccd.ccd_tuning)
+    lines = []
+    for st in structs:
+        lines.append(f'printf("%zu\\n", sizeof({st.__name__}));')
+        for name, _ in st._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({st.__name__}, {name}));')
+    open(src, "w").write('#include <stdio.h>\n#include <stddef.h>\n#include "ccd.h"\nint main(void){'
+                         + "".join(lines) + "return 0;}\n")
     exe = os.path.join(d, "s")
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), src, "-o", exe], check=True)
-    a, b, c, e = map(int, subprocess.run([exe], capture_output=True, text=True).stdout.split())
-    assert a == ctypes.sizeof(ccd.ccd_opts) and b == ctypes.sizeof(ccd.ccd_stats)
-    assert c == ccd.ccd_opts.profile_stages.offset and e == ccd.ccd_stats.n_launches.offset
+    vals = iter(map(int, subprocess.run([exe], capture_output=True, text=True).stdout.split()))
+    for st in structs:
+        assert next(vals) == ctypes.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert next(vals) == getattr(st, name).offset, (st.__name__, name)
 
 
 def test_status_strings_and_defaults():

@@ -25,11 +25,13 @@ def empty_scene():
                         np.zeros((0, 3), np.int32), {"name": "empty"})
 
 
-def test_batch_matches_each_scene_alone(ccd):
+@pytest.mark.parametrize("sweep,width", [(0, 0.0), (0, 0.5), (0, 1e-3), (2, 0.0)],
+                         ids=["strips", "narrow-strips", "strips-overflow", "tiled"])
+def test_batch_matches_each_scene_alone(ccd, sweep, width):
     envs = [scenes.rigid_environment(s, 500, 4000) for s in range(12)]
     batch = envs[:5] + [empty_scene()] + [scenes.folded_cloth(24, seed=3)] + envs[5:] + \
         [scenes.icosphere_on_plane(2, level=2, plane_n=9)]
-    c = ccd.CCD(0)
+    c = ccd.CCD(0, sweep_kernel=sweep, strip_width=width)
     try:
         got = c.step_batch(batch)
         again = c.step_batch(batch)

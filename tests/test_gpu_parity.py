@@ -230,15 +230,41 @@ def test_plain_fp64_form_matches_oracle(ccd, s):
         c.close()
 
 
-@pytest.mark.parametrize("s", [SCENES[0], SCENES[3], SCENES[5]], ids=["icosphere", "cloth97", "tiny"])
-def test_warp_per_box_sweep_matches_oracle(ccd, s):
-    c = ccd.CCD(0, sweep_kernel=1)
+def big_box_scene(seed=5):
+    """Small random triangles plus one triangle spanning the whole scene: its
+    box overlaps every strip."""
+    s = random_scene(seed, nv=400, nf=300, motion=0.02)
+    V0 = np.vstack([s.V0, [[-1.5, -1.5, 0.0], [1.5, -1.5, 0.1], [0.0, 1.5, -0.1]]])
+    V1 = np.vstack([s.V1, [[-1.5, -1.5, 0.0], [1.5, -1.5, 0.1], [0.0, 1.5, -0.1]]])
+    F = np.vstack([s.F, [[400, 401, 402]]]).astype(np.int32)
+    return scenes.Scene(V0, V1, scenes.edges_of(F), F, {"name": "big-box"})
+
+
+@pytest.mark.parametrize("sweep,width", [(1, 0.0), (2, 0.0), (0, 0.5), (0, 1.0), (0, 4.0), (0, 1e6), (0, 1e-3)],
+                         ids=["warp-per-box", "tiled", "strips0.5", "strips1", "strips4", "one-strip",
+                              "strips-overflow"])
+@pytest.mark.parametrize("s", [SCENES[0], SCENES[3], SCENES[5], big_box_scene()],
+                         ids=["icosphere", "cloth97", "tiny", "big-box"])
+def test_sweep_variants_match_oracle(ccd, s, sweep, width):
+    """Every sweep kernel and strip width gives the oracle's pair set and the
+    single-precision superset count (each pair reported once); a strip width
+    of 1e-3 mean widths overflows the copy buffers and takes the one-strip
+    fallback."""
+    c = ccd.CCD(0, sweep_kernel=sweep, strip_width=width)
     try:
         V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
         vf, ee = c.broad(V0, V1, E, F)
         ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
         np.testing.assert_array_equal(sorted_pairs(vf), ovf)
         np.testing.assert_array_equal(sorted_pairs(ee), oee)
+        rc, st = c.status()
+        assert rc == 0
+        v32, e32 = O.broad(s.V0, s.V1, s.E, s.F, fp32=True)
+        assert st["n_superset"] == len(v32) + len(e32)
+        if sweep != 0 or width == 1e-3:
+            assert st["n_box_copies"] == s.n_boxes
+        else:
+            assert st["n_box_copies"] >= s.n_boxes
     finally:
         c.close()
 
