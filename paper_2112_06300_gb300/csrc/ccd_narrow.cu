@@ -569,55 +569,10 @@ k_narrow(NarrowArgs A) {
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->t_start, 0ull, globaltimer());
 
   while (true) {
-    // ---- 1. refill lanes without work: exported intervals, then queries ---
-    // One lane claims, with a single CAS, as many ready ring cells as the
-    // warp has idle lanes; each idle lane then copies out its own cell.
+    // ---- 1. refill lanes without work: queries, then exported intervals --
+    // (intervals are exported only once every query has been handed out,
+    // so a warp looks at the ring only after its own claim came back empty)
     if (__any_sync(FULL, !have)) {
-      unsigned long long hd = 0, tl_ = 0;
-      if (lane == 0) {
-        hd = ld_relaxed_u64(&ctl->q_head);
-        tl_ = ld_relaxed_u64(&ctl->q_tail);
-      }
-      hd = __shfl_sync(FULL, hd, 0);
-      tl_ = __shfl_sync(FULL, tl_, 0);
-      if (hd != tl_) {
-        const unsigned m = __ballot_sync(FULL, !have);
-        unsigned long long pos0 = 0;
-        int r = 0;
-        if (lane == 0) {
-          const int want = __popc(m);
-          for (int tries = 0; tries < 8 && r == 0; ++tries) {
-            const unsigned long long h = ld_relaxed_u64(&ctl->q_head);
-            int k = 0;
-            while (k < want && ld_acquire_u64(&A.ring[(h + k) & A.ring_mask].seq) == h + k + 1) ++k;
-            if (k == 0) break;
-            if (atomicCAS(&ctl->q_head, h, h + k) == h) {
-              pos0 = h;
-              r = k;
-            }
-          }
-        }
-        pos0 = __shfl_sync(FULL, pos0, 0);
-        r = __shfl_sync(FULL, r, 0);
-        const int rank = __popc(m & lt_mask);
-        if (!have && rank < r) {
-          const unsigned long long pos = pos0 + rank;
-          RingCell *c = &A.ring[pos & A.ring_mask];
-          (void)ld_acquire_u64(&c->seq);   // pairs with the writer's release
-          const unsigned long long w0 = c->w[0], w1 = c->w[1], w2 = c->w[2];
-          const unsigned long long m54 = (1ull << 54) - 1;
-          q = c->q;
-          N.n0 = w0 & m54;
-          N.n1 = w1 & m54;
-          N.n2 = w2 & m54;
-          N.l0 = (int)(w0 >> 54);
-          N.l1 = (int)(w1 >> 54);
-          N.l2 = (int)(w2 >> 54);
-          st_release_u64(&c->seq, pos + A.ring_mask + 1);   // free for the next lap
-          have = fresh = true;
-          whole = false;
-        }
-      }
       const unsigned m = __ballot_sync(FULL, !have);
       if (m && !exhausted) {
         unsigned long long base = 0;
@@ -640,6 +595,53 @@ k_narrow(NarrowArgs A) {
                             ? (int)min((unsigned long long)__popc(m), (unsigned long long)nq - base)
                             : 0;
         if (lane == 0 && got) atomicAdd(&ctl->pending, (unsigned long long)got);
+      }
+      if (exhausted && __any_sync(FULL, !have)) {
+        unsigned long long hd = 0, tl_ = 0;
+        if (lane == 0) {
+          hd = ld_relaxed_u64(&ctl->q_head);
+          tl_ = ld_relaxed_u64(&ctl->q_tail);
+        }
+        hd = __shfl_sync(FULL, hd, 0);
+        tl_ = __shfl_sync(FULL, tl_, 0);
+        if (hd != tl_) {
+          const unsigned m = __ballot_sync(FULL, !have);
+          unsigned long long pos0 = 0;
+          int r = 0;
+          if (lane == 0) {
+            const int want = __popc(m);
+            for (int tries = 0; tries < 8 && r == 0; ++tries) {
+              const unsigned long long h = ld_relaxed_u64(&ctl->q_head);
+              int k = 0;
+              while (k < want && ld_acquire_u64(&A.ring[(h + k) & A.ring_mask].seq) == h + k + 1) ++k;
+              if (k == 0) break;
+              if (atomicCAS(&ctl->q_head, h, h + k) == h) {
+                pos0 = h;
+                r = k;
+              }
+            }
+          }
+          pos0 = __shfl_sync(FULL, pos0, 0);
+          r = __shfl_sync(FULL, r, 0);
+          const int rank = __popc(m & lt_mask);
+          if (!have && rank < r) {
+            const unsigned long long pos = pos0 + rank;
+            RingCell *c = &A.ring[pos & A.ring_mask];
+            (void)ld_acquire_u64(&c->seq);   // pairs with the writer's release
+            const unsigned long long w0 = c->w[0], w1 = c->w[1], w2 = c->w[2];
+            const unsigned long long m54 = (1ull << 54) - 1;
+            q = c->q;
+            N.n0 = w0 & m54;
+            N.n1 = w1 & m54;
+            N.n2 = w2 & m54;
+            N.l0 = (int)(w0 >> 54);
+            N.l1 = (int)(w1 >> 54);
+            N.l2 = (int)(w2 >> 54);
+            st_release_u64(&c->seq, pos + A.ring_mask + 1);   // free for the next lap
+            have = fresh = true;
+            whole = false;
+          }
+        }
       }
       // Intra-warp donation: lanes still idle (no query left, nothing ready in
       // the ring) take the shallowest pending sibling of a busy lane of their
