@@ -191,7 +191,9 @@ int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
   c->qrec = nullptr;
   c->qsid = nullptr;
   c->cap_q = 0;
-  int64_t cap = std::max<int64_t>(nq, 1024);
+  // a multiple of the narrow kernel's staged batch: its record copies stay
+  // aligned and in bounds
+  int64_t cap = (std::max<int64_t>(nq, 1024) + 31) / 32 * 32;
   CK(cudaMalloc(&c->qflags, cap * sizeof(uint32_t)));
   CK(cudaMalloc(&c->qiters, cap * sizeof(unsigned long long)));
   CK(cudaMalloc(&c->qrec, cap * (24 * sizeof(unsigned long long) + 28 * sizeof(float))));
@@ -448,7 +450,7 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   // query records: one dense pass (the zero-TOI pass has min_sep = 0: redo it)
   k_prepare_queries<<<(unsigned)std::min<int64_t>(cdiv(std::max<int64_t>(nq, 1), 256), (int64_t)c->sm_count * 16),
                       256, 0, s>>>(A);
-  k_narrow<<<c->narrow_blocks, kNarrowThreads, 0, s>>>(A);
+  k_narrow<<<c->narrow_blocks, kNarrowThreads, kNarrowDynSmem, s>>>(A);
   if (zero_rule_pass) k_nozero_finish<<<1, 1, 0, s>>>(c->ctl);
   mark(c, CCD_STAGE_NARROW, false, s);
   c->n_launches += zero_rule_pass ? 4 : 3;    // reset/prepare, records, narrow, finish
@@ -549,7 +551,13 @@ int ccd_create(ccd_ctx **out, const ccd_opts *o, int device) {
   c->opts = opts;
   c->sm_count = p.multiProcessorCount;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow, kNarrowThreads, 0) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNarrowDynSmem) !=
+      cudaSuccess) {
+    delete c;
+    return CCD_ECUDA;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow, kNarrowThreads, kNarrowDynSmem) !=
+          cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   c->narrow_blocks = per_sm * c->sm_count;

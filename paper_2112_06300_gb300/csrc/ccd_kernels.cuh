@@ -43,6 +43,11 @@ struct RingCell {
 };
 
 constexpr int kNarrowThreads = 128;
+// Claimed queries staged per warp in dynamic shared memory: two buffers of
+// kStageQ query records (24 words, 27 floats, scene id each).
+constexpr int kStageQ = 16;
+constexpr size_t kStageBytes = kStageQ * (24 * 8 + 27 * 4 + 4);
+constexpr size_t kNarrowDynSmem = (kNarrowThreads / 32) * 2 * kStageBytes;
 
 struct NarrowArgs {
   DevCtl *ctl;

@@ -512,6 +512,88 @@ __device__ __forceinline__ void load_record(QueryData &Q, bool &vf, const unsign
   }
 }
 
+// Staged queries: a warp claims kStageQ consecutive queries at a time and
+// copies their records into shared memory with cp.async one batch ahead, so
+// that neither the claim (an L2 atomic) nor the record (DRAM) is waited on
+// when lanes take new queries.
+constexpr int kRecFloats = 27;
+struct __align__(16) Stage {
+  unsigned long long w[kRecWords][kStageQ];
+  float f[kRecFloats][kStageQ];
+  int sid[kStageQ];
+};
+static_assert(sizeof(Stage) == kStageBytes, "stage layout");
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const size_t ga = __cvta_generic_to_global(gmem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(ga) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Copy the records of queries [b, b + kStageQ) into S (one commit group per
+// lane).  b is a multiple of kStageQ and the record arrays hold a multiple of
+// kStageQ entries, so every 16-byte chunk is aligned and in bounds.
+__device__ __forceinline__ void stage_copy(Stage &S, const NarrowArgs &A, unsigned long long b, int lane) {
+  constexpr int kW = kRecWords * kStageQ / 2;     // 16-byte chunks of the words
+  constexpr int kF = kRecFloats * kStageQ / 4;    // of the floats
+  constexpr int kS = kStageQ / 4;                 // of the scene ids
+  const float *r32 = (const float *)(A.qrec + kRecWords * A.rec_stride);
+  const int total = kW + kF + (A.mode == 2 ? kS : 0);
+  for (int c = lane; c < total; c += 32) {
+    if (c < kW) {
+      const int w = c / (kStageQ / 2), p = c % (kStageQ / 2);
+      cp_async16(&S.w[w][2 * p], A.qrec + w * A.rec_stride + b + 2 * p);
+    } else if (c < kW + kF) {
+      const int f = (c - kW) / (kStageQ / 4), p = (c - kW) % (kStageQ / 4);
+      cp_async16(&S.f[f][4 * p], r32 + f * A.rec_stride + b + 4 * p);
+    } else {
+      const int p = c - kW - kF;
+      cp_async16(&S.sid[4 * p], A.qsid + b + 4 * p);
+    }
+  }
+  cp_async_commit();
+}
+
+__device__ __forceinline__ void load_record_stage(QueryData &Q, bool &vf, const Stage &S, int i) {
+  int w = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) Q.c0[j][x] = __longlong_as_double((long long)S.w[w++][i]);
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) Q.dc[j][x] = __longlong_as_double((long long)S.w[w++][i]);
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const long long e = (long long)S.w[w++][i];
+    Q.ebox_p[x] = e;
+    Q.ebox_n[x] = f64_ord(-__longlong_as_double(e));
+  }
+  const unsigned long long k0 = S.w[w++][i];
+  vf = (k0 >> 63) != 0;
+  Q.K[0] = k0 & ~(1ull << 63);
+  Q.K[1] = S.w[w++][i];
+  Q.K[2] = S.w[w++][i];
+  int f = 0;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Q.c0f[j][x] = S.f[f++][i];
+      Q.dcf[j][x] = S.f[f++][i];
+    }
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    Q.e32[x] = S.f[f++][i];
+    Q.tm[x] = S.f[f++][i];
+    Q.wn[x] = S.f[f++][i];
+  }
+}
+
 }  // namespace
 
 constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a warp retires
@@ -568,13 +650,91 @@ k_narrow(NarrowArgs A) {
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->t_start, 0ull, globaltimer());
 
+  // Staged claims (with query records only): the current batch [s_base,
+  // s_base + s_n) of which s_pos are taken, the next batch (records in
+  // flight into the other buffer) and, in lane 0, the claim after it.
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+#define ST ((Stage *)dyn_smem + 2 * (threadIdx.x >> 5))
+  int sbuf = 0, s_n = 0, s_pos = 0, n_n = 0;
+  uint32_t s_base = 0, n_base = 0;           // query indices are below 2^32
+  unsigned long long c_reg = 0;
+  bool claims_done = false;                  // warp-uniform: a claim came back empty
+  const bool staged = A.qrec != nullptr;
+  if (staged) {
+    unsigned long long b0 = 0, b1 = 0;
+    if (lane == 0) {
+      b0 = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
+      b1 = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
+      c_reg = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
+    }
+    b0 = __shfl_sync(FULL, b0, 0);
+    b1 = __shfl_sync(FULL, b1, 0);
+    const unsigned long long un = (unsigned long long)nq;
+    s_base = (uint32_t)b0;
+    s_n = b0 < un ? (int)min((unsigned long long)kStageQ, un - b0) : 0;
+    n_base = (uint32_t)b1;
+    n_n = b1 < un ? (int)min((unsigned long long)kStageQ, un - b1) : 0;
+    claims_done = n_n < kStageQ;
+    if (lane == 0 && s_n + n_n > 0) atomicAdd(&ctl->pending, (unsigned long long)(s_n + n_n));
+    if (s_n > 0) stage_copy(ST[0], A, b0, lane);
+    if (n_n > 0) stage_copy(ST[1], A, b1, lane);
+    cp_async_wait_1();   // the first batch (the second may still be in flight)
+    if (n_n == 0) cp_async_wait_all();
+    __syncwarp(FULL);
+    if (claims_done && lane == 0 && ld_relaxed_u64(&ctl->t_exhausted) == 0)
+      atomicCAS(&ctl->t_exhausted, 0ull, globaltimer());
+  }
+
   while (true) {
+    int slot = -1;   // stage slot of a query taken in this iteration
     // ---- 1. refill lanes without work: queries, then exported intervals --
     // (intervals are exported only once every query has been handed out,
     // so a warp looks at the ring only after its own claim came back empty)
     if (__any_sync(FULL, !have)) {
       const unsigned m = __ballot_sync(FULL, !have);
-      if (m && !exhausted) {
+      if (m && !exhausted && staged) {
+        if (s_pos == s_n) {
+          if (n_n == 0) {
+            exhausted = true;
+          } else {
+            // start the next batch (copied one swap ago) and copy the batch
+            // claimed one swap ago into the buffer just emptied
+            cp_async_wait_all();
+            __syncwarp(FULL);
+            sbuf ^= 1;
+            s_base = n_base;
+            s_n = n_n;
+            s_pos = 0;
+            n_n = 0;
+            if (!claims_done) {
+              const unsigned long long nb = __shfl_sync(FULL, c_reg, 0);
+              const int nn = nb < (unsigned long long)nq ? (int)min((unsigned long long)kStageQ,
+                                                                    (unsigned long long)nq - nb) : 0;
+              claims_done = nn < kStageQ;
+              if (nn > 0) {
+                n_base = (uint32_t)nb;
+                n_n = nn;
+                stage_copy(ST[sbuf ^ 1], A, nb, lane);
+                if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)nn);
+              }
+              if (!claims_done && lane == 0) c_reg = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
+              if (claims_done && lane == 0 && ld_relaxed_u64(&ctl->t_exhausted) == 0)
+                atomicCAS(&ctl->t_exhausted, 0ull, globaltimer());
+            }
+          }
+        }
+        if (s_pos < s_n) {
+          const int k = min(__popc(m), s_n - s_pos);
+          const int rank = __popc(m & lt_mask);
+          if (!have && rank < k) {
+            slot = s_pos + rank;
+            q = (int64_t)s_base + slot;
+            have = fresh = whole = true;
+            N = Node{0, 0, 0, 0, 0, 0};
+          }
+          s_pos += k;
+        }
+      } else if (m && !exhausted) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&ctl->q_next, (unsigned long long)__popc(m));
         base = __shfl_sync(FULL, base, 0);
@@ -737,15 +897,19 @@ k_narrow(NarrowArgs A) {
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
       QueryData Q;
-      if (A.qrec) {
+      if (slot >= 0) {
+        load_record_stage(Q, vf, ST[sbuf], slot);
+        sid = A.mode == 2 ? ST[sbuf].sid[slot] : 0;
+      } else if (A.qrec) {
         load_record(Q, vf, A.qrec, A.rec_stride, q);
+        sid = A.mode == 2 ? A.qsid[q] : 0;
       } else {
         int ids[4];
         query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
         setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep, A.delta);
+        sid = A.mode == 2 ? A.qsid[q] : 0;
       }
       put_shared(SQ, tid, Q);
-      sid = A.mode == 2 ? A.qsid[q] : 0;
       pf_scene = nx_scene = kInfBits;   // the loaded values belonged to the previous query
 #pragma unroll
       for (int j = 0; j < 3; ++j)
@@ -974,6 +1138,7 @@ k_narrow(NarrowArgs A) {
   if (n_eval64) atomicAdd(&ctl->n_intervals_fp64, (unsigned long long)n_eval64);
   if (lane == 0) atomicMax(&ctl->t_end, globaltimer());
 }
+#undef ST
 
 // One thread per query: gather the 4 vertices at t = 0 and t = 1 and store the
 // query's set-up as a record, so that the narrow kernel's lanes set up a unit
