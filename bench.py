@@ -5,11 +5,25 @@ vertices (262,144 V, 784,385 E, 522,242 F, 1,568,771 boxes), delta = 1e-6,
 min_sep = 0, max_iter = 1e6, synthetic seeded input.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload cloth|batch|serve|precision]
 
 Prints one JSON line (rank 0).  `value` is CCD queries per second of the
 whole job: narrow-phase candidate pairs of every rank / max-over-ranks step
 time.  The reference arm times the CPU oracle (C, OpenMP) on the same scene.
 Multi-GPU: independent replicas, one per rank, no collective on the data path.
+
+The other workloads (one GPU) measure the batched, serving and precision
+forms:
+  batch      4,096 rigid environments (500-50,000 triangles, log-uniform),
+             stepped in batches sized by the memory model for a 64 GiB budget;
+             plus one batch stepped repeatedly under a captured CUDA graph.
+  serve      the same environments arriving as a Poisson stream at a given
+             rate (default 2e4 steps/s) into the serving runtime; p50/p99
+             latency and completed scenes per second.
+  precision  the folded cloth plus 1,000 rigid bodies (4.1M triangles):
+             single-precision broad phase with the exact FP64 filter against
+             the all-FP64 broad phase -- candidate counts, final-set
+             equality, time.
 """
 from __future__ import annotations
 
@@ -46,6 +60,9 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=512, help="cloth grid size")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=["cloth", "batch", "serve", "precision"], default="cloth")
+    p.add_argument("--envs", type=int, default=4096, help="batch/serve: environments")
+    p.add_argument("--rate", type=float, default=2e4, help="serve: arrivals per second")
     return p.parse_args()
 
 
@@ -156,15 +173,19 @@ FLOPS_PER_UNIT = 27 + 3 + 3 + 6 + 6
 def stage_algorithmic(st, nV, nE, nF):
     nB = nV + nE + nF
     pairs = st["n_vf"] + st["n_ee"]
+    nc = st.get("n_box_copies", nB)          # boxes placed in strips (strip sweep)
     return {
         # V0, V1 (48 B per vertex), topology (8 B per edge, 12 B per face);
         # out: float box (24 B), ordered FP64 extents (48 B), ids (16 B)
         "boxes": ("hbm", 48 * nV + 8 * nE + 12 * nF + 88 * nB),
-        # 4 passes of key + value in and out, plus the gather to sorted order
-        "sort": ("hbm", 4 * 16 * nB + 8 * nB + 44 * nB + 40 * nB),
-        # sorted boxes once (40 B), FP64 extents of box i (48 B) and of every
-        # single-precision survivor (48 B), 8 B per pair written
-        "sweep": ("hbm", 40 * nB + 48 * nB + 48 * st["n_superset"] + 8 * pairs),
+        # strip counts (8 B per box in), keys and values of the copies (12 B
+        # out), 6 passes of key + value in and out (24 B per copy), gather
+        # to sorted order (12 B key/value + 36 B box data in, 36 B out)
+        "sort": ("hbm", 8 * nB + 12 * nc + 6 * 24 * nc + 84 * nc),
+        # sorted copies once (44 B with the key), 8 B per candidate written,
+        # then the exact filter: 8 B read + 96 B of FP64 extents per
+        # candidate, 8 B per pair written
+        "sweep": ("hbm", 44 * nc + 8 * st["n_superset"] + 104 * st["n_superset"] + 8 * pairs),
         "narrow": ("alu", FLOPS_PER_INTERVAL * st["n_intervals"]
                    + FLOPS_PER_UNIT * (pairs + st["n_exported"])),
     }
@@ -251,7 +272,7 @@ def run_ours(args):
     fp64 = ccd.ccd_measure_fp64_peak(local_rank)            # GFLOP/s, DFMA chains
     dom = max(mean_stage, key=mean_stage.get)
     kind, work = algo[dom]
-    kernel = {"boxes": "k_build_boxes", "sort": "k_radix_scatter", "sweep": "k_sweep",
+    kernel = {"boxes": "k_build_boxes", "sort": "k_radix_scatter", "sweep": "k_sweep_strips",
               "narrow": "k_narrow"}[dom]
     traffic = None
     tr = NCU_TRAFFIC.get(kernel)
@@ -355,10 +376,201 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Batched, serving and precision forms (one GPU).
+# ---------------------------------------------------------------------------
+
+BUDGET = 64 << 30          # device memory budget of the batched and serving forms
+PAIRS_PER_BOX = 1.0        # candidate pairs per box budgeted (rigid environments: ~0.63)
+
+
+def environments(n):
+    from paper_2112_06300_gb300 import scenes
+    return [scenes.rigid_environment(seed) for seed in range(n)]
+
+
+def chunks_by_memory(envs, ccd):
+    """Consecutive environments per batch, as many as the memory model fits
+    in BUDGET with PAIRS_PER_BOX pairs per box (Section "Batching": the
+    candidate capacity follows from the free memory)."""
+    m = ccd.ccd_get_memory_model()
+    per_box = m["bytes_per_box"] + PAIRS_PER_BOX * m["bytes_per_pair"]
+    out, cur, boxes = [], [], 0
+    for e in envs:
+        b = e.n_boxes
+        if cur and m["bytes_fixed"] + (boxes + b) * per_box + (len(cur) + 1) * m["bytes_per_scene"] > BUDGET:
+            out.append(cur)
+            cur, boxes = [], 0
+        cur.append(e)
+        boxes += b
+    if cur:
+        out.append(cur)
+    return out
+
+
+def run_batch(args):
+    import torch
+    from oracle import oracle as O
+    from paper_2112_06300_gb300 import build, ccd, scenes
+    build.build()
+    torch.cuda.set_device(0)
+    envs = environments(args.envs)
+    groups = chunks_by_memory(envs, ccd)
+    nb_max = max(sum(e.n_boxes for e in g) for g in groups)
+    cap = int(PAIRS_PER_BOX * nb_max) + (1 << 20)
+    c = ccd.CCD(0, pair_capacity=cap)
+    dev = "cuda:0"
+    prepared = []
+    for g in groups:
+        V0, V1, E, F, vo, eo, fo = scenes.concat_scenes(g)
+        d = ccd.mesh_to_device(V0, V1, E, F, dev)
+        offs = [torch.from_numpy(a).to(dev) for a in (vo, eo, fo)]
+        prepared.append((d, offs, torch.empty(len(g), dtype=torch.float64, device=dev)))
+    stream = torch.cuda.current_stream()
+    for (d, offs, out) in prepared[:1] * max(1, args.warmup):
+        ccd.ccd_step_batch(c.ctx, *offs, *d, 1e-6, 0.0, 10 ** 6, out)
+    torch.cuda.synchronize()
+    ms_all = []
+    for _ in range(args.steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in prepared]
+        for (d, offs, out), (a, b) in zip(prepared, ev):
+            a.record(stream)
+            ccd.ccd_step_batch(c.ctx, *offs, *d, 1e-6, 0.0, 10 ** 6, out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms_all.append(sum(a.elapsed_time(b) for a, b in ev))
+        rc, st = c.status()
+        assert rc == 0, ccd.ccd_status_str(rc)
+    toi = np.concatenate([out.cpu().numpy() for (_, _, out) in prepared])
+    # parity on a seeded sample of environments
+    rng = np.random.default_rng(0)
+    sample = rng.choice(len(envs), size=min(16, len(envs)), replace=False)
+    for k in sample:
+        e = envs[k]
+        assert toi[k] == O.step(e.V0, e.V1, e.E, e.F), k
+    ms = float(np.median(ms_all))
+    # one batch of 512 environments stepped repeatedly: launch sequence vs
+    # captured graph
+    sub = envs[:512]
+    V0, V1, E, F, vo, eo, fo = scenes.concat_scenes(sub)
+    d = ccd.mesh_to_device(V0, V1, E, F, dev)
+    offs = [torch.from_numpy(a).to(dev) for a in (vo, eo, fo)]
+    out = torch.empty(len(sub), dtype=torch.float64, device=dev)
+    rep = {}
+    for g in (0, 1):
+        cg = ccd.CCD(0, use_graph=g, pair_capacity=cap)
+        for _ in range(3):
+            ccd.ccd_step_batch(cg.ctx, *offs, *d, 1e-6, 0.0, 10 ** 6, out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            ccd.ccd_step_batch(cg.ctx, *offs, *d, 1e-6, 0.0, 10 ** 6, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rep["graph" if g else "launches"] = a.elapsed_time(b) / 10
+        assert cg.status()[0] == 0
+        cg.close()
+    tri = sum(len(e.F) for e in envs)
+    boxes = sum(e.n_boxes for e in envs)
+    line = {"metric": "environments/s (batched earliest-TOI step)", "value": len(envs) / (ms * 1e-3),
+            "unit": "envs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded rigid environments)",
+            "config": {"workload": f"{len(envs)} rigid environments, 500-50,000 triangles (log-uniform), "
+                                   f"|v| <= 0.05, delta=1e-6", "triangles": tri, "boxes": boxes,
+                       "batches": len(groups), "pair_capacity": cap, "memory_budget_bytes": BUDGET,
+                       "pairs": int(st["n_vf"] + st["n_ee"]),
+                       "collisions": int(np.isfinite(toi).sum()), "parity_sample": len(sample)},
+            "boxes_per_s": boxes / (ms * 1e-3),
+            "batch512_ms": rep}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    import threading
+    from paper_2112_06300_gb300 import build, ccd
+    build.build()
+    envs = environments(args.envs)
+    srv = ccd.Server(0, n_slots=2, max_scenes=256, memory_cap=BUDGET, arena_bytes=4 << 30,
+                     pairs_per_box=PAIRS_PER_BOX)
+    for e in envs[:64]:                              # warm-up: contexts and buffers grow
+        srv.wait(srv.submit_scene(e.V0, e.V1, e.E, e.F))
+    rng = np.random.default_rng(3)
+    gaps = rng.exponential(1.0 / args.rate, len(envs))
+    arrive = np.cumsum(gaps)
+    tickets = []
+    t0 = time.perf_counter()
+    for k, e in enumerate(envs):
+        while time.perf_counter() - t0 < arrive[k]:
+            pass
+        tickets.append(srv.submit_scene(e.V0, e.V1, e.E, e.F))
+    t_sub = time.perf_counter() - t0
+    res = [srv.wait(t) for t in tickets]
+    t_all = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r[1] for r in res])
+    toi = np.array([r[0] for r in res])
+    line = {"metric": "served CCD steps/s and p50/p99 latency (ms), Poisson arrivals",
+            "value": len(envs) / t_all, "unit": "steps/s", "n_gpus": 1, "steps": len(envs), "warmup": 64,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded rigid environments)",
+            "config": {"workload": f"{len(envs)} rigid environments arriving as a Poisson stream at "
+                                   f"{args.rate:g}/s, 2 slots, <= 256 scenes per batch, 64 GiB cap",
+                       "offered_rate": len(envs) / t_sub, "target_rate": args.rate},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "batches": st["n_batches"], "max_batch_scenes": st["max_batch_scenes"],
+            "collisions": int(np.isfinite(toi).sum())}
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args):
+    import torch
+    from paper_2112_06300_gb300 import build, ccd, scenes
+    build.build()
+    torch.cuda.set_device(0)
+    s = scenes.cloth_and_bodies(args.n)
+    V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+    res = {}
+    sets = {}
+    for name, o in (("fp32_strips", {}), ("fp32_tiled", {"sweep_kernel": 2}), ("fp64", {"broad_fp64": 1})):
+        c = ccd.CCD(0, profile_stages=1, **o)
+        vf, ee = c.broad(V0, V1, E, F)
+        times = []
+        for _ in range(max(1, args.steps // 4)):
+            c.broad(V0, V1, E, F)
+            t = c.stage_times()
+            times.append(t["boxes"] + t["sort"] + t["sweep"])
+        rc, st = c.status()
+        t_step = c.step(V0, V1, E, F)
+        res[name] = {"broad_ms": float(np.median(times)), "candidates_fp32": int(st["n_superset"]),
+                     "pairs": int(len(vf) + len(ee)), "toi": t_step}
+        key = lambda t: torch.sort(t[:, 0].long() * (1 << 32) + t[:, 1].long())[0]
+        sets[name] = (key(vf), key(ee))
+        c.close()
+    eq = all(torch.equal(sets[n][0], sets["fp64"][0]) and torch.equal(sets[n][1], sets["fp64"][1])
+             for n in ("fp32_strips", "fp32_tiled"))
+    line = {"metric": "broad-phase ms: FP32 outward-rounded + exact FP64 filter vs all-FP64",
+            "value": res["fp64"]["broad_ms"] / res["fp32_strips"]["broad_ms"], "unit": "x (FP64 ms / FP32 ms)",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64 / f64", "data": "synthetic (seeded)",
+            "config": {"workload": f"folded cloth {args.n}x{args.n} + 500 icospheres (5,120 tri) + 500 tori "
+                                   f"(3,072 tri) in [0,10]^3", "boxes": s.n_boxes},
+            "forms": res, "final_sets_equal": bool(eq)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

@@ -252,6 +252,37 @@ typedef struct {
 int ccd_autotune(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
                  const int32_t *F, int64_t nF, int32_t reps, ccd_tuning *out, void *stream);
 
+/*
+ * Device memory model.  Section "Batching" sizes the candidate list C from
+ * the free memory M as S_C = (M - S_P) / (S_Q + S_i): per pair, the query
+ * data of the narrow phase plus the pair itself.  The same accounting for
+ * this implementation: a step over n_boxes boxes (in n_scenes scenes) with
+ * room for P candidate pairs needs
+ *     bytes_fixed + n_boxes * bytes_per_box + n_scenes * bytes_per_scene
+ *       + P * bytes_per_pair
+ * bytes of device memory (buffers grow to these sizes and are kept).
+ * o: the context's options (NULL = defaults; the interval-queue capacity
+ * enters bytes_fixed).
+ */
+typedef struct {
+    int64_t bytes_per_box;    /* boxes, sort keys, strip copies, sorted arrays */
+    int64_t bytes_per_pair;   /* pair, candidate slots, narrow-phase query scratch */
+    int64_t bytes_per_scene;  /* per-scene statistics and strip layout */
+    int64_t bytes_fixed;      /* control block and interval queue */
+} ccd_memory_model;
+
+int ccd_get_memory_model(const ccd_opts *o, ccd_memory_model *m);
+
+/* The largest pair capacity P that fits mem_bytes for a step over n_boxes
+ * boxes in n_scenes scenes under the model above (0 when even the boxes do
+ * not fit).  Use it as opts.pair_capacity for a memory budget. */
+int64_t ccd_pair_capacity_for(const ccd_opts *o, int64_t mem_bytes, int64_t n_boxes, int32_t n_scenes);
+
+/* Enqueue on `stream` a copy of the context's device status (a CCD_*
+ * value raised by its kernels, e.g. CCD_ETRUNC when pairs did not fit) into
+ * *status (host pinned or device memory); no synchronization. */
+int ccd_status_async(ccd_ctx *ctx, int32_t *status, void *stream);
+
 /* Synchronize the context's last stream and read its device status and
  * counters (stats may be NULL).  Returns the device status. */
 int ccd_get_status(ccd_ctx *ctx, ccd_stats *stats);
@@ -277,6 +308,79 @@ const char *ccd_status_str(int status);
  * small buffer.
  */
 int ccd_measure_fp64_peak(int device, double *gflops);
+
+/*
+ * Serving.  Continuous batching of steps that arrive one scene at a time
+ * (Section "Batching" runs the method over many independent inputs; here
+ * they arrive over time).  The server owns a pinned host arena, n_slots
+ * contexts each with its own stream, and a scheduler thread.  A client asks
+ * for space for one scene (ccd_server_request), writes the scene there --
+ * V0 and V1 as structure of arrays [3][nV], E [nE][2] and F [nF][3] with
+ * vertex ids local to the scene -- and queues it (ccd_server_submit).
+ * Whenever a slot is free, the scheduler takes the queued scenes in arrival
+ * order, up to max_scenes scenes and max_boxes boxes and within the slot's
+ * share of memory_cap (by the memory model above), and runs them as one
+ * batched step (ccd_step_batch) on the slot's stream: one copy of the
+ * scenes' contiguous arena range to the device, one kernel that lays them
+ * out, the step, one copy of the per-scene earliest times back.  Slots run
+ * concurrently, so copies of one batch overlap the work of another.
+ * ccd_server_wait returns a scene's earliest time (+inf: no collision) and
+ * its latency from submission to completion.  A scene's result does not
+ * depend on the other scenes of its batch.
+ */
+typedef struct ccd_server ccd_server;
+
+typedef struct {
+    int32_t n_slots;         /* batches in flight at once (1-16); default 2 */
+    int32_t max_scenes;      /* scenes per batch (1-65536); default 256 */
+    int64_t max_boxes;       /* boxes per batch; default 2^24 */
+    int64_t memory_cap;      /* device bytes for all slots (admission); default 64 GiB */
+    int64_t arena_bytes;     /* pinned host arena; default 1 GiB */
+    double delta, min_sep;   /* as in ccd_opts */
+    int64_t max_iter;
+    double pairs_per_box;    /* candidate pairs per box the admission budgets for
+                                (0 = 4); a batch with more pairs fails with
+                                CCD_ETRUNC */
+} ccd_server_opts;
+
+typedef struct {
+    int64_t n_submitted;     /* scenes submitted */
+    int64_t n_done;          /* scenes completed */
+    int64_t n_batches;       /* batches launched */
+    int64_t max_batch_scenes;  /* largest batch */
+    double sum_latency_ms;   /* sum of completed scenes' latencies */
+} ccd_server_stats;
+
+void ccd_server_default_opts(ccd_server_opts *o);
+
+/* Start a server on `device` (o: NULL = defaults).  Errors: CCD_EINVAL (bad
+ * option), CCD_ENOMEM (arena or context allocation), CCD_EDEVICE. */
+int ccd_server_create(ccd_server **out, const ccd_server_opts *o, int device);
+
+/* Stop the scheduler after the submitted scenes complete and free
+ * everything (scenes requested but never submitted are dropped). */
+int ccd_server_destroy(ccd_server *srv);
+
+/* Reserve arena space for one scene of nV vertices, nE edges, nF faces; the
+ * four pointers receive where to write it (pinned host memory, valid until
+ * the scene's ccd_server_wait returns).  Blocks while the arena is full.
+ * Scenes are batched in the order of their requests; a requested scene holds
+ * back later ones until it is submitted.  CCD_ENOMEM: the scene alone does
+ * not fit the arena, max_boxes or a slot's memory share. */
+int ccd_server_request(ccd_server *srv, int64_t nV, int64_t nE, int64_t nF, double **V0, double **V1,
+                       int32_t **E, int32_t **F, uint64_t *ticket);
+
+/* Queue a written scene (thread-safe). */
+int ccd_server_submit(ccd_server *srv, uint64_t ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a submitted scene; on completion
+ * writes its earliest time and latency (ms from submission to completion),
+ * releases the ticket and returns the batch's device status (CCD_OK, or e.g.
+ * CCD_ETRUNC).  CCD_ETIMEOUT: not done yet (the ticket stays valid). */
+int ccd_server_wait(ccd_server *srv, uint64_t ticket, double timeout_ms, double *toi, double *latency_ms);
+
+/* Counters; returns the first launch error seen (CCD_OK if none). */
+int ccd_server_get_stats(ccd_server *srv, ccd_server_stats *st);
 
 #ifdef __cplusplus
 }

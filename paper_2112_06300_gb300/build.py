@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libccd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ccd_api.cu", "ccd_broad.cu", "ccd_narrow.cu", "ccd_fp64_peak.cu", "ccd_noalloc.cu"]
+SOURCES = ["ccd_api.cu", "ccd_broad.cu", "ccd_narrow.cu", "ccd_fp64_peak.cu", "ccd_noalloc.cu", "ccd_server.cu"]
 HEADERS = ["ccd_common.cuh", "ccd_kernels.cuh"]
 
 

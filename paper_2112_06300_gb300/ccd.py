@@ -51,6 +51,25 @@ class ccd_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
 
 
+class ccd_memory_model(ctypes.Structure):
+    _fields_ = [("bytes_per_box", ctypes.c_int64), ("bytes_per_pair", ctypes.c_int64),
+                ("bytes_per_scene", ctypes.c_int64), ("bytes_fixed", ctypes.c_int64)]
+
+
+class ccd_server_opts(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("max_scenes", ctypes.c_int32), ("max_boxes", ctypes.c_int64),
+                ("memory_cap", ctypes.c_int64), ("arena_bytes", ctypes.c_int64), ("delta", ctypes.c_double),
+                ("min_sep", ctypes.c_double), ("max_iter", ctypes.c_int64), ("pairs_per_box", ctypes.c_double)]
+
+
+class ccd_server_stats(ctypes.Structure):
+    _fields_ = [("n_submitted", ctypes.c_int64), ("n_done", ctypes.c_int64), ("n_batches", ctypes.c_int64),
+                ("max_batch_scenes", ctypes.c_int64), ("sum_latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ccd_tuning(ctypes.Structure):
     _fields_ = [("sweep_kernel", ctypes.c_int32), ("export_budget", ctypes.c_int32),
                 ("strip_width", ctypes.c_double), ("queue_capacity", ctypes.c_int64),
@@ -100,6 +119,28 @@ def lib():
     L.ccd_narrow_noalloc.restype = ctypes.c_int
     L.ccd_autotune.argtypes = [P, P, P, i64, P, i64, P, i64, i32, ctypes.POINTER(ccd_tuning), P]
     L.ccd_autotune.restype = ctypes.c_int
+    L.ccd_status_async.argtypes = [P, P, P]
+    L.ccd_status_async.restype = ctypes.c_int
+    L.ccd_get_memory_model.argtypes = [ctypes.POINTER(ccd_opts), ctypes.POINTER(ccd_memory_model)]
+    L.ccd_get_memory_model.restype = ctypes.c_int
+    L.ccd_pair_capacity_for.argtypes = [ctypes.POINTER(ccd_opts), i64, i64, i32]
+    L.ccd_pair_capacity_for.restype = ctypes.c_int64
+    L.ccd_server_default_opts.argtypes = [ctypes.POINTER(ccd_server_opts)]
+    L.ccd_server_default_opts.restype = None
+    L.ccd_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ccd_server_opts), ctypes.c_int]
+    L.ccd_server_create.restype = ctypes.c_int
+    L.ccd_server_destroy.argtypes = [P]
+    L.ccd_server_destroy.restype = ctypes.c_int
+    PD, PI = ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))
+    L.ccd_server_request.argtypes = [P, i64, i64, i64, PD, PD, PI, PI, ctypes.POINTER(ctypes.c_uint64)]
+    L.ccd_server_request.restype = ctypes.c_int
+    L.ccd_server_submit.argtypes = [P, ctypes.c_uint64]
+    L.ccd_server_submit.restype = ctypes.c_int
+    L.ccd_server_wait.argtypes = [P, ctypes.c_uint64, d, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]
+    L.ccd_server_wait.restype = ctypes.c_int
+    L.ccd_server_get_stats.argtypes = [P, ctypes.POINTER(ccd_server_stats)]
+    L.ccd_server_get_stats.restype = ctypes.c_int
     for f in ("ccd_create", "ccd_destroy", "ccd_broad", "ccd_narrow", "ccd_step", "ccd_get_status",
               "ccd_measure_fp64_peak", "ccd_stage_times"):
         getattr(L, f).restype = ctypes.c_int
@@ -361,3 +402,86 @@ class CCD:
 
     def stage_times(self):
         return ccd_stage_times(self.ctx)
+
+
+def ccd_get_memory_model(opts: Optional[ccd_opts] = None) -> dict:
+    m = ccd_memory_model()
+    _check(lib().ccd_get_memory_model(ctypes.byref(opts) if opts is not None else None, ctypes.byref(m)),
+           "ccd_get_memory_model")
+    return {k: getattr(m, k) for k, _ in m._fields_}
+
+
+def ccd_pair_capacity_for(mem_bytes: int, n_boxes: int, n_scenes: int = 0, opts: Optional[ccd_opts] = None) -> int:
+    return int(lib().ccd_pair_capacity_for(ctypes.byref(opts) if opts is not None else None, int(mem_bytes),
+                                           int(n_boxes), int(n_scenes)))
+
+
+class Server:
+    """Serving runtime (ccd_server_*): scenes are written into the server's
+    pinned arena, queued, batched by its scheduler thread and completed
+    asynchronously."""
+
+    def __init__(self, device: int = 0, **opts):
+        o = ccd_server_opts()
+        lib().ccd_server_default_opts(ctypes.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown server option {k}")
+            setattr(o, k, v)
+        self.opts = o
+        self.handle = ctypes.c_void_p()
+        _check(lib().ccd_server_create(ctypes.byref(self.handle), ctypes.byref(o), device), "ccd_server_create")
+
+    def request(self, nV: int, nE: int, nF: int):
+        """Arena space for one scene: returns (ticket, V0 (3, nV), V1 (3, nV),
+        E (nE, 2), F (nF, 3)) as numpy views to fill."""
+        pv0, pv1 = ctypes.POINTER(ctypes.c_double)(), ctypes.POINTER(ctypes.c_double)()
+        pe, pf = ctypes.POINTER(ctypes.c_int32)(), ctypes.POINTER(ctypes.c_int32)()
+        t = ctypes.c_uint64()
+        _check(lib().ccd_server_request(self.handle, nV, nE, nF, ctypes.byref(pv0), ctypes.byref(pv1),
+                                        ctypes.byref(pe), ctypes.byref(pf), ctypes.byref(t)), "ccd_server_request")
+        view = lambda p, shape: np.ctypeslib.as_array(p, shape=shape) if shape[0] * shape[1] else \
+            np.zeros(shape, np.float64 if p._type_ is ctypes.c_double else np.int32)
+        return (t.value, view(pv0, (3, nV)), view(pv1, (3, nV)), view(pe, (nE, 2)), view(pf, (nF, 3)))
+
+    def submit_scene(self, V0, V1, E, F) -> int:
+        """Copy one scene ((nV, 3) positions, local (nE, 2) / (nF, 3) ids) into
+        the arena and queue it; returns its ticket."""
+        t, v0, v1, e, f = self.request(len(V0), len(E), len(F))
+        if len(V0):
+            v0[...] = np.asarray(V0, np.float64).T
+            v1[...] = np.asarray(V1, np.float64).T
+        if len(E):
+            e[...] = E
+        if len(F):
+            f[...] = F
+        _check(lib().ccd_server_submit(self.handle, t), "ccd_server_submit")
+        return t
+
+    def submit(self, ticket: int) -> None:
+        _check(lib().ccd_server_submit(self.handle, ticket), "ccd_server_submit")
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        """(earliest time, latency in ms) of a submitted scene; raises on a
+        device error."""
+        toi, lat = ctypes.c_double(), ctypes.c_double()
+        rc = lib().ccd_server_wait(self.handle, ticket, float(timeout_ms), ctypes.byref(toi), ctypes.byref(lat))
+        _check(rc, "ccd_server_wait")
+        return toi.value, lat.value
+
+    def stats(self) -> dict:
+        st = ccd_server_stats()
+        rc = lib().ccd_server_get_stats(self.handle, ctypes.byref(st))
+        _check(rc, "ccd_server_get_stats")
+        return st.as_dict()
+
+    def close(self) -> None:
+        if self.handle:
+            lib().ccd_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

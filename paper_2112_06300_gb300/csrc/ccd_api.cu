@@ -21,7 +21,9 @@ struct ccd_ctx {
   int64_t cap_boxes = 0;
   void *broad_mem = nullptr;
   BroadBufs bb{};
-  // pair buffers of ccd_step
+  // pair buffer of ccd_step / ccd_step_batch: pair_cap pairs, vertex-face
+  // from the front, edge-edge from the back (vf and ee point at the same
+  // buffer)
   int64_t pair_cap = 0;
   int32_t *vf = nullptr, *ee = nullptr;
   // single-precision candidates of the strip sweep
@@ -99,18 +101,21 @@ __global__ void k_reset_narrow(DevCtl *c) {
   c->n_donated = 0;
   c->n_intervals_tail = 0;
   c->n_intervals_fp64 = 0;
+  c->n_idle = 0;
 }
 __global__ void k_reset_status(DevCtl *c) { c->status = CCD_OK; }
 
 // Pair counts of the broad phase clamped to the buffer capacities (ccd_step:
 // the narrow phase reads them on the device, no host round trip).
-// Pairs that did not fit raise CCD_ETRUNC (the first error wins).
-__global__ void k_counts_from_broad(DevCtl *c, int64_t vf_cap, int64_t ee_cap) {
-  unsigned long long a = c->n_vf, b = c->n_ee;
-  c->pair_counts[0] = (long long)min(a, (unsigned long long)vf_cap);
-  c->pair_counts[1] = (long long)min(b, (unsigned long long)ee_cap);
-  if (a > (unsigned long long)vf_cap || b > (unsigned long long)ee_cap || c->sup_overflow)
-    atomicCAS(&c->status, CCD_OK, CCD_ETRUNC);
+// Pair counts of the shared pair buffer (cap pairs, vertex-face from the
+// front, edge-edge from the back), clamped so that the two lists do not
+// overlap; pairs that did not fit raise CCD_ETRUNC (the first error wins).
+__global__ void k_counts_from_broad(DevCtl *c, int64_t cap) {
+  const unsigned long long a = c->n_vf, b = c->n_ee, uc = (unsigned long long)cap;
+  const unsigned long long va = min(a, uc);
+  c->pair_counts[0] = (long long)va;
+  c->pair_counts[1] = (long long)min(b, uc - va);
+  if (a + b > uc || c->sup_overflow) atomicCAS(&c->status, CCD_OK, CCD_ETRUNC);
 }
 
 int ensure_broad(ccd_ctx *c, int64_t nB) {
@@ -245,14 +250,18 @@ int ensure_pairs(ccd_ctx *c, int64_t cap) {
   if (rc) return rc;
   if (cap <= c->pair_cap) return CCD_OK;
   if (c->vf) CK(cudaFree(c->vf));
-  if (c->ee) CK(cudaFree(c->ee));
   c->vf = c->ee = nullptr;
   c->pair_cap = 0;
   CK(cudaMalloc(&c->vf, cap * 2 * sizeof(int32_t)));
-  CK(cudaMalloc(&c->ee, cap * 2 * sizeof(int32_t)));
+  c->ee = c->vf;
   c->pair_cap = cap;
   return CCD_OK;
 }
+
+// Default pair capacity of ccd_step / ccd_step_batch: 4 pairs per box (the
+// 512 x 512 folded cloth, a dense self-contact case, needs 3.2), at least
+// 2^20; synchronous calls grow it on demand.
+int64_t default_pair_capacity(int64_t nB) { return std::max<int64_t>(1 << 20, 4 * nB); }
 
 bool mesh_args_ok(const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
                   const int32_t *F, int64_t nF) {
@@ -272,12 +281,12 @@ struct SceneSpec {
 
 int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
                  const int32_t *F, int64_t nF, int32_t *vf_out, int64_t vf_cap, int32_t *ee_out, int64_t ee_cap,
-                 cudaStream_t s, const SceneSpec &sc = SceneSpec{0, nullptr, nullptr, nullptr}) {
+                 cudaStream_t s, const SceneSpec &sc = SceneSpec{0, nullptr, nullptr, nullptr}, bool ee_rev = false) {
   const int64_t nB = nV + nE + nF;
   int rc = ensure_broad(c, nB);
   if (rc) return rc;
   if (!c->capturing) {
-    rc = ensure_sup(c, std::max<int64_t>(vf_cap + ee_cap, 8 * nB));
+    rc = ensure_sup(c, ee_rev ? 2 * vf_cap : std::max<int64_t>(vf_cap + ee_cap, 8 * nB));
     if (rc) return rc;
   }
   if (sc.n > 0) {
@@ -376,6 +385,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.ee_out = ee_out;
   A.vf_cap = vf_cap;
   A.ee_cap = ee_cap;
+  A.ee_rev = ee_rev ? 1 : 0;
   A.ctl = c->ctl;
   A.s_key = s_key;
   A.n_dev = &c->ctl->n_copies;
@@ -407,8 +417,8 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
                   const int32_t *F, double delta, double min_sep, int64_t max_iter, int mode,
                   unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s,
                   bool zero_rule_pass = false, int n_scenes = 0, const int64_t *voff = nullptr,
-                  unsigned long long *toi_scene = nullptr) {
-  const int64_t nq = n_vf + n_ee;
+                  unsigned long long *toi_scene = nullptr, int64_t ee_end = 0) {
+  const int64_t nq = counts_from_ctl && ee_end > 0 ? ee_end : n_vf + n_ee;
   int rc = ensure_narrow(c, nq, s);
   if (rc) return rc;
   if (zero_rule_pass)
@@ -422,6 +432,7 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   A.n_vf = n_vf;
   A.n_ee = n_ee;
   A.counts_from_ctl = counts_from_ctl;
+  A.ee_end = ee_end;
   A.V0 = V0;
   A.V1 = V1;
   A.nV = nV;
@@ -583,7 +594,6 @@ int ccd_destroy(ccd_ctx *c) {
   cudaDeviceSynchronize();
   cudaFree(c->broad_mem);
   cudaFree(c->vf);
-  cudaFree(c->ee);
   cudaFree(c->sup);
   cudaFree(c->qflags);
   cudaFree(c->qiters);
@@ -677,21 +687,22 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   const bool host_out = !is_device_ptr(toi_min);
-  int64_t want = c->opts.pair_capacity > 0 ? c->opts.pair_capacity : std::max<int64_t>(1 << 20, 8 * (nV + nE + nF));
+  int64_t want = c->opts.pair_capacity > 0 ? c->opts.pair_capacity : default_pair_capacity(nV + nE + nF);
   auto enqueue = [&](cudaStream_t st) -> int {
     clear_marks(c);
     k_reset_status<<<1, 1, 0, st>>>(c->ctl);
-    int r = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, st);
+    int r = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, st,
+                         SceneSpec{0, nullptr, nullptr, nullptr}, true);
     if (r) return r;
-    k_counts_from_broad<<<1, 1, 0, st>>>(c->ctl, c->pair_cap, c->pair_cap);
+    k_counts_from_broad<<<1, 1, 0, st>>>(c->ctl, c->pair_cap);
     c->n_launches += 2;
     r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep, max_iter, 1,
-                      nullptr, nullptr, st);
+                      nullptr, nullptr, st, false, 0, nullptr, nullptr, c->pair_cap);
     if (r) return r;
     if (c->opts.no_zero_toi) {
       // second pass only when the first found t* = 0 (decided on the device)
       r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, 0.0, max_iter, 1,
-                        nullptr, nullptr, st, true);
+                        nullptr, nullptr, st, true, 0, nullptr, nullptr, c->pair_cap);
       if (r) return r;
     }
     if (!host_out && cudaMemcpyAsync(toi_min, &c->ctl->toi_bits, sizeof(double), cudaMemcpyDeviceToDevice, st) !=
@@ -702,7 +713,7 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
   for (int attempt = 0; attempt < 3; ++attempt) {
     int rc = ensure_pairs(c, want);
     if (rc) return rc;
-    rc = ensure_narrow(c, 2 * c->pair_cap, s);
+    rc = ensure_narrow(c, c->pair_cap, s);
     if (rc) return rc;
     rc = ensure_broad(c, nV + nE + nF);
     if (rc) return rc;
@@ -732,12 +743,13 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     CK(cudaMemcpyAsync(&h.status, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&h.ovf, &c->ctl->sup_overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (!h.ovf && (int64_t)h.nvf <= c->pair_cap && (int64_t)h.nee <= c->pair_cap) {
+    if (!h.ovf && (int64_t)(h.nvf + h.nee) <= c->pair_cap) {
       std::memcpy(toi_min, &h.toi, sizeof(double));
       return h.status;
     }
-    unsigned long long need = std::max(h.nvf, h.nee);
-    if (h.ovf) need = std::max(need, h.nsup);
+    // the candidate buffer holds twice the pair capacity
+    unsigned long long need = h.nvf + h.nee;
+    if (h.ovf) need = std::max(need, h.nsup / 2 + 1);
     want = (int64_t)need + (int64_t)(need / 8) + 1024;
   }
   return CCD_ETRUNC;
@@ -756,9 +768,9 @@ int ccd_step_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const 
   c->last_stream = s;
   clear_marks(c);
   const int64_t nB = nV + nE + nF;
-  int rc = ensure_pairs(c, c->opts.pair_capacity > 0 ? c->opts.pair_capacity : std::max<int64_t>(1 << 20, 8 * nB));
+  int rc = ensure_pairs(c, c->opts.pair_capacity > 0 ? c->opts.pair_capacity : default_pair_capacity(nB));
   if (rc) return rc;
-  rc = ensure_narrow(c, 2 * c->pair_cap, s);
+  rc = ensure_narrow(c, c->pair_cap, s);
   if (rc) return rc;
   rc = ensure_broad(c, nB);
   if (rc) return rc;
@@ -768,14 +780,15 @@ int ccd_step_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const 
     clear_marks(c);
     k_reset_status<<<1, 1, 0, st>>>(c->ctl);
     const SceneSpec sc{n_scenes, vert_off, edge_off, face_off};
-    int r = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, st, sc);
+    int r = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, st, sc, true);
     if (r) return r;
-    k_counts_from_broad<<<1, 1, 0, st>>>(c->ctl, c->pair_cap, c->pair_cap);
+    k_counts_from_broad<<<1, 1, 0, st>>>(c->ctl, c->pair_cap);
     k_fill_u64<<<(unsigned)std::min<int64_t>(cdiv(n_scenes, 256), 1024), 256, 0, st>>>(
         (unsigned long long *)toi_out, n_scenes, 0x7FF0000000000000ull);
     c->n_launches += 3;
     return launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep, max_iter,
-                         2, nullptr, nullptr, st, false, n_scenes, vert_off, (unsigned long long *)toi_out);
+                         2, nullptr, nullptr, st, false, n_scenes, vert_off, (unsigned long long *)toi_out,
+                         c->pair_cap);
   };
   if (!c->opts.use_graph) return enqueue(s);
   struct {
@@ -823,12 +836,14 @@ int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     for (int r = 0; r < n; ++r) {
       if (narrow) {
         k_reset_status<<<1, 1, 0, s>>>(c->ctl);
-        k_counts_from_broad<<<1, 1, 0, s>>>(c->ctl, c->pair_cap, c->pair_cap);
+        k_counts_from_broad<<<1, 1, 0, s>>>(c->ctl, c->pair_cap);
       }
       cudaEventRecord(e0, s);
       int r2 = narrow ? launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F,
-                                      c->opts.delta, c->opts.min_sep, c->opts.max_iter, 1, nullptr, nullptr, s)
-                      : launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, s);
+                                      c->opts.delta, c->opts.min_sep, c->opts.max_iter, 1, nullptr, nullptr, s,
+                                      false, 0, nullptr, nullptr, c->pair_cap)
+                      : launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, s,
+                                     SceneSpec{0, nullptr, nullptr, nullptr}, true);
       cudaEventRecord(e1, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) r2 = CCD_ECUDA;
       int st = CCD_OK;
@@ -930,6 +945,41 @@ int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   out->default_ms = base_b + base_n;
   out->n_trials = trials;
   return CCD_OK;
+}
+
+int ccd_status_async(ccd_ctx *c, int32_t *status, void *stream) {
+  if (!c || !status) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  CK(cudaMemcpyAsync(status, &c->ctl->status, sizeof(int32_t), cudaMemcpyDefault, (cudaStream_t)stream));
+  return CCD_OK;
+}
+
+int ccd_get_memory_model(const ccd_opts *o, ccd_memory_model *m) {
+  if (!m) return CCD_EINVAL;
+  ccd_opts opts;
+  ccd_default_opts(&opts);
+  if (o) opts = *o;
+  // per box, as laid out by ensure_broad: FP32 and FP64 extents, vertex ids,
+  // sort keys and values and the sorted arrays for 3 copies per box (strip
+  // sweep), the one-list sorted arrays, copy offsets; plus the scene index
+  m->bytes_per_box = 24 + 48 + 16 + 3 * (16 + 8) + 2 + 4 + 3 * (4 + 16 + 16) + (8 + 8 + 32) + 4 + 4;
+  // per pair slot: the pair (8), two candidate slots (16), and the narrow
+  // phase's per-query flags (4), counter (8), record (24 words + 28 floats)
+  // and scene (4)
+  m->bytes_per_pair = 8 + 16 + 4 + 8 + (24 * 8 + 28 * 4) + 4;
+  // per scene: statistics, axis and strip layout
+  m->bytes_per_scene = 9 * 4 + 6 * 4 + 4 + (int64_t)sizeof(StripParam);
+  const int64_t ring = opts.queue_capacity > 0 ? opts.queue_capacity : (1 << 21);
+  m->bytes_fixed = ring * (int64_t)sizeof(RingCell) + (int64_t)sizeof(DevCtl) + 64 * 256;
+  return CCD_OK;
+}
+
+int64_t ccd_pair_capacity_for(const ccd_opts *o, int64_t mem_bytes, int64_t n_boxes, int32_t n_scenes) {
+  ccd_memory_model m;
+  if (n_boxes < 0 || n_scenes < 0 || ccd_get_memory_model(o, &m) != CCD_OK) return 0;
+  const int64_t rest = mem_bytes - m.bytes_fixed - std::max<int64_t>(n_boxes, 1024) * m.bytes_per_box -
+                       (int64_t)n_scenes * m.bytes_per_scene;
+  return rest > 0 ? rest / m.bytes_per_pair : 0;
 }
 
 int ccd_get_status(ccd_ctx *c, ccd_stats *st) {

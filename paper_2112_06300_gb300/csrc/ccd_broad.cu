@@ -630,8 +630,9 @@ __device__ __forceinline__ void emit(const SweepArgs &A, bool is_vf, bool is_ee,
   if (__any_sync(mask, is_ee)) {
     unsigned long long at = warp_append(&A.ctl->n_ee, is_ee, mask);
     if (is_ee && (int64_t)at < A.ee_cap) {
-      A.ee_out[2 * at] = p0;
-      A.ee_out[2 * at + 1] = p1;
+      const int64_t k = A.ee_rev ? A.ee_cap - 1 - (int64_t)at : (int64_t)at;
+      A.ee_out[2 * k] = p0;
+      A.ee_out[2 * k + 1] = p1;
     }
   }
 }
@@ -1025,8 +1026,9 @@ __global__ void __launch_bounds__(kFilterThreads) k_exact_filter(SweepArgs A) {
         int32_t *out = t == 0 ? A.vf_out : A.ee_out;
         const int64_t cap = t == 0 ? A.vf_cap : A.ee_cap;
         if ((int64_t)at[t] < cap) {
-          out[2 * at[t]] = (int32_t)(pr[r].x & 0x7FFFFFFFu);
-          out[2 * at[t] + 1] = (int32_t)pr[r].y;
+          const int64_t k = t == 1 && A.ee_rev ? cap - 1 - (int64_t)at[t] : (int64_t)at[t];
+          out[2 * k] = (int32_t)(pr[r].x & 0x7FFFFFFFu);
+          out[2 * k + 1] = (int32_t)pr[r].y;
         }
         ++at[t];
       }

@@ -27,6 +27,7 @@ struct DevCtl {
   unsigned long long n_donated;  // subtrees passed between lanes of a warp
   unsigned long long n_intervals_tail;  // intervals evaluated after the query list ran out
   unsigned long long n_intervals_fp64;  // intervals the FP32 filter could not decide
+  long long n_idle;              // warps of the narrow kernel waiting for work
   int rerun;                     // zero-TOI rule: 1 when the second pass must run
   int pad_;
   // strip sweep
@@ -55,6 +56,9 @@ struct NarrowArgs {
   const int32_t *ee;             // [n_ee][2]
   int64_t n_vf, n_ee;
   int counts_from_ctl;           // 1: take n_vf, n_ee from ctl->pair_counts
+  int64_t ee_end;                // > 0: one shared pair buffer of ee_end pairs, vertex-face
+                                 // from the front (vf), edge-edge from the back: the edge-edge
+                                 // list is the last n_ee pairs (with counts_from_ctl)
   const double *V0, *V1;         // [3][nV]
   int64_t nV;
   const int32_t *E, *F;
@@ -199,6 +203,7 @@ struct SweepArgs {
   const long long *lo64, *hi64;  // [3][nB] by box id
   int32_t *vf_out, *ee_out;
   int64_t vf_cap, ee_cap;
+  int ee_rev;                    // 1: edge-edge pair k goes to slot ee_cap - 1 - k (shared buffer)
   DevCtl *ctl;
   // strip sweep: sorted keys (strip segment << 32 | minimum on the sweep
   // axis) and the number of box copies, both on the device

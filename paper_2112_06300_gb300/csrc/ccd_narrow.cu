@@ -189,18 +189,24 @@ __device__ __forceinline__ int last_axis(const unsigned long long K[3], const No
 }
 
 // The shallowest pending right sibling on the path from the unit's root to
-// node N (depth `depth`): the largest subtree the lane still owes.  Returns its
-// depth (0 if none) and the sibling in S.
+// node N (depth `depth`) that starts before `cut` (bits of the current t*):
+// the largest subtree the lane still owes.  Returns its depth (0 if none) and
+// the sibling in S.  Pending siblings above it start at or after t*, so they
+// would be pruned: a lane that hands S off and keeps only what lies below
+// S's depth loses nothing (their accepts could not lower t*).
 __device__ __forceinline__ int shallowest_pending(const unsigned long long K[3], const Node &N, int depth,
-                                                  int root_depth, Node &S) {
+                                                  int root_depth, unsigned long long cut, Node &S) {
   Node W = N;
   int found = 0;
   for (int d = depth; d > root_depth; --d) {
     int a = last_axis(K, W);
     if ((W.n(a) & 1) == 0) {
-      S = W;
-      S.add(a, 1);
-      found = d;
+      const uint64_t n0 = a == 0 ? W.n0 + 1 : W.n0;   // the sibling's t numerator
+      if (dbits(dyadic(n0, W.l0)) < cut) {
+        S = W;
+        S.add(a, 1);
+        found = d;
+      }
     }
     W.up(a);
   }
@@ -598,6 +604,7 @@ __device__ __forceinline__ void load_record_stage(QueryData &Q, bool &vf, const 
 
 constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a warp retires
 constexpr int kRefresh = 8;            // iterations between reads of the shared values
+constexpr int kExportEvery = 4;        // iterations between hand-offs to idle warps
 
 // Control flow is warp-uniform at the loop level: refill, idling and exit are
 // decided for the whole warp (ballots and broadcasts), and the per-lane work
@@ -610,6 +617,7 @@ k_narrow(NarrowArgs A) {
   if (A.counts_from_ctl) {
     A.n_vf = ctl->pair_counts[0];
     A.n_ee = ctl->pair_counts[1];
+    if (A.ee_end > 0) A.ee = A.vf + 2 * (A.ee_end - A.n_ee);
   }
   const unsigned FULL = 0xFFFFFFFFu;
   const int64_t nq = A.n_vf + A.n_ee;
@@ -642,11 +650,17 @@ k_narrow(NarrowArgs A) {
   // only prune less or hand work out later.
   unsigned long long pf_toi = kInfBits, pf_qnext = 0;          // lane 0: values in use
   unsigned long long nx_toi = kInfBits, nx_qnext = 0;          // lane 0: loads in flight
+  unsigned long long pf_occ = 0, nx_head = 0, nx_tail = 0;     // lane 0: ring occupancy
+  long long pf_idle = 0, nx_idle = 0;                          // lane 0: idle warps
+  bool am_idle = false;                      // warp-uniform: counted in ctl->n_idle
+  int exp_age = 0;                           // warp-uniform: iterations since a forced hand-off
   unsigned long long nx_scene = kInfBits;                      // per lane
   int pf_age = 0;
   if (lane == 0) {
     nx_toi = ld_relaxed_u64(&ctl->toi_bits);
     nx_qnext = ld_relaxed_u64(&ctl->q_next);
+    nx_head = ld_relaxed_u64(&ctl->q_head);
+    nx_tail = ld_relaxed_u64(&ctl->q_tail);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->t_start, 0ull, globaltimer());
 
@@ -691,6 +705,7 @@ k_narrow(NarrowArgs A) {
     // (intervals are exported only once every query has been handed out,
     // so a warp looks at the ring only after its own claim came back empty)
     if (__any_sync(FULL, !have)) {
+      const unsigned long long pf_toi_b = __shfl_sync(FULL, pf_toi, 0);
       const unsigned m = __ballot_sync(FULL, !have);
       if (m && !exhausted && staged) {
         if (s_pos == s_n) {
@@ -756,51 +771,37 @@ k_narrow(NarrowArgs A) {
                             : 0;
         if (lane == 0 && got) atomicAdd(&ctl->pending, (unsigned long long)got);
       }
-      if (exhausted && __any_sync(FULL, !have)) {
-        unsigned long long hd = 0, tl_ = 0;
-        if (lane == 0) {
-          hd = ld_relaxed_u64(&ctl->q_head);
-          tl_ = ld_relaxed_u64(&ctl->q_tail);
-        }
-        hd = __shfl_sync(FULL, hd, 0);
-        tl_ = __shfl_sync(FULL, tl_, 0);
-        if (hd != tl_) {
-          const unsigned m = __ballot_sync(FULL, !have);
-          unsigned long long pos0 = 0;
-          int r = 0;
-          if (lane == 0) {
-            const int want = __popc(m);
-            for (int tries = 0; tries < 8 && r == 0; ++tries) {
-              const unsigned long long h = ld_relaxed_u64(&ctl->q_head);
-              int k = 0;
-              while (k < want && ld_acquire_u64(&A.ring[(h + k) & A.ring_mask].seq) == h + k + 1) ++k;
-              if (k == 0) break;
-              if (atomicCAS(&ctl->q_head, h, h + k) == h) {
-                pos0 = h;
-                r = k;
-              }
-            }
-          }
-          pos0 = __shfl_sync(FULL, pos0, 0);
-          r = __shfl_sync(FULL, r, 0);
-          const int rank = __popc(m & lt_mask);
-          if (!have && rank < r) {
-            const unsigned long long pos = pos0 + rank;
-            RingCell *c = &A.ring[pos & A.ring_mask];
-            (void)ld_acquire_u64(&c->seq);   // pairs with the writer's release
-            const unsigned long long w0 = c->w[0], w1 = c->w[1], w2 = c->w[2];
-            const unsigned long long m54 = (1ull << 54) - 1;
-            q = c->q;
-            N.n0 = w0 & m54;
-            N.n1 = w1 & m54;
-            N.n2 = w2 & m54;
-            N.l0 = (int)(w0 >> 54);
-            N.l1 = (int)(w1 >> 54);
-            N.l2 = (int)(w2 >> 54);
-            st_release_u64(&c->seq, pos + A.ring_mask + 1);   // free for the next lap
-            have = fresh = true;
-            whole = false;
-          }
+      if (exhausted && __any_sync(FULL, !have) && __shfl_sync(FULL, pf_occ, 0) > 0) {
+        // pop up to one cell per idle lane: lanes test the cells' sequence
+        // numbers in parallel, lane 0 claims the ready prefix with one CAS
+        const unsigned m = __ballot_sync(FULL, !have);
+        const int want = __popc(m);
+        unsigned long long h = 0;
+        if (lane == 0) h = ld_relaxed_u64(&ctl->q_head);
+        h = __shfl_sync(FULL, h, 0);
+        const bool ready = lane < want && ld_acquire_u64(&A.ring[(h + lane) & A.ring_mask].seq) == h + lane + 1;
+        const unsigned rb = __ballot_sync(FULL, ready);
+        const int r = rb == FULL ? 32 : __ffs(~rb) - 1;
+        int ok = 0;
+        if (r > 0 && lane == 0) ok = atomicCAS(&ctl->q_head, h, h + r) == h;
+        ok = __shfl_sync(FULL, ok, 0);
+        const int rank = __popc(m & lt_mask);
+        if (ok && !have && rank < r) {
+          const unsigned long long pos = h + rank;
+          RingCell *c = &A.ring[pos & A.ring_mask];
+          (void)ld_acquire_u64(&c->seq);   // pairs with the writer's release
+          const unsigned long long w0 = c->w[0], w1 = c->w[1], w2 = c->w[2];
+          const unsigned long long m54 = (1ull << 54) - 1;
+          q = c->q;
+          N.n0 = w0 & m54;
+          N.n1 = w1 & m54;
+          N.n2 = w2 & m54;
+          N.l0 = (int)(w0 >> 54);
+          N.l1 = (int)(w1 >> 54);
+          N.l2 = (int)(w2 >> 54);
+          st_release_u64(&c->seq, pos + A.ring_mask + 1);   // free for the next lap
+          have = fresh = true;
+          whole = false;
         }
       }
       // Intra-warp donation: lanes still idle (no query left, nothing ready in
@@ -815,7 +816,12 @@ k_narrow(NarrowArgs A) {
         const bool cand = have && !fresh && __popc(busy & lt_mask) < __popc(idle);
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
-        if (cand) dS = shallowest_pending(K, N, depth, root_depth, S);
+        if (cand) {
+          unsigned long long c = tq;
+          if (A.mode == 1) c = min(c, pf_toi_b);
+          if (A.mode == 2) c = min(c, pf_scene);
+          dS = shallowest_pending(K, N, depth, root_depth, c, S);
+        }
         const unsigned donors = __ballot_sync(FULL, dS > 0);
         const int pairs = min(__popc(donors), __popc(idle));
         if (pairs > 0) {
@@ -885,14 +891,23 @@ k_narrow(NarrowArgs A) {
     if (__ballot_sync(FULL, have) == 0) {
       int stop = 0;
       if (lane == 0) {
-        bool empty = ld_relaxed_u64(&ctl->q_head) == ld_relaxed_u64(&ctl->q_tail);
-        stop = (exhausted && empty && ld_relaxed_u64(&ctl->pending) == 0) || ++idle_rounds > kIdleRounds;
+        const unsigned long long h = ld_relaxed_u64(&ctl->q_head), t = ld_relaxed_u64(&ctl->q_tail);
+        const unsigned long long pend = ld_relaxed_u64(&ctl->pending);
+        pf_occ = t > h ? t - h : 0;   // an idle warp sees new exports at once
+        stop = (exhausted && pf_occ == 0 && pend == 0) || ++idle_rounds > kIdleRounds;
+        if (!am_idle && !stop) atomicAdd((unsigned long long *)&ctl->n_idle, 1ull);
+        if (am_idle && stop) atomicAdd((unsigned long long *)&ctl->n_idle, ~0ull);
       }
+      am_idle = true;
       if (__shfl_sync(FULL, stop, 0)) break;
       __nanosleep(1000);
       continue;
     }
     idle_rounds = 0;
+    if (am_idle) {
+      if (lane == 0) atomicAdd((unsigned long long *)&ctl->n_idle, ~0ull);
+      am_idle = false;
+    }
 
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
@@ -953,8 +968,14 @@ k_narrow(NarrowArgs A) {
       if (lane == 0) {
         pf_toi = nx_toi;
         pf_qnext = nx_qnext;
+        pf_occ = nx_tail > nx_head ? nx_tail - nx_head : 0;
+        pf_idle = nx_idle;
+        if (pf_occ > 0) atomicMax(&ctl->queue_peak, pf_occ);
         nx_toi = ld_relaxed_u64(&ctl->toi_bits);
         nx_qnext = ld_relaxed_u64(&ctl->q_next);
+        nx_head = ld_relaxed_u64(&ctl->q_head);
+        nx_tail = ld_relaxed_u64(&ctl->q_tail);
+        nx_idle = (long long)ld_relaxed_u64((const unsigned long long *)&ctl->n_idle);
       }
       if (A.mode == 2) {
         pf_scene = nx_scene;
@@ -1082,33 +1103,57 @@ k_narrow(NarrowArgs A) {
     }
 
     // ---- 6. in the tail phase, hand the shallowest pending sibling to the
-    //         ring every `budget` evaluations (other warps take it) ----------
-    if (have && !unit_end && since >= A.budget && tail_phase) {
-      Node S{0, 0, 0, 0, 0, 0};
-      const int dS = shallowest_pending(K, N, depth, root_depth, S);
-      since = 0;
-      if (dS > 0) {
-        const unsigned long long pos = ring_reserve(&ctl->q_tail, &ctl->q_head, 1ull, ring_cap >> 2);
-        if (pos != ~0ull) {
-          // publish what the taker reads before the item becomes visible
-          if (tq != kInfBits) {
-            if (A.mode == 0)
-              atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
-            else if (A.mode == 2)
-              atomicMin(&A.toi_scene[sid], tq);
-            else
-              atomicMin(&ctl->toi_bits, tq);
+    //         ring every `budget` evaluations; one reservation per warp -------
+    {
+      // while warps sit idle and the ring holds fewer than a few items for
+      // each, every kExportEvery iterations each lane with a pending sibling
+      // hands it off (lanes that share subtrees within the warp rarely reach
+      // the per-unit budget)
+      bool hungry = false;
+      if (tail_phase) {
+        const long long iw = __shfl_sync(FULL, pf_idle, 0);
+        const unsigned long long occ = __shfl_sync(FULL, pf_occ, 0);
+        hungry = ++exp_age >= kExportEvery && iw > 0 && occ < 4ull * (unsigned long long)iw;
+        if (hungry) exp_age = 0;
+      }
+      const bool want_exp = have && !unit_end && tail_phase && (since >= A.budget || hungry);
+      if (__any_sync(FULL, want_exp)) {
+        Node S{0, 0, 0, 0, 0, 0};
+        int dS = 0;
+        if (want_exp) {
+          dS = shallowest_pending(K, N, depth, root_depth, cut, S);
+          since = 0;
+        }
+        const unsigned xm = __ballot_sync(FULL, dS > 0);
+        if (xm) {
+          unsigned long long pos0 = ~0ull;
+          if (lane == 0) {
+            pos0 = ring_reserve(&ctl->q_tail, &ctl->q_head, (unsigned long long)__popc(xm), ring_cap >> 2);
+            // count the new units before any of them becomes visible
+            if (pos0 != ~0ull) {
+              atomicAdd(&ctl->pending, (unsigned long long)__popc(xm));
+              __threadfence();
+            }
           }
-          atomicAdd(&A.qiters[q], (unsigned long long)cnt);
-          cap_left -= cnt;
-          cnt = 0;
-          atomicAdd(&ctl->pending, 1ull);
-          ring_write(A.ring, A.ring_mask, pos, (uint32_t)q, S, &ctl->status);
-          root_depth = dS;
-          const unsigned long long h = ld_relaxed_u64(&ctl->q_head), t = pos + 1;
-          const unsigned long long occ = t > h ? t - h : 0;
-          if (occ > ld_relaxed_u64(&ctl->queue_peak)) atomicMax(&ctl->queue_peak, occ);
-          ++n_exp;
+          pos0 = __shfl_sync(FULL, pos0, 0);
+          __syncwarp(FULL);
+          if (pos0 != ~0ull && dS > 0) {
+            // publish what the taker reads before the item becomes visible
+            if (tq != kInfBits) {
+              if (A.mode == 0)
+                atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
+              else if (A.mode == 2)
+                atomicMin(&A.toi_scene[sid], tq);
+              else
+                atomicMin(&ctl->toi_bits, tq);
+            }
+            atomicAdd(&A.qiters[q], (unsigned long long)cnt);
+            cap_left -= cnt;
+            cnt = 0;
+            ring_write(A.ring, A.ring_mask, pos0 + __popc(xm & lt_mask), (uint32_t)q, S, &ctl->status);
+            root_depth = dS;
+            ++n_exp;
+          }
         }
       }
     }
@@ -1148,6 +1193,7 @@ __global__ void k_prepare_queries(NarrowArgs A) {
   if (A.counts_from_ctl) {
     A.n_vf = A.ctl->pair_counts[0];
     A.n_ee = A.ctl->pair_counts[1];
+    if (A.ee_end > 0) A.ee = A.vf + 2 * (A.ee_end - A.n_ee);
   }
   const int64_t nq = A.n_vf + A.n_ee;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
@@ -1171,6 +1217,7 @@ __global__ void k_nozero_prepare(DevCtl *ctl) {
     ctl->pending = 0;
     ctl->toi_bits = kInfBits;
     ctl->t_start = ctl->t_exhausted = ctl->t_end = 0;
+    ctl->n_idle = 0;
   }
 }
 

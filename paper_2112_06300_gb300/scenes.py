@@ -15,6 +15,7 @@ touching and near-miss cases.
 """
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass, field
 from typing import Dict
 
@@ -294,6 +295,23 @@ def _random_rotation(rng):
                      [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
 
 
+@functools.lru_cache(maxsize=None)
+def _body(kind: str, k: int):
+    """Template body (vertices, faces, edges), built once: kind 'ico' with
+    subdivision level k, or 'torus' with k x max(4, k // 2) quads (scaled by
+    1 / 1.35 to about unit radius)."""
+    if kind == "ico":
+        V, F = icosphere(k)
+    else:
+        V, F = torus(k, max(4, k // 2))
+        V = V / 1.35
+    V.setflags(write=False)
+    F.setflags(write=False)
+    E = edges_of(F)
+    E.setflags(write=False)
+    return V, F, E
+
+
 def rigid_environment(seed: int, tri_lo: float = 500, tri_hi: float = 50000, vmax: float = 0.05) -> Scene:
     """One environment: rigid icospheres (levels 1-3) and tori added until a
     total triangle count drawn log-uniformly from [tri_lo, tri_hi] is reached,
@@ -306,18 +324,16 @@ def rigid_environment(seed: int, tri_lo: float = 500, tri_hi: float = 50000, vma
     total = 0
     while total < target or not bodies:
         if rng.random() < 0.5:
-            Vb, Fb = icosphere(int(rng.integers(1, 4)))
+            b = _body("ico", int(rng.integers(1, 4)))
         else:
-            n = int(rng.integers(6, 25))
-            Vb, Fb = torus(n, max(4, n // 2))
-            Vb = Vb / 1.35
-        bodies.append((Vb, Fb))
-        total += len(Fb)
+            b = _body("torus", int(rng.integers(6, 25)))
+        bodies.append(b)
+        total += len(b[1])
     nb = len(bodies)
     side = max(1.0, 1.1 * nb ** (1.0 / 3.0))
-    Vs0, Vs1, Fs = [], [], []
+    Vs0, Vs1, Fs, Es = [], [], [], []
     off = 0
-    for Vb, Fb in bodies:
+    for Vb, Fb, Eb in bodies:
         Rm = _random_rotation(rng)
         sc = rng.uniform(0.2, 0.5)
         pos = rng.uniform(0, side, 3)
@@ -327,12 +343,16 @@ def rigid_environment(seed: int, tri_lo: float = 500, tri_hi: float = 50000, vma
         Vs0.append(P)
         Vs1.append(P + vel)
         Fs.append(Fb + off)
+        Es.append(Eb + off)
         off += len(Vb)
     V0 = np.concatenate(Vs0, 0)
     V1 = np.concatenate(Vs1, 0)
     F = np.concatenate(Fs, 0).astype(np.int32)
-    return Scene(V0, V1, edges_of(F), F, {"name": "rigid-environment", "seed": seed, "bodies": nb,
-                                           "triangles": len(F)})
+    # bodies own disjoint, increasing vertex ranges: the per-body sorted edge
+    # lists concatenate to the sorted edge list of the whole environment
+    E = np.concatenate(Es, 0).astype(np.int32)
+    return Scene(V0, V1, E, F, {"name": "rigid-environment", "seed": seed, "bodies": nb,
+                                "triangles": len(F)})
 
 
 def concat_scenes(scs):
@@ -351,3 +371,33 @@ def concat_scenes(scs):
     E = np.concatenate([s.E.astype(np.int64) + voff[k] for k, s in enumerate(scs)], 0).astype(np.int32)
     F = np.concatenate([s.F.astype(np.int64) + voff[k] for k, s in enumerate(scs)], 0).astype(np.int32)
     return V0, V1, E.reshape(-1, 2), F.reshape(-1, 3), voff, eoff, foff
+
+
+def cloth_and_bodies(n: int = 512, n_ico: int = 500, n_torus: int = 500, seed: int = 1, body_seed: int = 0) -> Scene:
+    """The folded cloth plus rigid bodies: n_ico icospheres (level 4, 5,120
+    triangles) and n_torus tori (48 x 32 quads, 3,072 triangles) placed
+    uniformly in [0, 10]^3 with random rotation and scale 0.2-0.5, each
+    translated by U(-0.02, 0.02)^3 over the step (500 + 500 bodies: 4,096,000
+    body triangles)."""
+    cl = folded_cloth(n, seed=seed)
+    rng = np.random.default_rng(body_seed)
+    ico = _body("ico", 4)
+    Vt, Ft = torus(48, 32)
+    Vt = Vt / 1.35
+    tor = (Vt, Ft, edges_of(Ft))
+    Vs0, Vs1, Fs, Es = [cl.V0], [cl.V1], [cl.F], [cl.E]
+    off = len(cl.V0)
+    for Vb, Fb, Eb in [ico] * n_ico + [tor] * n_torus:
+        Rm = _random_rotation(rng)
+        sc = rng.uniform(0.2, 0.5)
+        pos = rng.uniform(0.0, 10.0, 3)
+        d = rng.uniform(-0.02, 0.02, 3)
+        P = (Vb @ Rm.T) * sc + pos
+        Vs0.append(P)
+        Vs1.append(P + d)
+        Fs.append(Fb + off)
+        Es.append(Eb + off)
+        off += len(Vb)
+    return Scene(np.concatenate(Vs0, 0), np.concatenate(Vs1, 0), np.concatenate(Es, 0).astype(np.int32),
+                 np.concatenate(Fs, 0).astype(np.int32),
+                 {"name": "cloth-and-bodies", "n": n, "icospheres": n_ico, "tori": n_torus})

@@ -57,7 +57,8 @@ def test_struct_layouts_match_binding():
     from paper_2112_06300_gb300 import ccd
     d = tempfile.mkdtemp()
     src = os.path.join(d, "s.c")
-    structs = (ccd.ccd_opts, ccd.ccd_stats, ccd.ccd_tuning)
+    structs = (ccd.ccd_opts, ccd.ccd_stats, ccd.ccd_tuning, ccd.ccd_memory_model, ccd.ccd_server_opts,
+               ccd.ccd_server_stats)
     lines = []
     for st in structs:
         lines.append(f'printf("%zu\\n", sizeof({st.__name__}));')
