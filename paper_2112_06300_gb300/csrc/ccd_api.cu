@@ -101,7 +101,6 @@ __global__ void k_reset_narrow(DevCtl *c) {
   c->n_donated = 0;
   c->n_intervals_tail = 0;
   c->n_intervals_fp64 = 0;
-  c->n_idle = 0;
 }
 __global__ void k_reset_status(DevCtl *c) { c->status = CCD_OK; }
 

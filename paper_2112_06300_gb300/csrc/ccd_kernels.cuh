@@ -27,7 +27,6 @@ struct DevCtl {
   unsigned long long n_donated;  // subtrees passed between lanes of a warp
   unsigned long long n_intervals_tail;  // intervals evaluated after the query list ran out
   unsigned long long n_intervals_fp64;  // intervals the FP32 filter could not decide
-  long long n_idle;              // warps of the narrow kernel waiting for work
   int rerun;                     // zero-TOI rule: 1 when the second pass must run
   int pad_;
   // strip sweep

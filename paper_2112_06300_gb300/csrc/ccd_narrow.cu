@@ -604,7 +604,6 @@ __device__ __forceinline__ void load_record_stage(QueryData &Q, bool &vf, const 
 
 constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a warp retires
 constexpr int kRefresh = 8;            // iterations between reads of the shared values
-constexpr int kExportEvery = 4;        // iterations between hand-offs to idle warps
 
 // Control flow is warp-uniform at the loop level: refill, idling and exit are
 // decided for the whole warp (ballots and broadcasts), and the per-lane work
@@ -651,9 +650,6 @@ k_narrow(NarrowArgs A) {
   unsigned long long pf_toi = kInfBits, pf_qnext = 0;          // lane 0: values in use
   unsigned long long nx_toi = kInfBits, nx_qnext = 0;          // lane 0: loads in flight
   unsigned long long pf_occ = 0, nx_head = 0, nx_tail = 0;     // lane 0: ring occupancy
-  long long pf_idle = 0, nx_idle = 0;                          // lane 0: idle warps
-  bool am_idle = false;                      // warp-uniform: counted in ctl->n_idle
-  int exp_age = 0;                           // warp-uniform: iterations since a forced hand-off
   unsigned long long nx_scene = kInfBits;                      // per lane
   int pf_age = 0;
   if (lane == 0) {
@@ -895,19 +891,12 @@ k_narrow(NarrowArgs A) {
         const unsigned long long pend = ld_relaxed_u64(&ctl->pending);
         pf_occ = t > h ? t - h : 0;   // an idle warp sees new exports at once
         stop = (exhausted && pf_occ == 0 && pend == 0) || ++idle_rounds > kIdleRounds;
-        if (!am_idle && !stop) atomicAdd((unsigned long long *)&ctl->n_idle, 1ull);
-        if (am_idle && stop) atomicAdd((unsigned long long *)&ctl->n_idle, ~0ull);
       }
-      am_idle = true;
       if (__shfl_sync(FULL, stop, 0)) break;
       __nanosleep(1000);
       continue;
     }
     idle_rounds = 0;
-    if (am_idle) {
-      if (lane == 0) atomicAdd((unsigned long long *)&ctl->n_idle, ~0ull);
-      am_idle = false;
-    }
 
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
@@ -969,13 +958,11 @@ k_narrow(NarrowArgs A) {
         pf_toi = nx_toi;
         pf_qnext = nx_qnext;
         pf_occ = nx_tail > nx_head ? nx_tail - nx_head : 0;
-        pf_idle = nx_idle;
         if (pf_occ > 0) atomicMax(&ctl->queue_peak, pf_occ);
         nx_toi = ld_relaxed_u64(&ctl->toi_bits);
         nx_qnext = ld_relaxed_u64(&ctl->q_next);
         nx_head = ld_relaxed_u64(&ctl->q_head);
         nx_tail = ld_relaxed_u64(&ctl->q_tail);
-        nx_idle = (long long)ld_relaxed_u64((const unsigned long long *)&ctl->n_idle);
       }
       if (A.mode == 2) {
         pf_scene = nx_scene;
@@ -1105,18 +1092,7 @@ k_narrow(NarrowArgs A) {
     // ---- 6. in the tail phase, hand the shallowest pending sibling to the
     //         ring every `budget` evaluations; one reservation per warp -------
     {
-      // while warps sit idle and the ring holds fewer than a few items for
-      // each, every kExportEvery iterations each lane with a pending sibling
-      // hands it off (lanes that share subtrees within the warp rarely reach
-      // the per-unit budget)
-      bool hungry = false;
-      if (tail_phase) {
-        const long long iw = __shfl_sync(FULL, pf_idle, 0);
-        const unsigned long long occ = __shfl_sync(FULL, pf_occ, 0);
-        hungry = ++exp_age >= kExportEvery && iw > 0 && occ < 4ull * (unsigned long long)iw;
-        if (hungry) exp_age = 0;
-      }
-      const bool want_exp = have && !unit_end && tail_phase && (since >= A.budget || hungry);
+      const bool want_exp = have && !unit_end && tail_phase && since >= A.budget;
       if (__any_sync(FULL, want_exp)) {
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
@@ -1217,7 +1193,6 @@ __global__ void k_nozero_prepare(DevCtl *ctl) {
     ctl->pending = 0;
     ctl->toi_bits = kInfBits;
     ctl->t_start = ctl->t_exhausted = ctl->t_end = 0;
-    ctl->n_idle = 0;
   }
 }
 
