@@ -16,12 +16,16 @@ struct DevCtl {
   double var_sum[6];             // sum of centres and squared centres per axis
   int axis;
   int status;                    // CCD_* raised by kernels (first error wins)
-  // narrow phase
-  unsigned long long q_next;     // next query to hand out
-  unsigned long long q_head, q_tail;  // ring positions (monotonic, never reset)
-  unsigned long long pending;    // units fetched or queued and not finished
-  unsigned long long toi_bits;   // earliest t* so far, bits of a non-negative double
-  unsigned long long n_intervals, n_exported, n_capped, queue_peak;
+  // narrow phase: the words every warp reads or updates sit on their own
+  // 128-byte lines, so that atomics on one do not queue behind traffic on
+  // another
+  alignas(128) unsigned long long q_next;   // next query to hand out
+  alignas(128) unsigned long long q_head;   // ring positions (monotonic, never reset;
+  unsigned long long q_tail;                // adjacent: cleared together)
+  alignas(128) unsigned long long pending;  // units fetched or queued and not finished
+  alignas(128) unsigned long long toi_bits; // earliest t* so far, bits of a non-negative double
+  alignas(128) unsigned long long n_intervals;
+  unsigned long long n_exported, n_capped, queue_peak;
   long long pair_counts[2];      // ccd_step: pairs for the narrow phase (clamped)
   unsigned long long t_start, t_exhausted, t_end;  // %globaltimer stamps of the narrow kernel
   unsigned long long n_donated;  // subtrees passed between lanes of a warp

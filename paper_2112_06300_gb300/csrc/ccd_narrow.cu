@@ -103,12 +103,17 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     //   tm = e + eps + e32  (beyond it, the FP64 hull misses or sticks out of C)
     //   wn = (delta (1 + 2^-50) + 2 eps + 2 e32)(1 + 2^-23)  (an FP32 width at or
     //        above it means an FP64 width at or above delta)
-    const double m32 = fmax(__longlong_as_double((long long)m), 0x1p-100);
-    const double e32 = (double)__double2float_ru(__dmul_ru(m32, 40.0 * 0x1p-24));
-    Q.e32[x] = (float)e32;
-    Q.tm[x] = __double2float_ru(__dadd_ru(__dadd_ru(e, eps), e32));
-    const double wn = __dadd_ru(__dadd_ru(__dmul_ru(delta, 1.0 + 0x1p-50), __dmul_ru(2.0, eps)), __dmul_ru(2.0, e32));
-    Q.wn[x] = __double2float_ru(__dmul_ru(wn, 1.0 + 0x1p-23));
+    // (evaluated in single precision, every operation rounded upward, so each
+    // threshold is at least its exact value; delta (1 + 2^-50) is bounded by
+    // delta (1 + 2^-23))
+    const float m32 = fmaxf(__double2float_ru(__longlong_as_double((long long)m)), 0x1p-100f);
+    const float e32 = __fmul_ru(m32, 40.0f * 0x1p-24f);
+    const float eps32 = __double2float_ru(eps), e_32 = __double2float_ru(e);
+    Q.e32[x] = e32;
+    Q.tm[x] = __fadd_ru(__fadd_ru(e_32, eps32), e32);
+    const float d32 = __fmul_ru(__double2float_ru(delta), 1.0f + 0x1p-23f);
+    const float wn = __fadd_ru(__fadd_ru(d32, __fmul_ru(2.0f, eps32)), __fmul_ru(2.0f, e32));
+    Q.wn[x] = __fmul_ru(wn, 1.0f + 0x1p-23f);
     double st = __dadd_rn(dabs_int(Q.dc[0][x]), dabs_int(Q.dc[1][x]));
     st = __dadd_rn(st, dabs_int(Q.dc[2][x]));
     unsigned long long sb = dbits(st);
@@ -602,7 +607,8 @@ __device__ __forceinline__ void load_record_stage(QueryData &Q, bool &vf, const 
 
 }  // namespace
 
-constexpr int kIdleRounds = 1 << 14;   // idle warp rounds (~1 us naps) before a warp retires
+constexpr int kIdleRounds = 1 << 14;   // idle warp rounds before a warp retires
+constexpr unsigned kNapMin = 500, kNapMax = 8000;   // idle back-off bounds (ns)
 constexpr int kRefresh = 8;            // iterations between reads of the shared values
 
 // Control flow is warp-uniform at the loop level: refill, idling and exit are
@@ -643,6 +649,7 @@ k_narrow(NarrowArgs A) {
   unsigned flags = 0;
   long long n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0, n_eval64 = 0;
   int idle_rounds = 0;
+  unsigned nap = kNapMin;                    // warp-uniform: idle back-off (ns)
   // Shared values (global t*, next query, the scene's t*) are read from L2
   // every kRefresh iterations into a second register and used from the
   // first, so that no iteration waits for an L2 round trip; stale values
@@ -893,10 +900,12 @@ k_narrow(NarrowArgs A) {
         stop = (exhausted && pf_occ == 0 && pend == 0) || ++idle_rounds > kIdleRounds;
       }
       if (__shfl_sync(FULL, stop, 0)) break;
-      __nanosleep(1000);
+      __nanosleep(nap);          // back off while nothing turns up
+      nap = min(2 * nap, kNapMax);
       continue;
     }
     idle_rounds = 0;
+    nap = kNapMin;
 
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
@@ -1082,7 +1091,11 @@ k_narrow(NarrowArgs A) {
         int a = last_axis(K, N);
         if ((N.n(a) & 1) == 0) {
           N.add(a, 1);
-          break;
+          // a right sibling that would be pruned, or that lies outside the
+          // vertex-face simplex, is done at once (no iteration spent on it)
+          const bool pruned = dbits(dyadic(N.n0, N.l0)) >= cut;
+          const bool outside = vf && dbits(dyadic(N.n1, N.l1)) > dbits(dyadic((1ull << N.l2) - N.n2, N.l2));
+          if (!pruned && !outside) break;
         }
         N.up(a);
         depth -= 1;
