@@ -649,6 +649,7 @@ k_narrow(NarrowArgs A) {
   unsigned flags = 0;
   long long n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0, n_eval64 = 0;
   int idle_rounds = 0;
+  unsigned ended_acc = 0;                    // warp-uniform: ended units not yet subtracted from pending
   unsigned nap = kNapMin;                    // warp-uniform: idle back-off (ns)
   // Shared values (global t*, next query, the scene's t*) are read from L2
   // every kRefresh iterations into a second register and used from the
@@ -892,6 +893,11 @@ k_narrow(NarrowArgs A) {
 
     // ---- 2. a warp with no work idles or retires (uniform) ----------------
     if (__ballot_sync(FULL, have) == 0) {
+      if (ended_acc) {
+        if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)ended_acc));
+        ended_acc = 0;
+        __threadfence();
+      }
       int stop = 0;
       if (lane == 0) {
         const unsigned long long h = ld_relaxed_u64(&ctl->q_head), t = ld_relaxed_u64(&ctl->q_tail);
@@ -1006,6 +1012,8 @@ k_narrow(NarrowArgs A) {
           W.up(a);
         }
         tq = m < tq ? m : tq;
+        if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);       // (modes 1, 2: as an accept)
+        if (A.mode == 2) atomicMin(&A.toi_scene[sid], tq);
         flags |= CCD_FLAG_ITER_CAP;
         ++n_cap;
         --cnt;
@@ -1149,19 +1157,25 @@ k_narrow(NarrowArgs A) {
 
     // ---- 7. finish the unit ------------------------------------------------
     if (have && unit_end) {
-      if (tq != kInfBits) {
+      // (modes 1 and 2 published every accept already: t* and the scene's
+      // t*; the global t* of mode 2 and the per-pair result of mode 0 here)
+      if (tq != kInfBits && A.mode != 1) {
         if (A.mode == 0)
           atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
-        if (A.mode == 2) atomicMin(&A.toi_scene[sid], tq);
         atomicMin(&ctl->toi_bits, tq);
       }
       if (flags) atomicOr(&A.qflags[q], flags);
       if (!whole && cnt) atomicAdd(&A.qiters[q], (unsigned long long)cnt);
       have = false;
     }
-    // one pending decrement per warp for all units that ended
-    const unsigned ended = __ballot_sync(FULL, unit_end);
-    if (lane == 0 && ended) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)__popc(ended)));
+    // units that ended: one pending decrement per warp for 64 of them (the
+    // count stays an over-estimate until the warp flushes, at the latest
+    // before it idles)
+    ended_acc += __popc(__ballot_sync(FULL, unit_end));
+    if (ended_acc >= 64) {
+      if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)ended_acc));
+      ended_acc = 0;
+    }
   }
 
   if (n_eval) atomicAdd(&ctl->n_intervals, (unsigned long long)n_eval);

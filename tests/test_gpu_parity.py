@@ -158,6 +158,15 @@ def test_narrow_max_iter_zero(ctx, ccd):
     np.testing.assert_array_equal(g.view(np.uint64), t.view(np.uint64))
 
 
+def test_narrow_earliest_mode_capped(ctx, ccd):
+    """max_iter = 0 caps every query at its root, whose left end is 0: the
+    capped value must reach the earliest time in mode 1 as in mode 0."""
+    sc, vf, ee = _stress(300, 3)
+    for mode in (0, 1):
+        r, o = _narrow_both(ctx, ccd, sc, vf, ee, max_iter=0, mode=mode)
+        assert r.toi_min == o[4] == 0.0
+
+
 def test_narrow_earliest_mode(ctx, ccd):
     for s in SCENES[:4]:
         ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
