@@ -40,6 +40,12 @@ struct ccd_ctx {
   int *bsid = nullptr, *saxis = nullptr;
   float *ssum = nullptr;
   uint32_t *smm = nullptr;
+  // FP64 strip sweep buffers, sized for cap_boxes boxes (allocated on first use)
+  int64_t cap_strips64 = 0;
+  void *strips64_mem = nullptr;
+  uint32_t *c_box = nullptr, *c_seg = nullptr, *s_seg = nullptr;
+  long long *s_key64 = nullptr, *s_ahi64c = nullptr;
+  longlong2 *s_oth64c = nullptr;
   StripParam *sparam_sc = nullptr;             // strip layout per scene (batched scenes)
   RingCell *ring = nullptr;
   unsigned long long ring_cap = 0;
@@ -206,6 +212,29 @@ int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
   return CCD_OK;
 }
 
+int ensure_strips64(ccd_ctx *c) {
+  const int64_t capc = c->bb.cap_copies;
+  if (capc <= c->cap_strips64) return CCD_OK;
+  if (c->strips64_mem) CK(cudaFree(c->strips64_mem));
+  c->strips64_mem = nullptr;
+  c->cap_strips64 = 0;
+  size_t bytes = 0;
+  auto take = [&](size_t n) { size_t off = bytes; bytes += (n + 255) & ~size_t(255); return off; };
+  const size_t o_box = take(capc * 4), o_seg = take(capc * 4), o_sseg = take(capc * 4);
+  const size_t o_key = take(capc * 8), o_ahi = take(capc * 8), o_oth = take(2 * capc * sizeof(longlong2));
+  char *m = nullptr;
+  CK(cudaMalloc(&m, bytes));
+  c->strips64_mem = m;
+  c->c_box = (uint32_t *)(m + o_box);
+  c->c_seg = (uint32_t *)(m + o_seg);
+  c->s_seg = (uint32_t *)(m + o_sseg);
+  c->s_key64 = (long long *)(m + o_key);
+  c->s_ahi64c = (long long *)(m + o_ahi);
+  c->s_oth64c = (longlong2 *)(m + o_oth);
+  c->cap_strips64 = capc;
+  return CCD_OK;
+}
+
 int ensure_scenes(ccd_ctx *c, int64_t nB, int64_t n_scenes) {
   if (nB > c->cap_bsid) {
     if (c->bsid) CK(cudaFree(c->bsid));
@@ -312,7 +341,24 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   const bool fp64 = c->opts.broad_fp64 != 0;
   // sweep: 0 strips, 1 warp per box, 2 tiled over one sorted list
   // (the strip keys hold 16 bits of scene index: more scenes take the tiled sweep)
-  const int sweep = fp64 ? 1 : (c->opts.sweep_kernel == 0 && sc.n > 65536 ? 2 : c->opts.sweep_kernel);
+  // sweep: 0 strips, 1 warp per box, 2 tiled over one sorted list (the FP64
+  // form has strips and warp per box; more than 65,536 scenes take the tiled
+  // sweep: the strip keys hold 16 bits of scene index)
+  int sweep = c->opts.sweep_kernel;
+  if (fp64 && sweep == 2) sweep = 1;
+  if (!fp64 && sweep == 0 && sc.n > 65536) sweep = 2;
+  const bool strips64 = fp64 && sweep == 0;
+  B.strips_fp64 = strips64 ? 1 : 0;
+  if (strips64 && !c->capturing) {
+    rc = ensure_strips64(c);
+    if (rc) return rc;
+  }
+  B.c_box = c->c_box;
+  B.c_seg = c->c_seg;
+  B.s_seg = c->s_seg;
+  B.s_key64 = c->s_key64;
+  B.s_ahi64c = c->s_ahi64c;
+  B.s_oth64c = c->s_oth64c;
   const int nbuild = (int)cdiv(nB, kBuildThreads);
   mark(c, CCD_STAGE_BOXES, true, s);
   if (sc.n > 0) {
@@ -333,7 +379,24 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   int sbits = 0;   // bits of the scene index in the keys of batched scenes
   while ((1ll << sbits) < sc.n) ++sbits;
   const unsigned long long *s_key = nullptr;
-  if (sweep == 0) {
+  if (strips64) {
+    // FP64 strips: copies sorted by the ordered FP64 minimum (64 bits), then
+    // stably by strip segment (16 bits)
+    const int nblk = (int)cdiv(nB, kCopyBlock);
+    k_count_copies<<<nblk, kCopyBlock, 0, s>>>(nB, B);
+    k_scan_copies<<<1, 1024, 0, s>>>(nblk, nB, B, c->ctl);
+    k_expand_copies64<<<grid, 256, 0, s>>>(nB, B, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
+    const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, B.hist, s, 64, &c->ctl->n_copies);
+    const int cgrid = (int)std::min<int64_t>(cdiv(B.cap_copies, 256), (int64_t)c->sm_count * 8);
+    uint32_t *ka = (uint32_t *)B.keys[cur ^ 1];
+    void *k2[2] = {ka, ka + B.cap_copies};
+    uint32_t *v2[2] = {B.vals[cur], B.vals[cur ^ 1]};
+    k_gather_seg<<<cgrid, 256, 0, s>>>(B.cap_copies, c->ctl, B.vals[cur], B.c_seg, ka);
+    const int cur2 = radix_sort(k2, v2, 4, B.cap_copies, B.hist, s, 16, &c->ctl->n_copies);
+    k_gather_copies64<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, v2[cur2]);
+    sort_passes = 8 + 2;
+    extra = 3;
+  } else if (sweep == 0) {
     const int nblk = (int)cdiv(nB, kCopyBlock);
     k_count_copies<<<nblk, kCopyBlock, 0, s>>>(nB, B);
     k_scan_copies<<<1, 1024, 0, s>>>(nblk, nB, B, c->ctl);
@@ -392,7 +455,16 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.sup_cap = c->sup_cap;
   const int sgrid = (int)std::min<int64_t>(cdiv(nB * 32, 256), (int64_t)c->sm_count * 32);
   mark(c, CCD_STAGE_SWEEP, true, s);
-  if (fp64)
+  A.s_seg = B.s_seg;
+  A.s_key64 = B.s_key64;
+  A.s_ahi64c = B.s_ahi64c;
+  A.s_oth64c = B.s_oth64c;
+  if (strips64) {
+    k_sweep_strips64<<<(unsigned)std::min<int64_t>(cdiv(B.cap_copies, 256), (int64_t)c->sm_count * 16), 128, 0, s>>>(
+        A);
+    k_exact_filter<<<(unsigned)std::min<int64_t>(cdiv(c->sup_cap, 2048), (int64_t)c->sm_count * 8), 256, 0, s>>>(A);
+    extra += 1;
+  } else if (fp64)
     k_sweep64<<<sgrid, 256, 0, s>>>(A);
   else if (sweep == 1)
     k_sweep<<<sgrid, 256, 0, s>>>(A);
@@ -602,6 +674,7 @@ int ccd_destroy(ccd_ctx *c) {
   cudaFree(c->ssum);
   cudaFree(c->saxis);
   cudaFree(c->smm);
+  cudaFree(c->strips64_mem);
   cudaFree(c->sparam_sc);
   cudaFree(c->ring);
   if (c->g_step.valid) cudaGraphExecDestroy(c->g_step.exec);
@@ -716,6 +789,10 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     if (rc) return rc;
     rc = ensure_broad(c, nV + nE + nF);
     if (rc) return rc;
+    if (c->opts.broad_fp64 && c->opts.sweep_kernel == 0) {
+      rc = ensure_strips64(c);
+      if (rc) return rc;
+    }
     if (!host_out) {
       if (!c->opts.use_graph) return enqueue(s);
       struct {

@@ -462,8 +462,13 @@ __device__ __forceinline__ int box_scene(const BroadBufs &B, int64_t b) { return
 __device__ __forceinline__ void box_strips(const BroadBufs &B, int64_t nB, int64_t b, const StripParam &p, int &s0,
                                            int &s1) {
   const int a1 = (p.axes >> 2) & 3;
-  s0 = strip_of(B.lo32[a1 * nB + b], p);
-  s1 = strip_of(B.hi32[a1 * nB + b], p);
+  if (B.strips_fp64) {
+    s0 = strip_of64(f64_from_ord(B.lo64[a1 * nB + b]), p);
+    s1 = strip_of64(f64_from_ord(B.hi64[a1 * nB + b]), p);
+  } else {
+    s0 = strip_of(B.lo32[a1 * nB + b], p);
+    s1 = strip_of(B.hi32[a1 * nB + b], p);
+  }
 }
 
 // Copies per box and their exclusive prefix within each block of kCopyBlock
@@ -579,6 +584,62 @@ __global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, cons
     B.s_ahi[i] = B.hi32[a * nB + b];
     B.s_oth[i] = make_float4(lo1, B.hi32[a1 * nB + b], B.lo32[a2 * nB + b], B.hi32[a2 * nB + b]);
     const bool first = fallback || strip == strip_of(lo1, p);
+    const int4 v = B.vid[b];
+    B.s_vid[i] = make_int4(v.x, v.y, v.z, (int)((uint32_t)b | (first ? 0x80000000u : 0u)));
+  }
+}
+
+// FP64 form of the strip layout.  Copies carry the ordered FP64 minimum on
+// the sweep axis (as an unsigned key) and their strip segment; two stable
+// radix sorts order them by the key and then by the segment.
+__global__ void k_expand_copies64(int64_t nB, BroadBufs B, const DevCtl *ctl, unsigned long long *keys,
+                                  uint32_t *vals) {
+  const bool fallback = ctl->strip_fallback != 0;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nB; b += (int64_t)gridDim.x * blockDim.x) {
+    const int sid = box_scene(B, b);
+    const StripParam p = B.sparam[sid];
+    const uint32_t seg = B.n_scenes > 0 ? ((uint32_t)sid << 16) : 0u;
+    const unsigned long long k = (unsigned long long)B.lo64[(p.axes & 3) * nB + b] ^ 0x8000000000000000ull;
+    int s0 = 0, s1 = 0;
+    int64_t o = b;
+    if (!fallback) {
+      box_strips(B, nB, b, p, s0, s1);
+      o = (int64_t)(B.c_blk[b / kCopyBlock] + B.c_local[b]);
+    }
+    for (int t = s0; t <= s1; ++t) {
+      keys[o + (t - s0)] = k;
+      vals[o + (t - s0)] = (uint32_t)(o + (t - s0));
+      B.c_box[o + (t - s0)] = (uint32_t)b;
+      B.c_seg[o + (t - s0)] = seg | (uint32_t)t;
+    }
+  }
+}
+
+__global__ void k_gather_seg(int64_t cap, const DevCtl *ctl, const uint32_t *perm, const uint32_t *seg,
+                             uint32_t *out) {
+  const int64_t n = (int64_t)ctl->n_copies;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = seg[perm[i]];
+}
+
+__global__ void k_gather_copies64(int64_t nB, BroadBufs B, const DevCtl *ctl, const uint32_t *perm) {
+  const int64_t n = (int64_t)ctl->n_copies;
+  const bool fallback = ctl->strip_fallback != 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = perm[i];
+    const int64_t b = B.c_box[c];
+    const uint32_t seg = B.c_seg[c];
+    const int sid = B.n_scenes > 0 ? (int)(seg >> 16) : 0;
+    const int strip = (int)(seg & 0xFFFFu);
+    const StripParam p = B.sparam[sid];
+    const int a = p.axes & 3, a1 = (p.axes >> 2) & 3, a2 = (p.axes >> 4) & 3;
+    const long long lo1 = B.lo64[a1 * nB + b];
+    B.s_seg[i] = seg;
+    B.s_key64[i] = B.lo64[a * nB + b];
+    B.s_ahi64c[i] = B.hi64[a * nB + b];
+    B.s_oth64c[2 * i] = make_longlong2(lo1, B.hi64[a1 * nB + b]);
+    B.s_oth64c[2 * i + 1] = make_longlong2(B.lo64[a2 * nB + b], B.hi64[a2 * nB + b]);
+    const bool first = fallback || strip == strip_of64(f64_from_ord(lo1), p);
     const int4 v = B.vid[b];
     B.s_vid[i] = make_int4(v.x, v.y, v.z, (int)((uint32_t)b | (first ? 0x80000000u : 0u)));
   }
@@ -917,6 +978,122 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
                           (oi[0].x <= oj.y) & (oj.z <= oi[0].w) & (oi[0].z <= oj.w);
           const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & (fi[1] | fj) & (oj.x <= oi[1].y) &
                           (oi[1].x <= oj.y) & (oj.z <= oi[1].w) & (oi[1].z <= oj.w);
+          bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
+        }
+        if (__any_sync(0xFFFFFFFFu, bits)) {
+#pragma unroll
+          for (int bb = 0; bb < 8; ++bb) {
+            bool keep = false;
+            uint2 pr = make_uint2(0u, 0u);
+            if ((bits >> bb) & 1u) {
+              const int r = bb & 1;
+              int4 vj = sh_vid[k + (bb >> 1)];
+              vj.w &= 0x7FFFFFFF;
+              bool vf;
+              int p0, p1;
+              if (candidate(vi[r], ki[r], vj, A.nV, A.nE, vf, p0, p1)) {
+                keep = true;
+                pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)p1);
+              }
+            }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+            if (m) {
+              if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
+              if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
+              nbuf += __popc(m);
+              __syncwarp();
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (nbuf) sup_flush(A, buf, nbuf);
+}
+
+// FP64 strip sweep: k_sweep_strips on the FP64 extents (ordered int64 keys,
+// exact comparisons).  A copy's range ends at the first copy with a larger
+// (segment, minimum) than (its segment, its maximum).
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
+  __shared__ longlong2 sh_oth[kTJ][2];
+  __shared__ int4 sh_vid[kTJ];
+  __shared__ uint2 sh_sup[kSweepThreads / 32][kSupBuf];
+  __shared__ unsigned long long sh_end;
+  const int64_t n = (int64_t)*A.n_dev;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint2 *buf = sh_sup[wid];
+  int nbuf = 0;
+  for (int64_t i0 = (int64_t)blockIdx.x * kTI; i0 < n; i0 += (int64_t)gridDim.x * kTI) {
+    long long ahi[2];
+    longlong2 o1[2], o2[2];
+    int4 vi[2];
+    int ki[2];
+    bool fi[2];
+    const int li[2] = {2 * tid, 2 * tid + 1};
+    int endl[2] = {li[0] + 1, li[1] + 1};
+    int64_t end_max = i0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t i = i0 + li[r];
+      ahi[r] = (long long)0x8000000000000000ull;   // no copy: every test fails
+      o1[r] = o2[r] = make_longlong2(0, 0);
+      vi[r] = make_int4(-1, -1, -1, 0);
+      fi[r] = false;
+      if (i < n) {
+        ahi[r] = A.s_ahi64c[i];
+        o1[r] = A.s_oth64c[2 * i];
+        o2[r] = A.s_oth64c[2 * i + 1];
+        vi[r] = A.s_vid[i];
+        fi[r] = vi[r].w < 0;
+        vi[r].w &= 0x7FFFFFFF;
+        const uint32_t seg = A.s_seg[i];
+        int64_t lo = i + 1, hi = n;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          const uint32_t sm = A.s_seg[mid];
+          if (sm < seg || (sm == seg && A.s_key64[mid] <= ahi[r])) lo = mid + 1; else hi = mid;
+        }
+        endl[r] = (int)(lo - i0);
+        end_max = lo > end_max ? lo : end_max;
+      }
+      ki[r] = box_kind(vi[r].w, A.nV, A.nE);
+    }
+    int wend = max(endl[0], endl[1]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wend = max(wend, __shfl_xor_sync(0xFFFFFFFFu, wend, o));
+    const int wbeg = 64 * wid + 1;
+    if (tid == 0) sh_end = (unsigned long long)i0;
+    __syncthreads();
+    atomicMax(&sh_end, (unsigned long long)end_max);
+    __syncthreads();
+    const int64_t jend = (int64_t)sh_end;
+    const unsigned span0 = (unsigned)(endl[0] - li[0] - 1), span1 = (unsigned)(endl[1] - li[1] - 1);
+    for (int64_t jt = i0 + 1; jt < jend; jt += kTJ) {
+      __syncthreads();
+      for (int k = tid; k < kTJ; k += kSweepThreads) {
+        const int64_t j = jt + k;
+        if (j < n) {
+          sh_oth[k][0] = A.s_oth64c[2 * j];
+          sh_oth[k][1] = A.s_oth64c[2 * j + 1];
+          sh_vid[k] = A.s_vid[j];
+        }
+      }
+      __syncthreads();
+      const int jl0 = (int)(jt - i0);
+      const int kb = max(0, wbeg - jl0) & ~3;
+      const int ke = (int)min((int64_t)min(kTJ, wend - jl0), jend - jt);
+      for (int k = kb; k < ke; k += 4) {
+        unsigned bits = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const longlong2 p1 = sh_oth[k + u][0], p2 = sh_oth[k + u][1];
+          const bool fj = sh_vid[k + u].w < 0;
+          const int jl = jl0 + k + u;
+          const bool h0 = ((unsigned)(jl - li[0] - 1) < span0) & (fi[0] | fj) & (p1.x <= o1[0].y) &
+                          (o1[0].x <= p1.y) & (p2.x <= o2[0].y) & (o2[0].x <= p2.y);
+          const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & (fi[1] | fj) & (p1.x <= o1[1].y) &
+                          (o1[1].x <= p1.y) & (p2.x <= o2[1].y) & (o2[1].x <= p2.y);
           bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
         }
         if (__any_sync(0xFFFFFFFFu, bits)) {

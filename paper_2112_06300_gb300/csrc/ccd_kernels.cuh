@@ -122,6 +122,18 @@ __device__ __forceinline__ int strip_of(float x, const StripParam &p) {
   return t >= (float)(p.nstrips - 1) ? p.nstrips - 1 : (t > 0.f ? (int)t : 0);
 }
 
+// The same for an FP64 coordinate (the FP64 form bins on FP64 extents).
+__device__ __forceinline__ int strip_of64(double x, const StripParam &p) {
+  if (p.nstrips <= 1) return 0;
+  const double t = __dmul_rn(__dsub_rn(x, (double)p.org), (double)p.inv_w);
+  return t >= (double)(p.nstrips - 1) ? p.nstrips - 1 : (t > 0.0 ? (int)t : 0);
+}
+
+// Inverse of the ordered-int64 map of a double (f64_ord).
+__device__ __forceinline__ double f64_from_ord(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFll));
+}
+
 struct BroadBufs {
   // by box id
   float *lo32, *hi32;            // [3][nB]
@@ -153,6 +165,12 @@ struct BroadBufs {
   int64_t cap_copies;            // capacity of the sorted arrays and sort buffers
   uint32_t *c_local;             // [nB] offset of a box's copies within its block
   unsigned long long *c_blk;     // [nB / kCopyBlock + 1] copies per block, then their prefix
+  // FP64 form of the strip sweep (bins and sorts on FP64 extents), [cap_copies] each
+  int strips_fp64;               // 1: strips from the FP64 extents
+  uint32_t *c_box, *c_seg;       // copy -> box id, strip segment
+  uint32_t *s_seg;               // sorted: strip segment
+  long long *s_key64, *s_ahi64c; // sorted: ordered FP64 minimum / maximum on the sweep axis
+  longlong2 *s_oth64c;           // sorted: [2 per copy] the two other axes
 };
 
 constexpr int kStatWords = 15;   // per block: 3 centre sums, 3 squares, 3 widths, 3 min, 3 max
@@ -216,9 +234,19 @@ struct SweepArgs {
   // tested against the FP64 extents by k_exact_filter
   uint2 *sup;
   int64_t sup_cap;
+  // FP64 strip sweep
+  const uint32_t *s_seg;
+  const long long *s_key64, *s_ahi64c;
+  const longlong2 *s_oth64c;
 };
 __global__ void k_sweep(SweepArgs A);
 __global__ void k_sweep_strips(SweepArgs A);
+__global__ void k_sweep_strips64(SweepArgs A);
+__global__ void k_expand_copies64(int64_t nB, BroadBufs B, const DevCtl *ctl, unsigned long long *keys,
+                                  uint32_t *vals);
+__global__ void k_gather_seg(int64_t cap, const DevCtl *ctl, const uint32_t *perm, const uint32_t *seg,
+                             uint32_t *out);
+__global__ void k_gather_copies64(int64_t nB, BroadBufs B, const DevCtl *ctl, const uint32_t *perm);
 __global__ void k_exact_filter(SweepArgs A);
 __global__ void k_sweep_tiled(SweepArgs A);
 __global__ void k_sweep64(SweepArgs A);

@@ -222,10 +222,13 @@ def test_fp64_peak_probe(ccd):
     assert 10.0 < g < 1e6
 
 
+@pytest.mark.parametrize("sweep,width", [(0, 0.0), (0, 0.5), (0, 1e-3), (1, 0.0)],
+                         ids=["strips", "narrow-strips", "strips-overflow", "warp-per-box"])
 @pytest.mark.parametrize("s", [SCENES[0], SCENES[3], SCENES[4]], ids=["icosphere", "cloth97", "random"])
-def test_plain_fp64_form_matches_oracle(ccd, s):
-    # all-FP64 broad phase: 64-bit keys, exact comparisons, no filter stage
-    c = ccd.CCD(0, broad_fp64=1)
+def test_plain_fp64_form_matches_oracle(ccd, s, sweep, width):
+    # all-FP64 broad phase: 64-bit keys, exact comparisons, no single-precision
+    # stage (strips binned on FP64 extents, or one warp per box)
+    c = ccd.CCD(0, broad_fp64=1, sweep_kernel=sweep, strip_width=width)
     try:
         V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
         vf, ee = c.broad(V0, V1, E, F)
