@@ -64,9 +64,10 @@ typedef struct {
     int64_t max_iter;        /* per-query cap on processed intervals; default 1e6 */
     int32_t broad_fp64;      /* 0 (default): single-precision outward-rounded boxes
                                 then an exact FP64 filter; 1: FP64 boxes throughout */
-    int32_t sweep_kernel;    /* 0 (default): strip sweep (boxes are also binned
-                                into strips along a second axis and swept per
-                                strip, each pair reported in one strip only);
+    int32_t sweep_kernel;    /* 0 (default): cell sweep (boxes are also binned
+                                into a grid of cells on the two other axes and
+                                swept per cell, each pair reported in one cell
+                                only);
                                 1: one warp per box, one sorted list (Algorithm 2
                                 as printed); 2: tiled sweep over one sorted list
                                 (a block walks the sweep ranges of 256 boxes
@@ -90,10 +91,10 @@ typedef struct {
                                 (pointers, sizes, parameters) stay the same;
                                 default 0 */
     int32_t pad0;
-    double strip_width;      /* strip sweep: strip width as a multiple of the mean
-                                box width on the strip axis (0 = auto: 2); more
-                                strips mean fewer comparisons but more copies of
-                                boxes that straddle strip borders */
+    double strip_width;      /* cell sweep: cell width as a multiple of the mean
+                                box width on each cell axis (0 = auto: 3); more
+                                cells mean fewer comparisons but more copies of
+                                boxes that straddle cell borders */
 } ccd_opts;
 
 /* Work counters of the last broad/narrow/step call (see ccd_get_status). */
@@ -115,8 +116,8 @@ typedef struct {
     int64_t n_donated;       /* subtrees passed between lanes of one warp */
     int64_t n_intervals_tail;  /* intervals evaluated after every query was taken */
     int64_t n_intervals_fp64;  /* intervals the single-precision filter left to FP64 */
-    int64_t n_box_copies;    /* strip sweep: boxes placed in strips, counting each
-                                strip a box overlaps (n_boxes for the other sweeps) */
+    int64_t n_box_copies;    /* cell sweep: boxes placed in cells, counting each
+                                cell a box overlaps (n_boxes for the other sweeps) */
 } ccd_stats;
 
 /* Fill *o with the defaults. */
@@ -216,9 +217,9 @@ int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t *ee, int64
  * Asynchronous and allocation-free once the context's buffers have grown to
  * the sizes of a first call (it can then be captured in a CUDA graph); an
  * overflow of the pair buffers is reported by ccd_get_status (CCD_ETRUNC).
- * Each scene has its own strip layout under the strip sweep (more than
+ * Each scene has its own cell layout under the cell sweep (more than
  * 65,536 scenes take the tiled sweep).  Requires the single-precision broad
- * phase, the strip or tiled sweep (sweep_kernel 0 or 2), and no zero-TOI rule.
+ * phase, the cell or tiled sweep (sweep_kernel 0 or 2), and no zero-TOI rule.
  */
 int ccd_step_batch(ccd_ctx *ctx, int32_t n_scenes, const int64_t *vert_off, const int64_t *edge_off,
                    const int64_t *face_off, const double *V0, const double *V1, int64_t nV,
@@ -227,9 +228,9 @@ int ccd_step_batch(ccd_ctx *ctx, int32_t n_scenes, const int64_t *vert_off, cons
 
 /* Settings chosen by ccd_autotune. */
 typedef struct {
-    int32_t sweep_kernel;    /* 0 strips or 2 tiled */
+    int32_t sweep_kernel;    /* 0 cells or 2 tiled */
     int32_t export_budget;   /* intervals between hand-offs in the tail phase */
-    double strip_width;      /* strip width in mean box widths (strip sweep) */
+    double strip_width;      /* cell width in mean box widths (cell sweep) */
     int64_t queue_capacity;  /* interval-queue slots */
     double broad_ms;         /* median broad-phase time with the chosen settings */
     double narrow_ms;        /* median narrow-phase time with the chosen settings */
@@ -239,8 +240,8 @@ typedef struct {
 } ccd_tuning;
 
 /*
- * Autotuner: times the broad phase with the strip sweep at strip widths of
- * 0.5-8 mean box widths and with the tiled sweep, then the narrow phase with
+ * Autotuner: times the broad phase with the cell sweep at cell widths of
+ * 1.5-6 mean box widths and with the tiled sweep, then the narrow phase with
  * hand-off budgets of 16-256 intervals, each as the median of `reps` runs on
  * this mesh, and keeps the fastest settings in the context (later calls use
  * them; captured graphs are dropped).  The interval queue then shrinks to the
@@ -265,9 +266,9 @@ int ccd_autotune(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV, c
  * enters bytes_fixed).
  */
 typedef struct {
-    int64_t bytes_per_box;    /* boxes, sort keys, strip copies, sorted arrays */
+    int64_t bytes_per_box;    /* boxes, sort keys, cell copies, sorted arrays */
     int64_t bytes_per_pair;   /* pair, candidate slots, narrow-phase query scratch */
-    int64_t bytes_per_scene;  /* per-scene statistics and strip layout */
+    int64_t bytes_per_scene;  /* per-scene statistics and cell layout */
     int64_t bytes_fixed;      /* control block and interval queue */
 } ccd_memory_model;
 
@@ -292,7 +293,7 @@ enum { CCD_STAGE_BOXES = 0, CCD_STAGE_SORT = 1, CCD_STAGE_SWEEP = 2, CCD_STAGE_N
 
 /* Milliseconds spent in each stage by the last ccd_broad / ccd_narrow /
  * ccd_step call (CUDA events on its stream; boxes = box build and axis
- * choice, sort = keys (strip sweep: copies per strip), radix sort and
+ * choice, sort = keys (cell sweep: copies per cell), radix sort and
  * gather, sweep = sweep with the exact
  * filter, narrow = narrow-phase kernel); stages the call did not run read 0.
  * Synchronizes the stream.  Returns CCD_EINVAL unless profile_stages was set. */

@@ -95,6 +95,7 @@ __global__ void k_reset_broad(DevCtl *c) {
   c->n_copies = 0;
   c->strip_fallback = 0;
   c->sup_overflow = 0;
+  c->copy_oversize = 0;
   for (int i = 0; i < 6; ++i) c->var_sum[i] = 0;
   c->axis = 0;
 }
@@ -337,7 +338,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   B.smm = c->smm;
   B.saxis = c->saxis;
   if (sc.n > 0) B.sparam = c->sparam_sc;
-  B.strip_factor = c->opts.strip_width > 0 ? (float)c->opts.strip_width : 2.0f;
+  B.strip_factor = c->opts.strip_width > 0 ? (float)c->opts.strip_width : 3.0f;
   const bool fp64 = c->opts.broad_fp64 != 0;
   // sweep: 0 strips, 1 warp per box, 2 tiled over one sorted list
   // (the strip keys hold 16 bits of scene index: more scenes take the tiled sweep)
@@ -347,6 +348,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   int sweep = c->opts.sweep_kernel;
   if (fp64 && sweep == 2) sweep = 1;
   if (!fp64 && sweep == 0 && sc.n > 65536) sweep = 2;
+  if (sweep == 0 && nB >= (1ll << 30)) sweep = fp64 ? 1 : 2;   // copies carry 2 flag bits above the box id
   const bool strips64 = fp64 && sweep == 0;
   B.strips_fp64 = strips64 ? 1 : 0;
   if (strips64 && !c->capturing) {
@@ -383,7 +385,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     // FP64 strips: copies sorted by the ordered FP64 minimum (64 bits), then
     // stably by strip segment (16 bits)
     const int nblk = (int)cdiv(nB, kCopyBlock);
-    k_count_copies<<<nblk, kCopyBlock, 0, s>>>(nB, B);
+    k_count_copies<<<nblk, kCopyBlock, 0, s>>>(nB, B, c->ctl);
     k_scan_copies<<<1, 1024, 0, s>>>(nblk, nB, B, c->ctl);
     k_expand_copies64<<<grid, 256, 0, s>>>(nB, B, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
     const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, B.hist, s, 64, &c->ctl->n_copies);
@@ -392,16 +394,16 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     void *k2[2] = {ka, ka + B.cap_copies};
     uint32_t *v2[2] = {B.vals[cur], B.vals[cur ^ 1]};
     k_gather_seg<<<cgrid, 256, 0, s>>>(B.cap_copies, c->ctl, B.vals[cur], B.c_seg, ka);
-    const int cur2 = radix_sort(k2, v2, 4, B.cap_copies, B.hist, s, 16, &c->ctl->n_copies);
+    const int cur2 = radix_sort(k2, v2, 4, B.cap_copies, B.hist, s, 24, &c->ctl->n_copies);
     k_gather_copies64<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, v2[cur2]);
-    sort_passes = 8 + 2;
+    sort_passes = 8 + 3;
     extra = 3;
   } else if (sweep == 0) {
     const int nblk = (int)cdiv(nB, kCopyBlock);
-    k_count_copies<<<nblk, kCopyBlock, 0, s>>>(nB, B);
+    k_count_copies<<<nblk, kCopyBlock, 0, s>>>(nB, B, c->ctl);
     k_scan_copies<<<1, 1024, 0, s>>>(nblk, nB, B, c->ctl);
     k_expand_copies<<<grid, 256, 0, s>>>(nB, B, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
-    const int bits = 48 + (sc.n > 0 ? sbits : 0);
+    const int bits = sc.n > 0 ? 48 + sbits : 56;   // cell index: 16 bits batched, 24 bits alone
     const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, B.hist, s, bits, &c->ctl->n_copies);
     const int cgrid = (int)std::min<int64_t>(cdiv(B.cap_copies, 256), (int64_t)c->sm_count * 8);
     k_gather_copies<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, (const unsigned long long *)B.keys[cur], B.vals[cur]);
@@ -937,7 +939,7 @@ int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     return v[n / 2];
   };
   // 1. sweep: strips of several widths, or one sorted list
-  const double widths[] = {0.5, 1.0, 2.0, 4.0, 8.0};
+  const double widths[] = {1.5, 2.0, 3.0, 4.0, 6.0};
   double best_b = 1e30;
   int best_sweep = 0;
   double best_w = 2.0;

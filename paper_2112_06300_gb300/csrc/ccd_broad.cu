@@ -152,26 +152,36 @@ k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *__restrict__ V0,
   }
 }
 
-// Strip layout of one scene from its statistics: the strip axis is the axis
-// of second-largest centre variance; strips are strip_factor mean box widths
-// wide (at most kMaxStrips strips).
-__device__ StripParam make_strip_param(int a, int a1, double n, double wsum, float org, float top,
-                                       float strip_factor) {
+// Cell layout of one scene from its statistics: on each of the two axes
+// other than the sweep axis, cells strip_factor mean box widths wide (at
+// most max_cells of them).
+__device__ StripParam make_strip_param(int a, int c0, int c1, double n, const double wsum[2], const float org[2],
+                                       const float top[2], float strip_factor, int max_cells) {
   StripParam p;
-  p.axes = a | (a1 << 2) | ((3 - a - a1) << 4);
-  p.org = 0.f;
-  p.inv_w = 0.f;
-  p.nstrips = 1;
-  const double range = (double)top - (double)org;
-  const double mw = n > 0 ? wsum / n : 0.0;
-  const double w = fmax((double)strip_factor * mw, range / kMaxStrips * (1.0 + 1.0 / 1024));
-  if (!(range > 0) || !(w > 0) || !isfinite(range) || !isfinite(w)) return p;
-  const float inv = (float)(1.0 / w);
-  if (!(inv > 0.f) || !isfinite(inv)) return p;
-  p.org = org;
-  p.inv_w = inv;
-  p.nstrips = (int)fmin((double)kMaxStrips, floor(range * (double)inv) + 1.0);
-  if (p.nstrips < 1) p.nstrips = 1;
+  p.axes = a | (c0 << 2) | (c1 << 4);
+  p.pad = 0;
+  for (int k = 0; k < 2; ++k) {
+    p.org[k] = 0.f;
+    p.inv_w[k] = 0.f;
+    p.ncell[k] = 1;
+    const double range = (double)top[k] - (double)org[k];
+    const double mw = n > 0 ? wsum[k] / n : 0.0;
+    const double w = fmax((double)strip_factor * mw, range / max_cells * (1.0 + 1.0 / 1024));
+    if (!(range > 0) || !(w > 0) || !isfinite(range) || !isfinite(w)) continue;
+    const float inv = (float)(1.0 / w);
+    if (!(inv > 0.f) || !isfinite(inv)) continue;
+    p.org[k] = org[k];
+    p.inv_w[k] = inv;
+    p.ncell[k] = (int)fmin((double)max_cells, floor(range * (double)inv) + 1.0);
+    if (p.ncell[k] < 1) p.ncell[k] = 1;
+  }
+  // a thin second axis (fewer than 8 cells) is not binned: its copies would
+  // cost more than the comparisons they save
+  if (p.ncell[1] < 8) {
+    p.ncell[1] = 1;
+    p.inv_w[1] = 0.f;
+    p.org[1] = 0.f;
+  }
   return p;
 }
 
@@ -222,7 +232,10 @@ __global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, De
     int a, b;
     pick_axes(var, a, b);
     ctl->axis = a;
-    sp[0] = make_strip_param(a, b, (double)nB, t[6 + b], (float)t[9 + b], (float)t[12 + b], strip_factor);
+    const int c = 3 - a - b;
+    const double ws[2] = {t[6 + b], t[6 + c]};
+    const float lo[2] = {(float)t[9 + b], (float)t[9 + c]}, hi[2] = {(float)t[12 + b], (float)t[12 + c]};
+    sp[0] = make_strip_param(a, b, c, (double)nB, ws, lo, hi, strip_factor, kMaxCellsSingle);
   }
 }
 
@@ -253,13 +266,18 @@ __global__ void k_axis_select_scenes(BroadBufs B) {
   int a, b;
   pick_axes(var, a, b);
   B.saxis[s] = a;
-  StripParam p;
-  if (n > 0)
-    p = make_strip_param(a, b, n, (double)B.ssum[(6 + b) * ns + s], f32_from_sort_key(B.smm[b * ns + s]),
-                         f32_from_sort_key(B.smm[(3 + b) * ns + s]), B.strip_factor);
-  else
-    p = make_strip_param(a, b, 0.0, 0.0, 0.f, 0.f, B.strip_factor);
-  B.sparam[s] = p;
+  const int c = 3 - a - b;
+  double ws[2] = {0.0, 0.0};
+  float lo[2] = {0.f, 0.f}, hi[2] = {0.f, 0.f};
+  if (n > 0) {
+    ws[0] = (double)B.ssum[(6 + b) * ns + s];
+    ws[1] = (double)B.ssum[(6 + c) * ns + s];
+    lo[0] = f32_from_sort_key(B.smm[b * ns + s]);
+    lo[1] = f32_from_sort_key(B.smm[c * ns + s]);
+    hi[0] = f32_from_sort_key(B.smm[(3 + b) * ns + s]);
+    hi[1] = f32_from_sort_key(B.smm[(3 + c) * ns + s]);
+  }
+  B.sparam[s] = make_strip_param(a, b, c, n, ws, lo, hi, B.strip_factor, kMaxCellsBatched);
 }
 
 // Batched scenes: key = scene << 32 | ordered bits of the minimum on the
@@ -458,30 +476,44 @@ __global__ void k_gather_sorted(int64_t nB, const uint32_t *__restrict__ perm, c
 
 __device__ __forceinline__ int box_scene(const BroadBufs &B, int64_t b) { return B.n_scenes > 0 ? B.bsid[b] : 0; }
 
-// Strips [s0, s1] of box b on its scene's strip axis.
-__device__ __forceinline__ void box_strips(const BroadBufs &B, int64_t nB, int64_t b, const StripParam &p, int &s0,
-                                           int &s1) {
-  const int a1 = (p.axes >> 2) & 3;
-  if (B.strips_fp64) {
-    s0 = strip_of64(f64_from_ord(B.lo64[a1 * nB + b]), p);
-    s1 = strip_of64(f64_from_ord(B.hi64[a1 * nB + b]), p);
-  } else {
-    s0 = strip_of(B.lo32[a1 * nB + b], p);
-    s1 = strip_of(B.hi32[a1 * nB + b], p);
+// Cells [s0[k], s1[k]] of box b on its scene's two cell axes.
+__device__ __forceinline__ void box_cells(const BroadBufs &B, int64_t nB, int64_t b, const StripParam &p, int s0[2],
+                                          int s1[2]) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int x = (p.axes >> (2 + 2 * k)) & 3;
+    if (B.strips_fp64) {
+      s0[k] = strip_of64(f64_from_ord(B.lo64[x * nB + b]), p, k);
+      s1[k] = strip_of64(f64_from_ord(B.hi64[x * nB + b]), p, k);
+    } else {
+      s0[k] = strip_of(B.lo32[x * nB + b], p, k);
+      s1[k] = strip_of(B.hi32[x * nB + b], p, k);
+    }
   }
+}
+
+// A box's copies, capped so that a block's sum fits 32 bits; a box over the
+// cap raises copy_oversize (the layout then falls back to one cell).
+constexpr uint32_t kMaxCopiesPerBox = 1u << 21;
+__device__ __forceinline__ uint32_t cell_count(const int s0[2], const int s1[2], bool &oversize) {
+  const unsigned long long c = (unsigned long long)(s1[0] - s0[0] + 1) * (unsigned long long)(s1[1] - s0[1] + 1);
+  oversize = c > kMaxCopiesPerBox;
+  return oversize ? kMaxCopiesPerBox : (uint32_t)c;
 }
 
 // Copies per box and their exclusive prefix within each block of kCopyBlock
 // boxes; the block totals go to c_blk.
-__global__ void __launch_bounds__(kCopyBlock) k_count_copies(int64_t nB, BroadBufs B) {
+__global__ void __launch_bounds__(kCopyBlock) k_count_copies(int64_t nB, BroadBufs B, DevCtl *ctl) {
   __shared__ uint32_t wsum[kCopyBlock / 32];
   const int64_t b = (int64_t)blockIdx.x * kCopyBlock + threadIdx.x;
   uint32_t n = 0;
   if (b < nB) {
     const StripParam p = B.sparam[box_scene(B, b)];
-    int s0, s1;
-    box_strips(B, nB, b, p, s0, s1);
-    n = (uint32_t)(s1 - s0 + 1);
+    int s0[2], s1[2];
+    box_cells(B, nB, b, p, s0, s1);
+    bool over;
+    n = cell_count(s0, s1, over);
+    if (over) ctl->copy_oversize = 1;
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t x = n;
@@ -534,7 +566,7 @@ __global__ void __launch_bounds__(1024) k_scan_copies(int nblk, int64_t nB, Broa
     __syncthreads();
   }
   if (tid == 0) {
-    const bool fit = carry <= (unsigned long long)B.cap_copies;
+    const bool fit = carry <= (unsigned long long)B.cap_copies && ctl->copy_oversize == 0;
     ctl->strip_fallback = fit ? 0 : 1;
     ctl->n_copies = fit ? carry : (unsigned long long)nB;
   }
@@ -556,13 +588,14 @@ __global__ void k_expand_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, unsi
       vals[b] = (uint32_t)b;
       continue;
     }
-    int s0, s1;
-    box_strips(B, nB, b, p, s0, s1);
-    const unsigned long long o = B.c_blk[b / kCopyBlock] + B.c_local[b];
-    for (int t = s0; t <= s1; ++t) {
-      keys[o + (t - s0)] = ((seg | (unsigned)t) << 32) | k;
-      vals[o + (t - s0)] = (uint32_t)b;
-    }
+    int s0[2], s1[2];
+    box_cells(B, nB, b, p, s0, s1);
+    unsigned long long o = B.c_blk[b / kCopyBlock] + B.c_local[b];
+    for (int t = s0[0]; t <= s1[0]; ++t)
+      for (int u = s0[1]; u <= s1[1]; ++u, ++o) {
+        keys[o] = ((seg | (unsigned)(t * p.ncell[1] + u)) << 32) | k;
+        vals[o] = (uint32_t)b;
+      }
   }
 }
 
@@ -577,15 +610,16 @@ __global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, cons
     const int64_t b = perm[i];
     const unsigned long long key = keys[i];
     const int sid = B.n_scenes > 0 ? (int)(key >> 48) : 0;
-    const int strip = (int)((key >> 32) & 0xFFFFu);
+    const uint32_t cell = B.n_scenes > 0 ? (uint32_t)((key >> 32) & 0xFFFFu) : (uint32_t)(key >> 32);
     const StripParam p = B.sparam[sid];
     const int a = p.axes & 3, a1 = (p.axes >> 2) & 3, a2 = (p.axes >> 4) & 3;
-    const float lo1 = B.lo32[a1 * nB + b];
+    const float lo1 = B.lo32[a1 * nB + b], lo2 = B.lo32[a2 * nB + b];
     B.s_ahi[i] = B.hi32[a * nB + b];
-    B.s_oth[i] = make_float4(lo1, B.hi32[a1 * nB + b], B.lo32[a2 * nB + b], B.hi32[a2 * nB + b]);
-    const bool first = fallback || strip == strip_of(lo1, p);
+    B.s_oth[i] = make_float4(lo1, B.hi32[a1 * nB + b], lo2, B.hi32[a2 * nB + b]);
+    const uint32_t f0 = fallback || (int)(cell / p.ncell[1]) == strip_of(lo1, p, 0);
+    const uint32_t f1 = fallback || (int)(cell % p.ncell[1]) == strip_of(lo2, p, 1);
     const int4 v = B.vid[b];
-    B.s_vid[i] = make_int4(v.x, v.y, v.z, (int)((uint32_t)b | (first ? 0x80000000u : 0u)));
+    B.s_vid[i] = make_int4(v.x, v.y, v.z, (int)((uint32_t)b | (f0 << 31) | (f1 << 30)));
   }
 }
 
@@ -600,18 +634,19 @@ __global__ void k_expand_copies64(int64_t nB, BroadBufs B, const DevCtl *ctl, un
     const StripParam p = B.sparam[sid];
     const uint32_t seg = B.n_scenes > 0 ? ((uint32_t)sid << 16) : 0u;
     const unsigned long long k = (unsigned long long)B.lo64[(p.axes & 3) * nB + b] ^ 0x8000000000000000ull;
-    int s0 = 0, s1 = 0;
+    int s0[2] = {0, 0}, s1[2] = {0, 0};
     int64_t o = b;
     if (!fallback) {
-      box_strips(B, nB, b, p, s0, s1);
+      box_cells(B, nB, b, p, s0, s1);
       o = (int64_t)(B.c_blk[b / kCopyBlock] + B.c_local[b]);
     }
-    for (int t = s0; t <= s1; ++t) {
-      keys[o + (t - s0)] = k;
-      vals[o + (t - s0)] = (uint32_t)(o + (t - s0));
-      B.c_box[o + (t - s0)] = (uint32_t)b;
-      B.c_seg[o + (t - s0)] = seg | (uint32_t)t;
-    }
+    for (int t = s0[0]; t <= s1[0]; ++t)
+      for (int u = s0[1]; u <= s1[1]; ++u, ++o) {
+        keys[o] = k;
+        vals[o] = (uint32_t)o;
+        B.c_box[o] = (uint32_t)b;
+        B.c_seg[o] = seg | (uint32_t)(t * p.ncell[1] + u);
+      }
   }
 }
 
@@ -630,18 +665,19 @@ __global__ void k_gather_copies64(int64_t nB, BroadBufs B, const DevCtl *ctl, co
     const int64_t b = B.c_box[c];
     const uint32_t seg = B.c_seg[c];
     const int sid = B.n_scenes > 0 ? (int)(seg >> 16) : 0;
-    const int strip = (int)(seg & 0xFFFFu);
+    const uint32_t cell = B.n_scenes > 0 ? (seg & 0xFFFFu) : seg;
     const StripParam p = B.sparam[sid];
     const int a = p.axes & 3, a1 = (p.axes >> 2) & 3, a2 = (p.axes >> 4) & 3;
-    const long long lo1 = B.lo64[a1 * nB + b];
+    const long long lo1 = B.lo64[a1 * nB + b], lo2 = B.lo64[a2 * nB + b];
     B.s_seg[i] = seg;
     B.s_key64[i] = B.lo64[a * nB + b];
     B.s_ahi64c[i] = B.hi64[a * nB + b];
     B.s_oth64c[2 * i] = make_longlong2(lo1, B.hi64[a1 * nB + b]);
-    B.s_oth64c[2 * i + 1] = make_longlong2(B.lo64[a2 * nB + b], B.hi64[a2 * nB + b]);
-    const bool first = fallback || strip == strip_of64(f64_from_ord(lo1), p);
+    B.s_oth64c[2 * i + 1] = make_longlong2(lo2, B.hi64[a2 * nB + b]);
+    const uint32_t f0 = fallback || (int)(cell / p.ncell[1]) == strip_of64(f64_from_ord(lo1), p, 0);
+    const uint32_t f1 = fallback || (int)(cell % p.ncell[1]) == strip_of64(f64_from_ord(lo2), p, 1);
     const int4 v = B.vid[b];
-    B.s_vid[i] = make_int4(v.x, v.y, v.z, (int)((uint32_t)b | (first ? 0x80000000u : 0u)));
+    B.s_vid[i] = make_int4(v.x, v.y, v.z, (int)((uint32_t)b | (f0 << 31) | (f1 << 30)));
   }
 }
 
@@ -915,7 +951,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
     float4 oi[2];
     int4 vi[2];
     int ki[2];
-    bool fi[2];
+    unsigned fi[2];
     const int li[2] = {2 * tid, 2 * tid + 1};   // local indices of the thread's two copies
     int endl[2] = {li[0] + 1, li[1] + 1};      // no copy: empty range
     int64_t end_max = i0;
@@ -925,13 +961,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
       ahi[r] = -__int_as_float(0x7F800000);
       oi[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       vi[r] = make_int4(-1, -1, -1, 0);
-      fi[r] = false;
+      fi[r] = 0u;
       if (i < n) {
         ahi[r] = A.s_ahi[i];
         oi[r] = A.s_oth[i];
         vi[r] = A.s_vid[i];
-        fi[r] = vi[r].w < 0;
-        vi[r].w &= 0x7FFFFFFF;
+        fi[r] = ((uint32_t)vi[r].w >> 30) & 3u;   // first cell on each axis
+        vi[r].w &= 0x3FFFFFFF;
         const unsigned long long target = (A.s_key[i] & 0xFFFFFFFF00000000ull) | f32_sort_key(ahi[r]);
         int64_t lo = i + 1, hi = n;
         while (lo < hi) {
@@ -972,11 +1008,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float4 oj = sh_oth[k + u];
-          const bool fj = sh_vid[k + u].w < 0;
+          const unsigned fj = ((uint32_t)sh_vid[k + u].w >> 30) & 3u;
           const int jl = jl0 + k + u;
-          const bool h0 = ((unsigned)(jl - li[0] - 1) < span0) & (fi[0] | fj) & (oj.x <= oi[0].y) &
+          const bool h0 = ((unsigned)(jl - li[0] - 1) < span0) & ((fi[0] | fj) == 3u) & (oj.x <= oi[0].y) &
                           (oi[0].x <= oj.y) & (oj.z <= oi[0].w) & (oi[0].z <= oj.w);
-          const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & (fi[1] | fj) & (oj.x <= oi[1].y) &
+          const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & ((fi[1] | fj) == 3u) & (oj.x <= oi[1].y) &
                           (oi[1].x <= oj.y) & (oj.z <= oi[1].w) & (oi[1].z <= oj.w);
           bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
         }
@@ -988,7 +1024,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
             if ((bits >> bb) & 1u) {
               const int r = bb & 1;
               int4 vj = sh_vid[k + (bb >> 1)];
-              vj.w &= 0x7FFFFFFF;
+              vj.w &= 0x3FFFFFFF;
               bool vf;
               int p0, p1;
               if (candidate(vi[r], ki[r], vj, A.nV, A.nE, vf, p0, p1)) {
@@ -1029,7 +1065,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
     longlong2 o1[2], o2[2];
     int4 vi[2];
     int ki[2];
-    bool fi[2];
+    unsigned fi[2];
     const int li[2] = {2 * tid, 2 * tid + 1};
     int endl[2] = {li[0] + 1, li[1] + 1};
     int64_t end_max = i0;
@@ -1039,14 +1075,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
       ahi[r] = (long long)0x8000000000000000ull;   // no copy: every test fails
       o1[r] = o2[r] = make_longlong2(0, 0);
       vi[r] = make_int4(-1, -1, -1, 0);
-      fi[r] = false;
+      fi[r] = 0u;
       if (i < n) {
         ahi[r] = A.s_ahi64c[i];
         o1[r] = A.s_oth64c[2 * i];
         o2[r] = A.s_oth64c[2 * i + 1];
         vi[r] = A.s_vid[i];
-        fi[r] = vi[r].w < 0;
-        vi[r].w &= 0x7FFFFFFF;
+        fi[r] = ((uint32_t)vi[r].w >> 30) & 3u;   // first cell on each axis
+        vi[r].w &= 0x3FFFFFFF;
         const uint32_t seg = A.s_seg[i];
         int64_t lo = i + 1, hi = n;
         while (lo < hi) {
@@ -1088,11 +1124,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const longlong2 p1 = sh_oth[k + u][0], p2 = sh_oth[k + u][1];
-          const bool fj = sh_vid[k + u].w < 0;
+          const unsigned fj = ((uint32_t)sh_vid[k + u].w >> 30) & 3u;
           const int jl = jl0 + k + u;
-          const bool h0 = ((unsigned)(jl - li[0] - 1) < span0) & (fi[0] | fj) & (p1.x <= o1[0].y) &
+          const bool h0 = ((unsigned)(jl - li[0] - 1) < span0) & ((fi[0] | fj) == 3u) & (p1.x <= o1[0].y) &
                           (o1[0].x <= p1.y) & (p2.x <= o2[0].y) & (o2[0].x <= p2.y);
-          const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & (fi[1] | fj) & (p1.x <= o1[1].y) &
+          const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & ((fi[1] | fj) == 3u) & (p1.x <= o1[1].y) &
                           (o1[1].x <= p1.y) & (p2.x <= o2[1].y) & (o2[1].x <= p2.y);
           bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
         }
@@ -1104,7 +1140,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
             if ((bits >> bb) & 1u) {
               const int r = bb & 1;
               int4 vj = sh_vid[k + (bb >> 1)];
-              vj.w &= 0x7FFFFFFF;
+              vj.w &= 0x3FFFFFFF;
               bool vf;
               int p0, p1;
               if (candidate(vi[r], ki[r], vj, A.nV, A.nE, vf, p0, p1)) {

@@ -35,8 +35,10 @@ struct DevCtl {
   int pad_;
   // strip sweep
   unsigned long long n_copies;   // boxes placed in strips (with repeats)
-  int strip_fallback;            // 1: the copies did not fit; one strip per scene
+  int strip_fallback;            // 1: the copies did not fit; one cell per scene
   int sup_overflow;              // 1: the candidate buffer of the strip sweep overflowed
+  int copy_oversize;             // 1: a box overlaps more cells than its count can hold
+  int pad3_;
 };
 
 struct RingCell {
@@ -101,32 +103,35 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;                  // keys per thread per tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 
-// Strip sweep.  Per scene, the boxes are binned into strips of equal width
-// along a second axis (a box goes into every strip it overlaps) and the sweep
-// runs inside each strip; a pair is reported only in the strip where the
-// later of the two minima on the strip axis falls, so it is reported once.
-constexpr int kMaxStrips = 65535;
+// Cell sweep.  Per scene, the boxes are binned into a grid of cells on the
+// two axes other than the sweep axis (a box goes into every cell it
+// overlaps) and the sweep runs inside each cell; a pair is reported only in
+// the cell where, on each of the two axes, the later of the two minima
+// falls, so it is reported once.
+constexpr int kMaxCellsSingle = 4095;    // per axis, one scene (24-bit cell index)
+constexpr int kMaxCellsBatched = 255;    // per axis, batched scenes (16-bit cell index)
 struct StripParam {
-  float org;                     // smallest box minimum on the strip axis
-  float inv_w;                   // 1 / strip width (0: a single strip)
-  int nstrips;                   // 1 .. kMaxStrips
-  int axes;                      // sweep axis | strip axis << 2 | third axis << 4
+  float org[2];                  // smallest box minimum on each cell axis
+  float inv_w[2];                // 1 / cell width (0: one cell on that axis)
+  int ncell[2];                  // cells on each axis, >= 1
+  int axes;                      // sweep axis | first cell axis << 2 | second cell axis << 4
+  int pad;
 };
 
-// Strip of a coordinate x >= org: monotone non-decreasing in x, which is all
-// the reporting rule needs (two boxes that overlap on the strip axis share
-// the strip of the larger of their minima).
-__device__ __forceinline__ int strip_of(float x, const StripParam &p) {
-  if (p.nstrips <= 1) return 0;
-  const float t = __fmul_rn(__fsub_rn(x, p.org), p.inv_w);
-  return t >= (float)(p.nstrips - 1) ? p.nstrips - 1 : (t > 0.f ? (int)t : 0);
+// Cell of a coordinate x >= org on cell axis k: monotone non-decreasing in
+// x, which is all the reporting rule needs (two boxes that overlap on that
+// axis share the cell of the larger of their minima).
+__device__ __forceinline__ int strip_of(float x, const StripParam &p, int k) {
+  if (p.ncell[k] <= 1) return 0;
+  const float t = __fmul_rn(__fsub_rn(x, p.org[k]), p.inv_w[k]);
+  return t >= (float)(p.ncell[k] - 1) ? p.ncell[k] - 1 : (t > 0.f ? (int)t : 0);
 }
 
 // The same for an FP64 coordinate (the FP64 form bins on FP64 extents).
-__device__ __forceinline__ int strip_of64(double x, const StripParam &p) {
-  if (p.nstrips <= 1) return 0;
-  const double t = __dmul_rn(__dsub_rn(x, (double)p.org), (double)p.inv_w);
-  return t >= (double)(p.nstrips - 1) ? p.nstrips - 1 : (t > 0.0 ? (int)t : 0);
+__device__ __forceinline__ int strip_of64(double x, const StripParam &p, int k) {
+  if (p.ncell[k] <= 1) return 0;
+  const double t = __dmul_rn(__dsub_rn(x, (double)p.org[k]), (double)p.inv_w[k]);
+  return t >= (double)(p.ncell[k] - 1) ? p.ncell[k] - 1 : (t > 0.0 ? (int)t : 0);
 }
 
 // Inverse of the ordered-int64 map of a double (f64_ord).
@@ -190,7 +195,7 @@ __global__ void k_build_boxes(int64_t nV, int64_t nE, int64_t nF, const double *
                               const int32_t *E, const int32_t *F, BroadBufs B);
 __global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl, StripParam *sp,
                               float strip_factor);
-__global__ void k_count_copies(int64_t nB, BroadBufs B);
+__global__ void k_count_copies(int64_t nB, BroadBufs B, DevCtl *ctl);
 __global__ void k_scan_copies(int nblk, int64_t nB, BroadBufs B, DevCtl *ctl);
 __global__ void k_expand_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, unsigned long long *keys,
                                 uint32_t *vals);

@@ -31,7 +31,7 @@ def test_autotune_then_step_matches_oracle(ccd, use_graph):
         t = c.autotune(V0, V1, E, F, reps=2)
         assert t["sweep_kernel"] in (0, 2)
         assert t["export_budget"] in (16, 32, 64, 128, 256)
-        assert t["sweep_kernel"] == 2 or t["strip_width"] in (0.5, 1.0, 2.0, 4.0, 8.0)
+        assert t["sweep_kernel"] == 2 or t["strip_width"] in (1.5, 2.0, 3.0, 4.0, 6.0)
         q = t["queue_capacity"]
         assert q >= 1024 and q & (q - 1) == 0 and q <= 1 << 21
         assert t["n_trials"] >= 14 and t["broad_ms"] > 0 and t["narrow_ms"] > 0
