@@ -95,6 +95,15 @@ typedef struct {
                                 box width on each cell axis (0 = auto: 3); more
                                 cells mean fewer comparisons but more copies of
                                 boxes that straddle cell borders */
+    int64_t memory_limit;    /* device bytes ccd_step may size its buffers for (by the
+                                memory model, ccd_get_memory_model; 0 = no limit).
+                                A synchronous step whose candidate pairs exceed the
+                                capacity that fits runs the paper's batching
+                                (Section "Batching"): the sorted boxes are swept in
+                                ranges whose pairs fit, each range's narrow phase
+                                carrying the earliest time over (cell sweep only, no
+                                zero-TOI rule); an asynchronous step raises
+                                CCD_ETRUNC instead */
 } ccd_opts;
 
 /* Work counters of the last broad/narrow/step call (see ccd_get_status). */
@@ -118,6 +127,7 @@ typedef struct {
     int64_t n_intervals_fp64;  /* intervals the single-precision filter left to FP64 */
     int64_t n_box_copies;    /* cell sweep: boxes placed in cells, counting each
                                 cell a box overlaps (n_boxes for the other sweeps) */
+    int64_t n_ranges;        /* ranges the last step swept under memory_limit (0: one pass) */
 } ccd_stats;
 
 /* Fill *o with the defaults. */
@@ -253,6 +263,13 @@ typedef struct {
 int ccd_autotune(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
                  const int32_t *F, int64_t nF, int32_t reps, ccd_tuning *out, void *stream);
 
+/* The autotuner on batched scenes (arguments as in ccd_step_batch): times
+ * the batched broad phase and the per-scene narrow phase. */
+int ccd_autotune_batch(ccd_ctx *ctx, int32_t n_scenes, const int64_t *vert_off, const int64_t *edge_off,
+                       const int64_t *face_off, const double *V0, const double *V1, int64_t nV,
+                       const int32_t *E, int64_t nE, const int32_t *F, int64_t nF, int32_t reps,
+                       ccd_tuning *out, void *stream);
+
 /*
  * Device memory model.  Section "Batching" sizes the candidate list C from
  * the free memory M as S_C = (M - S_P) / (S_Q + S_i): per pair, the query
@@ -342,6 +359,9 @@ typedef struct {
     double pairs_per_box;    /* candidate pairs per box the admission budgets for
                                 (0 = 4); a batch with more pairs fails with
                                 CCD_ETRUNC */
+    int32_t autotune;        /* 1: each slot runs ccd_autotune_batch on its first
+                                batch (cell width, hand-off budget, queue) */
+    int32_t pad;
 } ccd_server_opts;
 
 typedef struct {

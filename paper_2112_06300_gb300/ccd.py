@@ -33,7 +33,7 @@ class ccd_opts(ctypes.Structure):
                 ("queue_capacity", ctypes.c_int64), ("export_budget", ctypes.c_int32),
                 ("profile_stages", ctypes.c_int32), ("no_zero_toi", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("pad0", ctypes.c_int32),
-                ("strip_width", ctypes.c_double)]
+                ("strip_width", ctypes.c_double), ("memory_limit", ctypes.c_int64)]
 
 
 class ccd_stats(ctypes.Structure):
@@ -45,7 +45,7 @@ class ccd_stats(ctypes.Structure):
                 ("n_launches", ctypes.c_int64), ("narrow_bulk_ns", ctypes.c_int64),
                 ("narrow_tail_ns", ctypes.c_int64), ("n_donated", ctypes.c_int64),
                 ("n_intervals_tail", ctypes.c_int64), ("n_intervals_fp64", ctypes.c_int64),
-                ("n_box_copies", ctypes.c_int64)]
+                ("n_box_copies", ctypes.c_int64), ("n_ranges", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
@@ -59,7 +59,8 @@ class ccd_memory_model(ctypes.Structure):
 class ccd_server_opts(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("max_scenes", ctypes.c_int32), ("max_boxes", ctypes.c_int64),
                 ("memory_cap", ctypes.c_int64), ("arena_bytes", ctypes.c_int64), ("delta", ctypes.c_double),
-                ("min_sep", ctypes.c_double), ("max_iter", ctypes.c_int64), ("pairs_per_box", ctypes.c_double)]
+                ("min_sep", ctypes.c_double), ("max_iter", ctypes.c_int64), ("pairs_per_box", ctypes.c_double),
+                ("autotune", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class ccd_server_stats(ctypes.Structure):
@@ -119,6 +120,8 @@ def lib():
     L.ccd_narrow_noalloc.restype = ctypes.c_int
     L.ccd_autotune.argtypes = [P, P, P, i64, P, i64, P, i64, i32, ctypes.POINTER(ccd_tuning), P]
     L.ccd_autotune.restype = ctypes.c_int
+    L.ccd_autotune_batch.argtypes = [P, i32, P, P, P, P, P, i64, P, i64, P, i64, i32, ctypes.POINTER(ccd_tuning), P]
+    L.ccd_autotune_batch.restype = ctypes.c_int
     L.ccd_status_async.argtypes = [P, P, P]
     L.ccd_status_async.restype = ctypes.c_int
     L.ccd_get_memory_model.argtypes = [ctypes.POINTER(ccd_opts), ctypes.POINTER(ccd_memory_model)]

@@ -2,6 +2,9 @@
 // sequence of Algorithm 1 (boxes, broad phase, narrow phase), status.
 
 #include <algorithm>
+#include <climits>
+#include <utility>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -40,6 +43,8 @@ struct ccd_ctx {
   int *bsid = nullptr, *saxis = nullptr;
   float *ssum = nullptr;
   uint32_t *smm = nullptr;
+  const unsigned long long *s_key_last = nullptr;   // sorted copy keys of the last broad phase
+  int64_t last_ranges = 0;                          // ranges of the last memory-limited step
   // FP64 strip sweep buffers, sized for cap_boxes boxes (allocated on first use)
   int64_t cap_strips64 = 0;
   void *strips64_mem = nullptr;
@@ -99,10 +104,11 @@ __global__ void k_reset_broad(DevCtl *c) {
   for (int i = 0; i < 6; ++i) c->var_sum[i] = 0;
   c->axis = 0;
 }
-__global__ void k_reset_narrow(DevCtl *c) {
+// keep_toi: a later batch of the same step (the earliest time carries over)
+__global__ void k_reset_narrow(DevCtl *c, int keep_toi) {
   c->q_next = 0;
   c->pending = 0;
-  c->toi_bits = 0x7FF0000000000000ull;
+  if (!keep_toi) c->toi_bits = 0x7FF0000000000000ull;
   c->n_intervals = c->n_exported = c->n_capped = c->queue_peak = 0;
   c->t_start = c->t_exhausted = c->t_end = 0;
   c->n_donated = 0;
@@ -310,7 +316,10 @@ struct SceneSpec {
 
 int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
                  const int32_t *F, int64_t nF, int32_t *vf_out, int64_t vf_cap, int32_t *ee_out, int64_t ee_cap,
-                 cudaStream_t s, const SceneSpec &sc = SceneSpec{0, nullptr, nullptr, nullptr}, bool ee_rev = false) {
+                 cudaStream_t s, const SceneSpec &sc = SceneSpec{0, nullptr, nullptr, nullptr}, bool ee_rev = false,
+                 int phase = 3, int64_t i_begin = 0, int64_t i_end = INT64_MAX) {
+  // phase 1: boxes and sort; phase 2: the sweep (over sorted copies
+  // [i_begin, i_end) for the cell sweeps); 3: both
   const int64_t nB = nV + nE + nF;
   int rc = ensure_broad(c, nB);
   if (rc) return rc;
@@ -323,7 +332,10 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     if (rc) return rc;
   }
   c->last_nB = nB;
-  k_reset_broad<<<1, 1, 0, s>>>(c->ctl);
+  if (phase & 1)
+    k_reset_broad<<<1, 1, 0, s>>>(c->ctl);
+  else
+    k_reset_sweep<<<1, 1, 0, s>>>(c->ctl);
   if (nB == 0) {
     c->n_launches += 1;
     return cudaGetLastError() == cudaSuccess ? CCD_OK : CCD_ECUDA;
@@ -340,9 +352,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   if (sc.n > 0) B.sparam = c->sparam_sc;
   B.strip_factor = c->opts.strip_width > 0 ? (float)c->opts.strip_width : 3.0f;
   const bool fp64 = c->opts.broad_fp64 != 0;
-  // sweep: 0 strips, 1 warp per box, 2 tiled over one sorted list
-  // (the strip keys hold 16 bits of scene index: more scenes take the tiled sweep)
-  // sweep: 0 strips, 1 warp per box, 2 tiled over one sorted list (the FP64
+  // sweep: 0 cells, 1 warp per box, 2 tiled over one sorted list (the FP64
   // form has strips and warp per box; more than 65,536 scenes take the tiled
   // sweep: the strip keys hold 16 bits of scene index)
   int sweep = c->opts.sweep_kernel;
@@ -362,6 +372,14 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   B.s_ahi64c = c->s_ahi64c;
   B.s_oth64c = c->s_oth64c;
   const int nbuild = (int)cdiv(nB, kBuildThreads);
+  const int grid = (int)std::min<int64_t>(cdiv(nB, 256), (int64_t)c->sm_count * 8);
+  int sort_passes = 0;
+  int extra = 0;
+  int sbits = 0;   // bits of the scene index in the keys of batched scenes
+  while ((1ll << sbits) < sc.n) ++sbits;
+  const unsigned long long *s_key = c->s_key_last;
+  if (phase & 1) {
+  sort_passes = fp64 ? 8 : 4;
   mark(c, CCD_STAGE_BOXES, true, s);
   if (sc.n > 0) {
     CK(cudaMemsetAsync(c->ssum, 0, 9 * sc.n * sizeof(float), s));
@@ -375,12 +393,6 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   }
   mark(c, CCD_STAGE_BOXES, false, s);
   mark(c, CCD_STAGE_SORT, true, s);
-  const int grid = (int)std::min<int64_t>(cdiv(nB, 256), (int64_t)c->sm_count * 8);
-  int sort_passes = fp64 ? 8 : 4;
-  int extra = 0;
-  int sbits = 0;   // bits of the scene index in the keys of batched scenes
-  while ((1ll << sbits) < sc.n) ++sbits;
-  const unsigned long long *s_key = nullptr;
   if (strips64) {
     // FP64 strips: copies sorted by the ordered FP64 minimum (64 bits), then
     // stably by strip segment (16 bits)
@@ -427,6 +439,9 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     k_gather_sorted64<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
   }
   mark(c, CCD_STAGE_SORT, false, s);
+  c->s_key_last = s_key;
+  }
+
   SweepArgs A;
   A.nB = nB;
   A.nV = nV;
@@ -455,7 +470,10 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.n_dev = &c->ctl->n_copies;
   A.sup = c->sup;
   A.sup_cap = c->sup_cap;
+  A.i_begin = i_begin;
+  A.i_end = i_end;
   const int sgrid = (int)std::min<int64_t>(cdiv(nB * 32, 256), (int64_t)c->sm_count * 32);
+  if (phase & 2) {
   mark(c, CCD_STAGE_SWEEP, true, s);
   A.s_seg = B.s_seg;
   A.s_key64 = B.s_key64;
@@ -478,9 +496,10 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     extra += 1;
   }
   mark(c, CCD_STAGE_SWEEP, false, s);
+  }
   // reset, build, axis, keys (or count, scan, expand), passes x (hist, scan,
   // scatter), gather, sweep (and exact filter)
-  c->n_launches += 6 + extra + 3 * sort_passes;
+  c->n_launches += (phase & 1 ? 5 : 1) + (phase & 2 ? 1 : 0) + extra + 3 * sort_passes;
   CK(cudaGetLastError());
   return CCD_OK;
 }
@@ -490,14 +509,14 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
                   const int32_t *F, double delta, double min_sep, int64_t max_iter, int mode,
                   unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s,
                   bool zero_rule_pass = false, int n_scenes = 0, const int64_t *voff = nullptr,
-                  unsigned long long *toi_scene = nullptr, int64_t ee_end = 0) {
+                  unsigned long long *toi_scene = nullptr, int64_t ee_end = 0, bool keep_toi = false) {
   const int64_t nq = counts_from_ctl && ee_end > 0 ? ee_end : n_vf + n_ee;
   int rc = ensure_narrow(c, nq, s);
   if (rc) return rc;
   if (zero_rule_pass)
     k_nozero_prepare<<<1, 1, 0, s>>>(c->ctl);
   else
-    k_reset_narrow<<<1, 1, 0, s>>>(c->ctl);
+    k_reset_narrow<<<1, 1, 0, s>>>(c->ctl, keep_toi ? 1 : 0);
   NarrowArgs A;
   A.ctl = c->ctl;
   A.vf = vf;
@@ -752,6 +771,78 @@ int ccd_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee, i
   return CCD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The paper's batching for one scene whose candidate pairs do not fit the
+// memory limit: boxes and sort once, then the sweep over ranges of the
+// sorted copies, each range's pairs narrowed with the earliest time carried
+// over; a range whose pairs overflow is halved.  Synchronous.
+int ranged_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+                const int32_t *F, int64_t nF, double delta, double min_sep, int64_t max_iter, unsigned long long need,
+                double *toi_min, cudaStream_t s) {
+  if (c->opts.sweep_kernel != 0 || c->opts.no_zero_toi) return CCD_ETRUNC;
+  const int64_t cap = c->pair_cap;
+  clear_marks(c);
+  k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+  int rc = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, cap, c->ee, cap, s,
+                        SceneSpec{0, nullptr, nullptr, nullptr}, true, 1);
+  if (rc) return rc;
+  unsigned long long ncopy = 0;
+  CK(cudaMemcpyAsync(&ncopy, &c->ctl->n_copies, sizeof(ncopy), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int64_t k0 = std::max<int64_t>(2, (int64_t)(need / (unsigned long long)std::max<int64_t>(1, cap * 3 / 4)) + 1);
+  std::vector<std::pair<int64_t, int64_t>> todo;
+  for (int64_t k = k0 - 1; k >= 0; --k)
+    todo.push_back({(int64_t)ncopy * k / k0, (int64_t)ncopy * (k + 1) / k0});
+  bool first = true;
+  int64_t ranges = 0;
+  while (!todo.empty()) {
+    const auto r = todo.back();
+    todo.pop_back();
+    if (r.first >= r.second) continue;
+    rc = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, cap, c->ee, cap, s, SceneSpec{0, nullptr, nullptr, nullptr},
+                      true, 2, r.first, r.second);
+    if (rc) return rc;
+    struct {
+      unsigned long long nvf, nee, nsup;
+      int ovf;
+    } h;
+    CK(cudaMemcpyAsync(&h.nvf, &c->ctl->n_vf, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&h.ovf, &c->ctl->sup_overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h.ovf || (int64_t)(h.nvf + h.nee) > cap) {
+      if (r.second - r.first <= 1) return CCD_ETRUNC;   // one box's pairs alone do not fit
+      const int64_t m = (r.first + r.second) / 2;
+      todo.push_back({m, r.second});
+      todo.push_back({r.first, m});
+      continue;
+    }
+    k_counts_from_broad<<<1, 1, 0, s>>>(c->ctl, cap);
+    c->n_launches += 1;
+    rc = launch_narrow(c, c->vf, cap, c->ee, cap, 1, V0, V1, nV, E, F, delta, min_sep, max_iter, 1, nullptr,
+                       nullptr, s, false, 0, nullptr, nullptr, cap, !first);
+    if (rc) return rc;
+    first = false;
+    ++ranges;
+  }
+  c->last_ranges = ranges;
+  struct {
+    unsigned long long toi;
+    int status;
+  } h;
+  CK(cudaMemcpyAsync(&h.toi, &c->ctl->toi_bits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&h.status, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::memcpy(toi_min, &h.toi, sizeof(double));
+  return h.status;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
              const int32_t *F, int64_t nF, double delta, double min_sep, int64_t max_iter, double *toi_min,
              void *stream) {
@@ -762,6 +853,13 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
   c->last_stream = s;
   const bool host_out = !is_device_ptr(toi_min);
   int64_t want = c->opts.pair_capacity > 0 ? c->opts.pair_capacity : default_pair_capacity(nV + nE + nF);
+  int64_t limit_cap = INT64_MAX;   // pair capacity that fits opts.memory_limit
+  if (c->opts.memory_limit > 0) {
+    limit_cap = ccd_pair_capacity_for(&c->opts, c->opts.memory_limit, nV + nE + nF, 0);
+    if (limit_cap < 1024) return CCD_ENOMEM;
+    want = std::min(want, limit_cap);
+  }
+  c->last_ranges = 0;
   auto enqueue = [&](cudaStream_t st) -> int {
     clear_marks(c);
     k_reset_status<<<1, 1, 0, st>>>(c->ctl);
@@ -828,7 +926,9 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     // the candidate buffer holds twice the pair capacity
     unsigned long long need = h.nvf + h.nee;
     if (h.ovf) need = std::max(need, h.nsup / 2 + 1);
-    want = (int64_t)need + (int64_t)(need / 8) + 1024;
+    if ((int64_t)need > limit_cap - limit_cap / 8 - 1024 || c->pair_cap >= limit_cap)
+      return ranged_step(c, V0, V1, nV, E, nE, F, nF, delta, min_sep, max_iter, need, toi_min, s);
+    want = std::min<int64_t>((int64_t)need + (int64_t)(need / 8) + 1024, limit_cap);
   }
   return CCD_ETRUNC;
 }
@@ -884,8 +984,14 @@ int ccd_step_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const 
   return run_graph(c, c->g_batch, &key, sizeof(key), s, enqueue);
 }
 
-int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
-                 const int32_t *F, int64_t nF, int32_t reps, ccd_tuning *out, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// The autotuner on one scene (sc.n == 0) or on batched scenes.
+int autotune_impl(ccd_ctx *c, const SceneSpec &sc, const double *V0, const double *V1, int64_t nV,
+                  const int32_t *E, int64_t nE, const int32_t *F, int64_t nF, int32_t reps, ccd_tuning *out,
+                  void *stream) {
   if (!c || !out || reps < 1 || c->opts.broad_fp64 != 0) return CCD_EINVAL;
   if (!mesh_args_ok(V0, V1, nV, E, nE, F, nF)) return CCD_EINVAL;
   CK(cudaSetDevice(c->device));
@@ -894,11 +1000,21 @@ int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   const bool graph = c->opts.use_graph != 0;
   c->opts.use_graph = 0;
   std::memset(out, 0, sizeof(*out));
-  // one synchronous step sizes every buffer (pairs grow to fit)
-  double t0 = 0.0;
-  int rc = ccd_step(c, V0, V1, nV, E, nE, F, nF, c->opts.delta, c->opts.min_sep, c->opts.max_iter, &t0, stream);
+  // one step sizes every buffer (pairs grow to fit)
+  unsigned long long *toi_sc = nullptr;   // per-scene earliest times (batched scenes)
+  int rc = CCD_OK;
+  if (sc.n > 0) {
+    CK(cudaMalloc(&toi_sc, sc.n * sizeof(double)));
+    rc = ccd_step_batch(c, sc.n, sc.voff, sc.eoff, sc.foff, V0, V1, nV, E, nE, F, nF, c->opts.delta,
+                        c->opts.min_sep, c->opts.max_iter, (double *)toi_sc, stream);
+    if (rc == CCD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = CCD_ECUDA;
+  } else {
+    double t0 = 0.0;
+    rc = ccd_step(c, V0, V1, nV, E, nE, F, nF, c->opts.delta, c->opts.min_sep, c->opts.max_iter, &t0, stream);
+  }
   if (rc) {
     c->opts = saved;
+    cudaFree(toi_sc);
     return rc;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -917,11 +1033,14 @@ int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
         k_counts_from_broad<<<1, 1, 0, s>>>(c->ctl, c->pair_cap);
       }
       cudaEventRecord(e0, s);
+      if (narrow && sc.n > 0)
+        k_fill_u64<<<(unsigned)std::min<int64_t>(cdiv(sc.n, 256), 1024), 256, 0, s>>>(toi_sc, sc.n,
+                                                                                     0x7FF0000000000000ull);
       int r2 = narrow ? launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F,
-                                      c->opts.delta, c->opts.min_sep, c->opts.max_iter, 1, nullptr, nullptr, s,
-                                      false, 0, nullptr, nullptr, c->pair_cap)
-                      : launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, s,
-                                     SceneSpec{0, nullptr, nullptr, nullptr}, true);
+                                      c->opts.delta, c->opts.min_sep, c->opts.max_iter, sc.n > 0 ? 2 : 1, nullptr,
+                                      nullptr, s, false, sc.n, sc.voff, toi_sc, c->pair_cap)
+                      : launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, s, sc,
+                                     true);
       cudaEventRecord(e1, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) r2 = CCD_ECUDA;
       int st = CCD_OK;
@@ -1003,6 +1122,11 @@ int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (toi_sc) {
+    cudaStreamSynchronize(s);
+    cudaFree(toi_sc);
+    toi_sc = nullptr;
+  }
   // launch configurations changed: captured graphs are stale
   if (c->g_step.valid) { cudaGraphExecDestroy(c->g_step.exec); c->g_step.valid = false; }
   if (c->g_batch.valid) { cudaGraphExecDestroy(c->g_batch.exec); c->g_batch.valid = false; }
@@ -1023,6 +1147,23 @@ int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   out->default_ms = base_b + base_n;
   out->n_trials = trials;
   return CCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccd_autotune(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+                 const int32_t *F, int64_t nF, int32_t reps, ccd_tuning *out, void *stream) {
+  return autotune_impl(c, SceneSpec{0, nullptr, nullptr, nullptr}, V0, V1, nV, E, nE, F, nF, reps, out, stream);
+}
+
+int ccd_autotune_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const int64_t *edge_off,
+                       const int64_t *face_off, const double *V0, const double *V1, int64_t nV, const int32_t *E,
+                       int64_t nE, const int32_t *F, int64_t nF, int32_t reps, ccd_tuning *out, void *stream) {
+  if (n_scenes < 1 || !vert_off || !edge_off || !face_off) return CCD_EINVAL;
+  return autotune_impl(c, SceneSpec{n_scenes, vert_off, edge_off, face_off}, V0, V1, nV, E, nE, F, nF, reps, out,
+                       stream);
 }
 
 int ccd_status_async(ccd_ctx *c, int32_t *status, void *stream) {
@@ -1083,6 +1224,7 @@ int ccd_get_status(ccd_ctx *c, ccd_stats *st) {
     st->device_status = h.status;
     st->n_launches = c->n_launches;
     st->n_box_copies = h.n_copies ? (int64_t)h.n_copies : c->last_nB;
+    st->n_ranges = c->last_ranges;
     if (h.t_end > h.t_start && h.t_start) {
       const unsigned long long tx = h.t_exhausted ? h.t_exhausted : h.t_end;
       st->narrow_bulk_ns = (int64_t)(tx - h.t_start);

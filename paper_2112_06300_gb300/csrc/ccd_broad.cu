@@ -946,7 +946,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   uint2 *buf = sh_sup[wid];
   int nbuf = 0;   // warp-uniform
-  for (int64_t i0 = (int64_t)blockIdx.x * kTI; i0 < n; i0 += (int64_t)gridDim.x * kTI) {
+  const int64_t ie = min(n, A.i_end);
+  for (int64_t i0 = A.i_begin + (int64_t)blockIdx.x * kTI; i0 < ie; i0 += (int64_t)gridDim.x * kTI) {
     float ahi[2];
     float4 oi[2];
     int4 vi[2];
@@ -962,7 +963,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
       oi[r] = make_float4(0.f, 0.f, 0.f, 0.f);
       vi[r] = make_int4(-1, -1, -1, 0);
       fi[r] = 0u;
-      if (i < n) {
+      if (i < ie) {
         ahi[r] = A.s_ahi[i];
         oi[r] = A.s_oth[i];
         vi[r] = A.s_vid[i];
@@ -1060,7 +1061,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   uint2 *buf = sh_sup[wid];
   int nbuf = 0;
-  for (int64_t i0 = (int64_t)blockIdx.x * kTI; i0 < n; i0 += (int64_t)gridDim.x * kTI) {
+  const int64_t ie = min(n, A.i_end);
+  for (int64_t i0 = A.i_begin + (int64_t)blockIdx.x * kTI; i0 < ie; i0 += (int64_t)gridDim.x * kTI) {
     long long ahi[2];
     longlong2 o1[2], o2[2];
     int4 vi[2];
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
       o1[r] = o2[r] = make_longlong2(0, 0);
       vi[r] = make_int4(-1, -1, -1, 0);
       fi[r] = 0u;
-      if (i < n) {
+      if (i < ie) {
         ahi[r] = A.s_ahi64c[i];
         o1[r] = A.s_oth64c[2 * i];
         o2[r] = A.s_oth64c[2 * i + 1];
@@ -1162,6 +1164,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
     __syncthreads();
   }
   if (nbuf) sup_flush(A, buf, nbuf);
+}
+
+__global__ void k_reset_sweep(DevCtl *ctl) {
+  ctl->n_vf = ctl->n_ee = ctl->n_superset = 0;
+  ctl->sup_overflow = 0;
 }
 
 // Exact test of the strip sweep's candidates on the FP64 extents (ordered

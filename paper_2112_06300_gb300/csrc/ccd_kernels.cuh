@@ -239,7 +239,10 @@ struct SweepArgs {
   // tested against the FP64 extents by k_exact_filter
   uint2 *sup;
   int64_t sup_cap;
-  // FP64 strip sweep
+  // cell sweeps: sorted copies [i_begin, i_end) start ranges (the paper's
+  // batching: a range's pairs fit the buffers; ranges read past their end)
+  int64_t i_begin, i_end;
+  // FP64 cell sweep
   const uint32_t *s_seg;
   const long long *s_key64, *s_ahi64c;
   const longlong2 *s_oth64c;
@@ -253,6 +256,7 @@ __global__ void k_gather_seg(int64_t cap, const DevCtl *ctl, const uint32_t *per
                              uint32_t *out);
 __global__ void k_gather_copies64(int64_t nB, BroadBufs B, const DevCtl *ctl, const uint32_t *perm);
 __global__ void k_exact_filter(SweepArgs A);
+__global__ void k_reset_sweep(DevCtl *ctl);
 __global__ void k_sweep_tiled(SweepArgs A);
 __global__ void k_sweep64(SweepArgs A);
 

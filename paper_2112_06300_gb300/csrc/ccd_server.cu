@@ -164,6 +164,7 @@ struct Slot {
   int32_t *h_status = nullptr;
   int64_t cap_h_status = 0;
   Batch *batch = nullptr;
+  bool tuned = false;
 };
 
 }  // namespace
@@ -282,6 +283,13 @@ int run_batch(ccd_server *S, Slot &sl, Batch *b) {
   int64_t *voff = sl.offs, *eoff = sl.offs + (n + 1), *foff = sl.offs + 2 * (n + 1);
   k_unpack<<<n, 256, 0, s>>>(sl.staging, sl.desc, n, nV, sl.V0, sl.V1, sl.E, sl.F, voff, eoff, foff);
   if (cudaGetLastError() != cudaSuccess) return CCD_ECUDA;
+  if (S->opts.autotune && !sl.tuned) {
+    // tune the slot's context on its first batch (synchronous)
+    ccd_tuning t;
+    rc = ccd_autotune_batch(sl.ctx, n, voff, eoff, foff, sl.V0, sl.V1, nV, sl.E, nE, sl.F, nF, 2, &t, s);
+    if (rc) return rc;
+    sl.tuned = true;
+  }
   rc = ccd_step_batch(sl.ctx, n, voff, eoff, foff, sl.V0, sl.V1, nV, sl.E, nE, sl.F, nF, S->opts.delta,
                       S->opts.min_sep, S->opts.max_iter, sl.toi, s);
   if (rc) return rc;
@@ -394,7 +402,8 @@ int ccd_server_create(ccd_server **out, const ccd_server_opts *o, int device) {
   if (o) opts = *o;
   if (opts.n_slots < 1 || opts.n_slots > 16 || opts.max_scenes < 1 || opts.max_scenes > 65536 ||
       opts.max_boxes < 1 || opts.memory_cap <= 0 || opts.arena_bytes < (1 << 20) || !(opts.delta >= 0) ||
-      !(opts.min_sep >= 0) || opts.max_iter < 0 || !(opts.pairs_per_box >= 0))
+      !(opts.min_sep >= 0) || opts.max_iter < 0 || !(opts.pairs_per_box >= 0) ||
+      (opts.autotune != 0 && opts.autotune != 1))
     return CCD_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return CCD_EINVAL;
   ccd_server *S = new (std::nothrow) ccd_server();

@@ -301,3 +301,24 @@ def test_no_zero_toi_rule_matches_oracle(ccd):
             assert t == O.step(s.V0, s.V1, s.E, s.F, min_sep=ms, no_zero_toi=True)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("pairs", [20000, 3000])
+def test_memory_limited_step_runs_in_ranges(ccd, pairs):
+    """A memory limit that fits fewer candidate pairs than the step has: the
+    step sweeps ranges of the sorted boxes (the paper's batching) and still
+    returns the oracle's earliest time."""
+    s = scenes.folded_cloth(64, seed=1)
+    m = ccd.ccd_get_memory_model()
+    limit = m["bytes_fixed"] + max(s.n_boxes, 1024) * m["bytes_per_box"] + pairs * m["bytes_per_pair"]
+    c = ccd.CCD(0, memory_limit=limit)
+    try:
+        V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+        t = c.step(V0, V1, E, F)
+        rc, st = c.status()
+        assert rc == 0 and st["n_ranges"] >= 2
+        assert t == O.step(s.V0, s.V1, s.E, s.F)
+    finally:
+        c.close()
+    ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+    assert len(ovf) + len(oee) > pairs

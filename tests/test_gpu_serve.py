@@ -36,8 +36,8 @@ def mix():
         [scenes.icosphere_on_plane(2, level=2, plane_n=9)]
 
 
-@pytest.mark.parametrize("max_scenes,n_slots", [(6, 2), (1, 1), (256, 3)])
-def test_served_scene_equals_alone_and_oracle(ccd, max_scenes, n_slots):
+@pytest.mark.parametrize("max_scenes,n_slots,tune", [(6, 2, 0), (1, 1, 0), (256, 3, 0), (8, 2, 1)])
+def test_served_scene_equals_alone_and_oracle(ccd, max_scenes, n_slots, tune):
     batch = mix()
     ref = np.array([O.step(s.V0, s.V1, s.E, s.F) if len(s.V0) else np.inf for s in batch])
     c = ccd.CCD(0)
@@ -46,7 +46,8 @@ def test_served_scene_equals_alone_and_oracle(ccd, max_scenes, n_slots):
     finally:
         c.close()
     np.testing.assert_array_equal(alone.view(np.uint64), ref.view(np.uint64))
-    srv = ccd.Server(0, n_slots=n_slots, max_scenes=max_scenes, arena_bytes=64 << 20, memory_cap=8 << 30)
+    srv = ccd.Server(0, n_slots=n_slots, max_scenes=max_scenes, arena_bytes=64 << 20, memory_cap=8 << 30,
+                     autotune=tune)
     try:
         tickets = [srv.submit_scene(s.V0, s.V1, s.E, s.F) for s in batch]
         got = [srv.wait(t) for t in tickets]
