@@ -49,7 +49,11 @@ HBM_FALLBACK_GBS = 6800.0
 # Per-launch DRAM traffic from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel with the hash of the source file it
 # was taken on; ignored once the source changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_narrow -s 1 -c 1
+    #     python bench.py --steps 2 --warmup 3 --no-cpu-baseline   (1.49 GB read + 59.5 MB written)
+    "k_narrow": (1.4900e9 + 59.5e6, "0f68124f1314c7a0"),
+}
 
 
 def parse():
