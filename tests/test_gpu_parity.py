@@ -322,3 +322,22 @@ def test_memory_limited_step_runs_in_ranges(ccd, pairs):
         c.close()
     ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
     assert len(ovf) + len(oee) > pairs
+
+
+def test_cloth_min_sep_step(ccd):
+    """The cloth with min_sep = 1e-4: the first contact within min_sep is a
+    patch, so some queries reach the iteration cap; the earliest time stays
+    conservative (no later than with min_sep = 0) and agrees with the oracle's
+    earliest-time step."""
+    s = scenes.folded_cloth(64, seed=1)
+    c = ccd.CCD(0)
+    try:
+        V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+        t = c.step(V0, V1, E, F, min_sep=1e-4)
+        assert c.status()[0] == 0
+        t0 = c.step(V0, V1, E, F, min_sep=0.0)
+    finally:
+        c.close()
+    to = O.step(s.V0, s.V1, s.E, s.F, min_sep=1e-4)
+    assert 0.0 < t <= t0
+    assert t == to or abs(t - to) <= 1e-3
