@@ -208,12 +208,13 @@ int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
   c->qrec = nullptr;
   c->qsid = nullptr;
   c->cap_q = 0;
-  // a multiple of the narrow kernel's staged batch: its record copies stay
-  // aligned and in bounds
-  int64_t cap = (std::max<int64_t>(nq, 1024) + 31) / 32 * 32;
+  // a multiple of the narrow kernel's staged batch (and of 32): its record
+  // copies stay aligned and in bounds
+  constexpr int64_t kCapUnit = 32 * kStageQ;
+  int64_t cap = (std::max<int64_t>(nq, 1024) + kCapUnit - 1) / kCapUnit * kCapUnit;
   CK(cudaMalloc(&c->qflags, cap * sizeof(uint32_t)));
   CK(cudaMalloc(&c->qiters, cap * sizeof(unsigned long long)));
-  CK(cudaMalloc(&c->qrec, cap * (24 * sizeof(unsigned long long) + 28 * sizeof(float))));
+  CK(cudaMalloc(&c->qrec, cap * (24 * sizeof(unsigned long long) + 33 * sizeof(float))));
   CK(cudaMalloc(&c->qsid, cap * sizeof(int)));
   c->cap_q = cap;
   return CCD_OK;
@@ -1183,9 +1184,9 @@ int ccd_get_memory_model(const ccd_opts *o, ccd_memory_model *m) {
   // sweep), the one-list sorted arrays, copy offsets; plus the scene index
   m->bytes_per_box = 24 + 48 + 16 + 3 * (16 + 8) + 2 + 4 + 3 * (4 + 16 + 16) + (8 + 8 + 32) + 4 + 4;
   // per pair slot: the pair (8), two candidate slots (16), and the narrow
-  // phase's per-query flags (4), counter (8), record (24 words + 28 floats)
+  // phase's per-query flags (4), counter (8), record (24 words + 33 floats)
   // and scene (4)
-  m->bytes_per_pair = 8 + 16 + 4 + 8 + (24 * 8 + 28 * 4) + 4;
+  m->bytes_per_pair = 8 + 16 + 4 + 8 + (24 * 8 + 33 * 4) + 4;
   // per scene: statistics, axis and strip layout
   m->bytes_per_scene = 9 * 4 + 6 * 4 + 4 + (int64_t)sizeof(StripParam);
   const int64_t ring = opts.queue_capacity > 0 ? opts.queue_capacity : (1 << 21);

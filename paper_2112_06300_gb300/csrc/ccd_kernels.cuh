@@ -50,9 +50,10 @@ struct RingCell {
 
 constexpr int kNarrowThreads = 128;
 // Claimed queries staged per warp in dynamic shared memory: two buffers of
-// kStageQ query records (24 words, 27 floats, scene id each).
+// kStageQ query records (24 words, 33 floats, scene id each).
 constexpr int kStageQ = 16;
-constexpr size_t kStageBytes = kStageQ * (24 * 8 + 27 * 4 + 4);
+static_assert(kStageQ % 4 == 0, "staged records are copied in 16-byte chunks");
+constexpr size_t kStageBytes = kStageQ * (24 * 8 + 33 * 4 + 4);
 constexpr size_t kNarrowDynSmem = (kNarrowThreads / 32) * 2 * kStageBytes;
 
 struct NarrowArgs {
@@ -83,7 +84,7 @@ struct NarrowArgs {
   const int64_t *voff;
   unsigned long long *toi_scene; // [n_scenes] bits of each scene's t* (+inf initialised)
   int *qsid;                     // [n_vf + n_ee] scene of each query
-  unsigned long long *qrec;      // query records: 24 words then 27 floats, x rec_stride
+  unsigned long long *qrec;      // query records: 24 words then 33 floats, x rec_stride
                                  // (NULL: lanes set their queries up themselves)
   int64_t rec_stride;
 };

@@ -44,13 +44,30 @@ struct QueryData {
   long long ebox_p[3], ebox_n[3];  // ordered keys of +ebox and -ebox
   unsigned long long K[3];         // split keys: bits of L_t, L_u, L_v (0: never)
   // single-precision filter (see inclusion32): rounded c0, dc and, per axis,
-  // the FP32 error bound e32 and the decision thresholds tm and wn
+  // the decision thresholds tn, tm, wn and the bounds cc0, cdc of the
+  // rounding of c0 and dc to float (summed over the three vectors)
   float c0f[3][3], dcf[3][3];
-  float e32[3], tm[3], wn[3];
+  float tn[3], tm[3], wn[3];
+  float cc0[3], cdc[3];
 };
 
 __device__ __forceinline__ unsigned long long dbits(double d) {
   return (unsigned long long)__double_as_longlong(d);
+}
+
+// An upper bound of |float(d) - d| for round-to-nearest: 0 when d is a float
+// (its low 29 significand bits are zero and it lies in the normal float
+// range), else one float ulp at d's exponent; 2^-149 below the normal range,
+// infinity from 2^127 up.  Integer operations only.
+__device__ __forceinline__ float to_float_error(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull;
+  if (b == 0) return 0.f;
+  const int E = (int)(b >> 52) - 1023;
+  if (E > 126) return __int_as_float(0x7F800000);   // may round to infinity
+  if (E < -126) return 0x1p-149f;
+  if ((b & ((1ull << 29) - 1)) == 0) return 0.f;
+  const int fe = E - 23;   // float ulp at exponent E
+  return fe >= -126 ? __int_as_float((fe + 127) << 23) : __int_as_float(1 << (fe + 149));
 }
 
 // Per-query set-up; the reading of the error box and split weights matches the
@@ -96,20 +113,29 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     e = __longlong_as_double(__double_as_longlong(e) + 1);                   // one ulp up
     Q.ebox_p[x] = f64_ord(e);
     Q.ebox_n[x] = f64_ord(-e);
-    // FP32 filter bounds, all rounded upward.  e32 = 40 * 2^-24 * max(m, 2^-100)
-    // bounds the distance of every FP32 corner from the exact one (derivation
-    // at inclusion32).  A decision taken on the FP32 hull must hold for the
-    // FP64 hull, which is within eps of the exact one:
-    //   tm = e + eps + e32  (beyond it, the FP64 hull misses or sticks out of C)
+    // FP32 filter bounds (derivations at inclusion32).  With S the sum over
+    // the three vectors of |c0| + |dc| on this axis, the FP32 and FP64 hulls
+    // are less than e32 = 8 * 2^-24 * max(S, 2^-100) apart, and the FP64 hull
+    // is within e64 = 4 * 2^-53 S (+ 2^-1060 for subnormals) of R, the hull
+    // evaluated exactly from c0 and dc.  A decision taken on the FP32 hull must
+    // hold for the FP64 hull:
+    //   tm = e + eps + e32  (beyond it, the FP64 hull misses or sticks out of C;
+    //                        eps is spare margin)
     //   wn = (delta (1 + 2^-50) + 2 eps + 2 e32)(1 + 2^-23)  (an FP32 width at or
     //        above it means an FP64 width at or above delta)
-    // (evaluated in single precision, every operation rounded upward, so each
-    // threshold is at least its exact value; delta (1 + 2^-50) is bounded by
+    //   tn = e - e64, rounded down  (an upper bound of R's low end at or below
+    //        it means the FP64 low end is at most e: no miss on that side)
+    // (tm and wn evaluated in single precision, every operation rounded upward,
+    // so each is at least its exact value; delta (1 + 2^-50) is bounded by
     // delta (1 + 2^-23))
-    const float m32 = fmaxf(__double2float_ru(__longlong_as_double((long long)m)), 0x1p-100f);
-    const float e32 = __fmul_ru(m32, 40.0f * 0x1p-24f);
+    double S = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) S = __dadd_ru(__dadd_ru(S, dabs_int(Q.c0[j][x])), dabs_int(Q.dc[j][x]));
+    const float s32 = fmaxf(__double2float_ru(S), 0x1p-100f);
+    const float e32 = __fmul_ru(s32, 8.0f * 0x1p-24f);
     const float eps32 = __double2float_ru(eps), e_32 = __double2float_ru(e);
-    Q.e32[x] = e32;
+    const double e64 = __dadd_ru(__dmul_ru(S, 0x1p-51), 0x1p-1060);
+    Q.tn[x] = __double2float_rd(__dsub_rd(e, e64));
     Q.tm[x] = __fadd_ru(__fadd_ru(e_32, eps32), e32);
     const float d32 = __fmul_ru(__double2float_ru(delta), 1.0f + 0x1p-23f);
     const float wn = __fadd_ru(__fadd_ru(d32, __fmul_ru(2.0f, eps32)), __fmul_ru(2.0f, e32));
@@ -134,6 +160,17 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
       Q.c0f[j][x] = __double2float_rn(Q.c0[j][x]);
       Q.dcf[j][x] = __double2float_rn(Q.dc[j][x]);
     }
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      a = __fadd_ru(a, to_float_error(Q.c0[j][x]));
+      b = __fadd_ru(b, to_float_error(Q.dc[j][x]));
+    }
+    Q.cc0[x] = a;
+    Q.cdc[x] = b;
+  }
   const unsigned long long kFloor = 0x0DF0000000000000ull;  // 2^-800
   Q.K[0] = Lt < kFloor ? 0 : Lt;
   Q.K[1] = Lu < kFloor ? 0 : Lu;
@@ -265,24 +302,50 @@ __device__ __forceinline__ void inclusion(const QueryData &Q, bool vf, double tl
 
 // Single-precision hull of F over an interval with every level <= 24 (its
 // ends are then exact floats), same expression tree and corner selection as
-// inclusion().  Error bound, with u = 2^-24, m the largest |coordinate| on the
-// axis and the FP64 set-up errors (O(2^-53 m)) included:
-//   rounding c0 and dc to float:      2 u m and 4 u m;
-//   c(t) = fma(t, dc, c0):            |c(t) - exact| <= 6 u m + 2 u m = 8 u m;
-//   inner term fma(-v, e2, w):        2 x 8 u m + 4 u m = 20 u m;
-//   corner fma(-u, e1, g):            20 u m + 8 u m + 6 u m = 34 u m;
-// e32 = 40 u m leaves room for second-order and FP64 terms.  Rounding is
-// monotone, so the selected corners are the extremes of the computed ones,
-// and the FP32 hull is within e32 of the exact hull on every axis.
+// inclusion().  Error bound on one axis, with u = 2^-24, c0 and dc the FP64
+// set-up values, S_j = |c0_j| + |dc_j| for the vectors j = w, e1, e2 and
+// S = S_w + S_1 + S_2 (t, u, v in [0, 1]; second-order terms dropped):
+//   c_j(t) = fma(t, dcf, c0f) with c0f, dcf rounded from c0, dc:
+//       |c_j(t) - (c0 + t dc)| <= u |dc| + u |c0| + u S_j = 2 u S_j;
+//   inner term g = fma(-v, c_k, w), one rounding of a value below S_w + S_k:
+//       2 u S_w + 2 u S_k + u (S_w + S_k) = 3 u (S_w + S_k);
+//   corner f = fma(-u, c_i, g): 3 u (S_w + S_k) + 2 u S_i + u S <= 4 u S;
+//   corner choice: a sign of c_i(t) taken wrong in FP32 means |c_i| <= 2 u S_i,
+//       and the chosen corner is then within 2 u S_i of the extreme one, so
+//       both choices together add at most 2 u (S_1 + S_2).
+// That is at most 6 u S from R, the hull evaluated exactly from the FP64 c0
+// and dc.  The same steps in FP64 (no conversion, unit 2^-53) put inclusion()
+// within 4 * 2^-53 S of R.  So on every axis the FP32 and FP64 hulls are less
+// than e32 = 8 u S apart, whatever the size of the coordinates: S is built
+// from differences of vertex positions, not from the positions.
+//
+// e32 is too wide to settle a hull end that lies at or near 0, and such ends
+// are common: start positions in a common plane give corners that are exactly
+// 0 at t = 0, and a vertex on a grid line of the other element gives corners
+// where nonzero terms cancel exactly.  For those the kernel also evaluates the
+// selected low and high corners in interval arithmetic: c_j(t) from
+// fma_rd / fma_ru of (t, dcf, c0f), the corner from outward-rounded fmas of
+// those ends, then widened by conv(t) = cc0 + t cdc, with cc0, cdc bounding
+// the rounding of c0 and dc to float summed over the vectors (the corner's
+// multipliers are at most 1).  L = min over t of the upper bound of R at the
+// low corner bounds R's low end from above (R's low end is at most R at any
+// corner); H likewise from below.  Where every operation is exact the two
+// directions agree and the bound is the exact value, 0 at such an end.  The
+// FP64 low end is then at most L + e64, and the kernel compares L against
+// tn = e - e64.
 struct Box3f {
-  float lo[3], hi[3];
+  float lo[3], hi[3];   // the FP32 hull
+  float L[3], H[3];     // upper bound of R's low end, lower bound of its high end
+  unsigned tb;          // bit x: L[x] came from the t = tr end, bit 3 + x: H[x] did
 };
 
-__device__ __forceinline__ void inclusion32(const float c0f[3][3], const float dcf[3][3], bool vf, float tl, float tr,
-                                            float ul, float ur, float vl, float vr, Box3f &B) {
+__device__ __forceinline__ void inclusion32(const float c0f[3][3], const float dcf[3][3], const float cc0[3],
+                                            const float cdc[3], bool vf, float tl, float tr, float ul, float ur,
+                                            float vl, float vr, Box3f &B) {
+  B.tb = 0;
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
-    float lo = 0.f, hi = 0.f;
+    float lo = 0.f, hi = 0.f, L = 0.f, H = 0.f;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
       const float tt = it ? tr : tl;
@@ -290,23 +353,50 @@ __device__ __forceinline__ void inclusion32(const float c0f[3][3], const float d
       const float a = fmaf(tt, dcf[1][x], c0f[1][x]);
       const float b = fmaf(tt, dcf[2][x], c0f[2][x]);
       const bool ap = a > 0.f, bp = b > 0.f;
+      // multipliers of the low and high corners: u on a, v on b
+      float ulo, uhi, vlo, vhi;
       float fmin, fmax;
       if (vf) {
-        const float gmin = fmaf(-(bp ? vr : vl), b, w);
-        const float gmax = fmaf(-(bp ? vl : vr), b, w);
-        fmin = fmaf(-(ap ? ur : ul), a, gmin);
-        fmax = fmaf(-(ap ? ul : ur), a, gmax);
+        vlo = bp ? vr : vl;
+        vhi = bp ? vl : vr;
+        ulo = ap ? ur : ul;
+        uhi = ap ? ul : ur;
+        fmin = fmaf(-ulo, a, fmaf(-vlo, b, w));
+        fmax = fmaf(-uhi, a, fmaf(-vhi, b, w));
       } else {
-        const float gmin = fmaf(ap ? ul : ur, a, w);
-        const float gmax = fmaf(ap ? ur : ul, a, w);
-        fmin = fmaf(-(bp ? vr : vl), b, gmin);
-        fmax = fmaf(-(bp ? vl : vr), b, gmax);
+        ulo = ap ? ul : ur;
+        uhi = ap ? ur : ul;
+        vlo = bp ? vr : vl;
+        vhi = bp ? vl : vr;
+        fmin = fmaf(-vlo, b, fmaf(ulo, a, w));
+        fmax = fmaf(-vhi, b, fmaf(uhi, a, w));
       }
+      // certified ends: the same corners in interval arithmetic, every
+      // operation rounded outward, widened by the rounding of c0, dc to float
+      const float wu = __fmaf_ru(tt, dcf[0][x], c0f[0][x]), wd = __fmaf_rd(tt, dcf[0][x], c0f[0][x]);
+      const float au = __fmaf_ru(tt, dcf[1][x], c0f[1][x]), ad = __fmaf_rd(tt, dcf[1][x], c0f[1][x]);
+      const float bu = __fmaf_ru(tt, dcf[2][x], c0f[2][x]), bd = __fmaf_rd(tt, dcf[2][x], c0f[2][x]);
+      const float conv = __fmaf_ru(tt, cdc[x], cc0[x]);
+      float Lt, Ht;
+      if (vf) {
+        Lt = __fmaf_ru(-ulo, ad, __fmaf_ru(-vlo, bd, wu));
+        Ht = __fmaf_rd(-uhi, au, __fmaf_rd(-vhi, bu, wd));
+      } else {
+        Lt = __fmaf_ru(-vlo, bd, __fmaf_ru(ulo, au, wu));
+        Ht = __fmaf_rd(-vhi, bu, __fmaf_rd(uhi, ad, wd));
+      }
+      Lt = __fadd_ru(Lt, conv);
+      Ht = __fsub_rd(Ht, conv);
+      if (it) B.tb |= (Lt < L ? 1u << x : 0u) | (Ht > H ? 8u << x : 0u);
       lo = it ? fminf(lo, fmin) : fmin;
       hi = it ? fmaxf(hi, fmax) : fmax;
+      L = it ? fminf(L, Lt) : Lt;
+      H = it ? fmaxf(H, Ht) : Ht;
     }
     B.lo[x] = lo;
     B.hi[x] = hi;
+    B.L[x] = L;
+    B.H[x] = H;
   }
 }
 
@@ -325,6 +415,7 @@ struct SharedQuery {
   double c0[9][kNarrowThreads];
   double dc[9][kNarrowThreads];
   long long ep[3][kNarrowThreads], en[3][kNarrowThreads];
+  float cc0[3][kNarrowThreads], cdc[3][kNarrowThreads];   // used by the FP32 filter
 };
 
 __device__ __forceinline__ void put_shared(SharedQuery &S, int tid, const QueryData &Q) {
@@ -339,6 +430,8 @@ __device__ __forceinline__ void put_shared(SharedQuery &S, int tid, const QueryD
   for (int x = 0; x < 3; ++x) {
     S.ep[x][tid] = Q.ebox_p[x];
     S.en[x][tid] = Q.ebox_n[x];
+    S.cc0[x][tid] = Q.cc0[x];
+    S.cdc[x][tid] = Q.cdc[x];
   }
 }
 
@@ -352,6 +445,8 @@ __device__ __forceinline__ void copy_shared(SharedQuery &S, int dst, int src) {
   for (int x = 0; x < 3; ++x) {
     S.ep[x][dst] = S.ep[x][src];
     S.en[x][dst] = S.en[x][src];
+    S.cc0[x][dst] = S.cc0[x][src];
+    S.cdc[x][dst] = S.cdc[x][src];
   }
 }
 
@@ -478,9 +573,11 @@ __device__ __forceinline__ void store_record(const QueryData &Q, bool vf, unsign
     }
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
-    r32[(f++) * stride + q] = Q.e32[x];
+    r32[(f++) * stride + q] = Q.tn[x];
     r32[(f++) * stride + q] = Q.tm[x];
     r32[(f++) * stride + q] = Q.wn[x];
+    r32[(f++) * stride + q] = Q.cc0[x];
+    r32[(f++) * stride + q] = Q.cdc[x];
   }
 }
 
@@ -517,9 +614,11 @@ __device__ __forceinline__ void load_record(QueryData &Q, bool &vf, const unsign
     }
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
-    Q.e32[x] = __ldg(&r32[(f++) * stride + q]);
+    Q.tn[x] = __ldg(&r32[(f++) * stride + q]);
     Q.tm[x] = __ldg(&r32[(f++) * stride + q]);
     Q.wn[x] = __ldg(&r32[(f++) * stride + q]);
+    Q.cc0[x] = __ldg(&r32[(f++) * stride + q]);
+    Q.cdc[x] = __ldg(&r32[(f++) * stride + q]);
   }
 }
 
@@ -527,7 +626,7 @@ __device__ __forceinline__ void load_record(QueryData &Q, bool &vf, const unsign
 // copies their records into shared memory with cp.async one batch ahead, so
 // that neither the claim (an L2 atomic) nor the record (DRAM) is waited on
 // when lanes take new queries.
-constexpr int kRecFloats = 27;
+constexpr int kRecFloats = 33;
 struct __align__(16) Stage {
   unsigned long long w[kRecWords][kStageQ];
   float f[kRecFloats][kStageQ];
@@ -599,9 +698,11 @@ __device__ __forceinline__ void load_record_stage(QueryData &Q, bool &vf, const 
     }
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
-    Q.e32[x] = S.f[f++][i];
+    Q.tn[x] = S.f[f++][i];
     Q.tm[x] = S.f[f++][i];
     Q.wn[x] = S.f[f++][i];
+    Q.cc0[x] = S.f[f++][i];
+    Q.cdc[x] = S.f[f++][i];
   }
 }
 
@@ -634,7 +735,7 @@ k_narrow(NarrowArgs A) {
   __shared__ SharedQuery SQ;                 // FP64 part of each lane's query
   const int tid = threadIdx.x;
   // single-precision filter data and split keys of the lane's query
-  float c0f[3][3], dcf[3][3], e32[3], tm[3], wn[3];
+  float c0f[3][3], dcf[3][3], tn[3], tm[3], wn[3];
   unsigned long long K[3] = {0, 0, 0};
   bool vf = false;
   int sid = 0;                               // scene of the lane's query (mode 2)
@@ -849,12 +950,12 @@ k_narrow(NarrowArgs A) {
             }
 #pragma unroll
           for (int x = 0; x < 3; ++x) {
-            const float a = __shfl_sync(FULL, e32[x], src);
+            const float a = __shfl_sync(FULL, tn[x], src);
             const float b = __shfl_sync(FULL, tm[x], src);
             const float c = __shfl_sync(FULL, wn[x], src);
             const unsigned long long kk = __shfl_sync(FULL, K[x], src);
             if (recv) {
-              e32[x] = a;
+              tn[x] = a;
               tm[x] = b;
               wn[x] = c;
               K[x] = kk;
@@ -939,7 +1040,7 @@ k_narrow(NarrowArgs A) {
         }
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        e32[x] = Q.e32[x];
+        tn[x] = Q.tn[x];
         tm[x] = Q.tm[x];
         wn[x] = Q.wn[x];
         K[x] = Q.K[x];
@@ -1027,27 +1128,79 @@ k_narrow(NarrowArgs A) {
       n_eval_tail += tail_phase;
       ++since;
       // Single-precision filter: when every level is <= 24 the interval's
-      // ends are exact floats and the FP32 hull is within e32 of the exact
-      // hull; a miss, or a split (no miss, not narrow, not inside), proven on
-      // it is certainly the FP64 decision, so FP64 runs only on the rest.
+      // ends are exact floats and the FP32 hull is within e32 of the FP64
+      // hull, its certified ends L, H bound R's; a miss, or a split (no miss,
+      // not narrow, not inside), proven on it is certainly the FP64 decision,
+      // so FP64 runs only on the rest.
       bool decided = false, miss = false, accept = false;
+      bool full = true;            // the full FP64 evaluation decides
+      unsigned need = 0, tb = 0;   // ends FP32 left open: bit x low, bit 3 + x high
       if (max(max(N.l0, N.l1), N.l2) <= 24) {
         Box3f Bf;
-        inclusion32(c0f, dcf, vf, dyadic32(N.n0, N.l0), dyadic32(N.n0 + 1, N.l0), dyadic32(N.n1, N.l1),
+        float cc0[3], cdc[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          cc0[x] = SQ.cc0[x][tid];
+          cdc[x] = SQ.cdc[x][tid];
+        }
+        inclusion32(c0f, dcf, cc0, cdc, vf, dyadic32(N.n0, N.l0), dyadic32(N.n0 + 1, N.l0), dyadic32(N.n1, N.l1),
                     dyadic32(N.n1 + 1, N.l1), dyadic32(N.n2, N.l2), dyadic32(N.n2 + 1, N.l2), Bf);
-        bool cmiss = false, cnm = true, cni = false, cnn = false;
+        bool cmiss = false, cni = false, cnn = false;
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
           cmiss |= (Bf.lo[x] > tm[x]) | (Bf.hi[x] < -tm[x]);
-          cnm &= (Bf.lo[x] <= -e32[x]) & (Bf.hi[x] >= e32[x]);
+          need |= (Bf.L[x] <= tn[x] ? 0u : 1u << x) | (Bf.H[x] >= -tn[x] ? 0u : 8u << x);
           cni |= (Bf.lo[x] < -tm[x]) | (Bf.hi[x] > tm[x]);
           cnn |= __fsub_rn(Bf.hi[x], Bf.lo[x]) >= wn[x];
         }
+        tb = Bf.tb;
         if (cmiss) {
           decided = miss = true;
-        } else if (cnm & cni & cnn) {
-          decided = true;   // split
+        } else if (cni & cnn) {
+          full = false;
+          decided = need == 0;   // split
         }
+      }
+      // Not narrow and not inside, and "no miss" settled on every end but a
+      // few: each remaining end is checked on one FP64 corner, the one the FP64
+      // hull selects at the t end FP32 points to, computed with the FP64
+      // hull's own operations.  The FP64 low end is the smaller of its two
+      // t ends, so a low corner at or below e means no miss on that side, as
+      // the full evaluation would find; likewise a high corner at or above -e.
+      // An end the corner leaves open goes to the full FP64 evaluation.
+      if (!decided && !full) {
+        const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
+        const double vl = dyadic(N.n2, N.l2), vr = dyadic(N.n2 + 1, N.l2);
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          if (need & (9u << x)) {
+            const bool nlo = (need >> x) & 1u, nhi = (need >> (3 + x)) & 1u;
+            double w = SQ.c0[x][tid], a = SQ.c0[3 + x][tid], b = SQ.c0[6 + x][tid];
+            const double dw = SQ.dc[x][tid], da = SQ.dc[3 + x][tid], db = SQ.dc[6 + x][tid];
+            // an axis with no motion: fma(t, 0, c) is c (up to the sign of a
+            // zero, which neither the selection nor the ordered keys see)
+            if (((__double_as_longlong(dw) | __double_as_longlong(da) | __double_as_longlong(db)) << 1) != 0) {
+              const bool at_r = nlo ? ((tb >> x) & 1u) : ((tb >> (3 + x)) & 1u);
+              const double tt = at_r ? dyadic(N.n0 + 1, N.l0) : tl;
+              w = fma(tt, dw, w);
+              a = fma(tt, da, a);
+              b = fma(tt, db, b);
+            }
+            const bool ap = __double_as_longlong(a) > 0;
+            const bool bp = __double_as_longlong(b) > 0;
+            if (nlo) {
+              const double fmin = vf ? fma(-(ap ? ur : ul), a, fma(-(bp ? vr : vl), b, w))
+                                     : fma(-(bp ? vr : vl), b, fma(ap ? ul : ur, a, w));
+              if (f64_ord(fmin) <= SQ.ep[x][tid]) need &= ~(1u << x);
+            }
+            if (nhi) {
+              const double fmax = vf ? fma(-(ap ? ul : ur), a, fma(-(bp ? vl : vr), b, w))
+                                     : fma(-(bp ? vl : vr), b, fma(ap ? ur : ul, a, w));
+              if (f64_ord(fmax) >= SQ.en[x][tid]) need &= ~(8u << x);
+            }
+          }
+        }
+        decided = need == 0;   // split
       }
       if (!decided) {
         ++n_eval64;
