@@ -204,6 +204,24 @@ struct Node {
   __device__ __forceinline__ int depth() const { return l0 + l1 + l2; }
 };
 
+// Interval ends as integers: n / 2^l scaled by 2^53 (exact, below 2^53 for
+// n < 2^l, l <= 53), and a t* given by its bits as ceil(t* 2^53), at most
+// 2^53.  Then t_lo >= t* is s53(n, l) >= ceil53(t*), and the vertex-face
+// simplex test u_lo + v_lo > 1 is s53(n1, l1) + s53(n2, l2) > 2^53.
+__device__ __forceinline__ uint64_t s53(uint64_t n, int l) { return n << (53 - l); }
+__device__ __forceinline__ uint64_t ceil53(unsigned long long cb) {
+  if (cb >= 0x3FF0000000000000ull) return 1ull << 53;   // t* >= 1 (or +inf): nothing starts there
+  if (cb == 0) return 0;
+  const int sh = 1022 - (int)(cb >> 52);                // t* = m 2^(E - 52), times 2^53 = m >> sh
+  const uint64_t m = (cb & 0x000FFFFFFFFFFFFFull) | ((cb >> 52) ? (1ull << 52) : 0ull);
+  if (sh >= 64) return 1;                               // 0 < t* < 2^-53
+  const uint64_t q = m >> sh;
+  return (q << sh) == m ? q : q + 1;
+}
+__device__ __forceinline__ bool outside_simplex(const Node &N) {
+  return s53(N.n1, N.l1) + s53(N.n2, N.l2) > (1ull << 53);
+}
+
 __device__ __forceinline__ int split_axis(const unsigned long long K[3], const Node &N) {
   const int l[3] = {N.l0, N.l1, N.l2};
   int best = -1;
@@ -240,11 +258,12 @@ __device__ __forceinline__ int shallowest_pending(const unsigned long long K[3],
                                                   int root_depth, unsigned long long cut, Node &S) {
   Node W = N;
   int found = 0;
+  const uint64_t cut53 = ceil53(cut);
   for (int d = depth; d > root_depth; --d) {
     int a = last_axis(K, W);
     if ((W.n(a) & 1) == 0) {
       const uint64_t n0 = a == 0 ? W.n0 + 1 : W.n0;   // the sibling's t numerator
-      if (dbits(dyadic(n0, W.l0)) < cut) {
+      if (s53(n0, W.l0) < cut53) {
         S = W;
         S.add(a, 1);
         found = d;
@@ -398,6 +417,14 @@ __device__ __forceinline__ void inclusion32(const float c0f[3][3], const float d
     B.L[x] = L;
     B.H[x] = H;
   }
+}
+
+// A non-negative float that is 0 or normal, as a double (exact), from bits.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  if (b == 0) return 0.0;
+  const unsigned long long e = (unsigned long long)(b >> 23) + (1023 - 127);
+  return __longlong_as_double((long long)((e << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
 }
 
 // n / 2^l as a float, exact for n <= 2^24 and l <= 24, assembled from bits.
@@ -1094,15 +1121,15 @@ k_narrow(NarrowArgs A) {
     bool node_done = true;     // false when the node was split (go to its left child)
     bool unit_end = false;
     bool evaluate = false;
-    const double tl = dyadic(N.n0, N.l0);
+    const uint64_t cut53 = ceil53(cut);
     if (have) {
-      if (dbits(tl) >= cut) {
+      if (s53(N.n0, N.l0) >= cut53) {
         // pruned: starts at or after the current t*
-      } else if (vf && dbits(dyadic(N.n1, N.l1)) > dbits(dyadic((1ull << N.l2) - N.n2, N.l2))) {
+      } else if (vf && outside_simplex(N)) {
         // vertex-face: u_lo > 1 - v_lo, the interval lies outside the simplex
       } else if (!(A.no_zero && N.n0 == 0) && ++cnt > cap_left) {
         // iteration cap: t* = min(t*, earliest left end among the live intervals)
-        unsigned long long m = dbits(tl);
+        unsigned long long m = dbits(dyadic(N.n0, N.l0));
         Node W = N;
         for (int d = depth; d > root_depth; --d) {
           int a = last_axis(K, W);
@@ -1124,6 +1151,7 @@ k_narrow(NarrowArgs A) {
       }
     }
     if (evaluate) {
+      const double tl = dyadic(N.n0, N.l0);
       ++n_eval;
       n_eval_tail += tail_phase;
       ++since;
@@ -1145,6 +1173,8 @@ k_narrow(NarrowArgs A) {
         }
         inclusion32(c0f, dcf, cc0, cdc, vf, dyadic32(N.n0, N.l0), dyadic32(N.n0 + 1, N.l0), dyadic32(N.n1, N.l1),
                     dyadic32(N.n1 + 1, N.l1), dyadic32(N.n2, N.l2), dyadic32(N.n2 + 1, N.l2), Bf);
+        // (levels <= 24 here: the corner checks below take their ends as
+        // exact doubles from these floats)
         bool cmiss = false, cni = false, cnn = false;
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
@@ -1169,8 +1199,8 @@ k_narrow(NarrowArgs A) {
       // the full evaluation would find; likewise a high corner at or above -e.
       // An end the corner leaves open goes to the full FP64 evaluation.
       if (!decided && !full) {
-        const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
-        const double vl = dyadic(N.n2, N.l2), vr = dyadic(N.n2 + 1, N.l2);
+        const double ul = f2d_exact(dyadic32(N.n1, N.l1)), ur = f2d_exact(dyadic32(N.n1 + 1, N.l1));
+        const double vl = f2d_exact(dyadic32(N.n2, N.l2)), vr = f2d_exact(dyadic32(N.n2 + 1, N.l2));
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
           if (need & (9u << x)) {
@@ -1181,7 +1211,7 @@ k_narrow(NarrowArgs A) {
             // zero, which neither the selection nor the ordered keys see)
             if (((__double_as_longlong(dw) | __double_as_longlong(da) | __double_as_longlong(db)) << 1) != 0) {
               const bool at_r = nlo ? ((tb >> x) & 1u) : ((tb >> (3 + x)) & 1u);
-              const double tt = at_r ? dyadic(N.n0 + 1, N.l0) : tl;
+              const double tt = f2d_exact(dyadic32(N.n0 + (at_r ? 1 : 0), N.l0));
               w = fma(tt, dw, w);
               a = fma(tt, da, a);
               b = fma(tt, db, b);
@@ -1254,8 +1284,8 @@ k_narrow(NarrowArgs A) {
           N.add(a, 1);
           // a right sibling that would be pruned, or that lies outside the
           // vertex-face simplex, is done at once (no iteration spent on it)
-          const bool pruned = dbits(dyadic(N.n0, N.l0)) >= cut;
-          const bool outside = vf && dbits(dyadic(N.n1, N.l1)) > dbits(dyadic((1ull << N.l2) - N.n2, N.l2));
+          const bool pruned = s53(N.n0, N.l0) >= cut53;
+          const bool outside = vf && outside_simplex(N);
           if (!pruned && !outside) break;
         }
         N.up(a);
