@@ -125,17 +125,29 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     //        above it means an FP64 width at or above delta)
     //   tn = e - e64, rounded down  (an upper bound of R's low end at or below
     //        it means the FP64 low end is at most e: no miss on that side)
-    // (tm and wn evaluated in single precision, every operation rounded upward,
-    // so each is at least its exact value; delta (1 + 2^-50) is bounded by
-    // delta (1 + 2^-23))
-    double S = 0.0;
+    // (all in single precision, every operation rounded toward the safe side,
+    // so each threshold is at least (tn: at most) its exact value; S from
+    // |c0| <= |float(c0)| + cc0-term; delta (1 + 2^-50) is bounded by
+    // delta (1 + 2^-23); 2^-149 stands in for 2^-1060)
+    float s32 = 0.f, cc0 = 0.f, cdc = 0.f;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) S = __dadd_ru(__dadd_ru(S, dabs_int(Q.c0[j][x])), dabs_int(Q.dc[j][x]));
-    const float s32 = fmaxf(__double2float_ru(S), 0x1p-100f);
+    for (int j = 0; j < 3; ++j) {
+      const float cf = __double2float_rn(Q.c0[j][x]), df = __double2float_rn(Q.dc[j][x]);
+      const float ec = to_float_error(Q.c0[j][x]), ed = to_float_error(Q.dc[j][x]);
+      Q.c0f[j][x] = cf;
+      Q.dcf[j][x] = df;
+      cc0 = __fadd_ru(cc0, ec);
+      cdc = __fadd_ru(cdc, ed);
+      s32 = __fadd_ru(s32, __fadd_ru(fabsf(cf), ec));
+      s32 = __fadd_ru(s32, __fadd_ru(fabsf(df), ed));
+    }
+    Q.cc0[x] = cc0;
+    Q.cdc[x] = cdc;
+    s32 = fmaxf(s32, 0x1p-100f);
     const float e32 = __fmul_ru(s32, 8.0f * 0x1p-24f);
     const float eps32 = __double2float_ru(eps), e_32 = __double2float_ru(e);
-    const double e64 = __dadd_ru(__dmul_ru(S, 0x1p-51), 0x1p-1060);
-    Q.tn[x] = __double2float_rd(__dsub_rd(e, e64));
+    const float e64 = __fmaf_ru(s32, 0x1p-51f, 0x1p-149f);
+    Q.tn[x] = __fsub_rd(__double2float_rd(e), e64);
     Q.tm[x] = __fadd_ru(__fadd_ru(e_32, eps32), e32);
     const float d32 = __fmul_ru(__double2float_ru(delta), 1.0f + 0x1p-23f);
     const float wn = __fadd_ru(__fadd_ru(d32, __fmul_ru(2.0f, eps32)), __fmul_ru(2.0f, e32));
@@ -152,24 +164,6 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     v0 = v1 > v0 ? v1 : v0;
     Lu = u0 > Lu ? u0 : Lu;
     Lv = v0 > Lv ? v0 : Lv;
-  }
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      Q.c0f[j][x] = __double2float_rn(Q.c0[j][x]);
-      Q.dcf[j][x] = __double2float_rn(Q.dc[j][x]);
-    }
-#pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    float a = 0.f, b = 0.f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      a = __fadd_ru(a, to_float_error(Q.c0[j][x]));
-      b = __fadd_ru(b, to_float_error(Q.dc[j][x]));
-    }
-    Q.cc0[x] = a;
-    Q.cdc[x] = b;
   }
   const unsigned long long kFloor = 0x0DF0000000000000ull;  // 2^-800
   Q.K[0] = Lt < kFloor ? 0 : Lt;
