@@ -89,7 +89,8 @@ struct NarrowArgs {
   int64_t rec_stride;
 };
 
-__global__ void k_narrow(NarrowArgs A);
+__global__ void k_narrow(NarrowArgs A);         // on query records (A.qrec required)
+__global__ void k_narrow_setup(NarrowArgs A);   // lanes set queries up themselves (A.qrec unused)
 __global__ void k_prepare_queries(NarrowArgs A);
 __global__ void k_ring_init(RingCell *ring, unsigned long long cap, unsigned long long base);
 __global__ void k_nozero_prepare(DevCtl *ctl);

@@ -55,16 +55,50 @@ __device__ __forceinline__ unsigned long long dbits(double d) {
   return (unsigned long long)__double_as_longlong(d);
 }
 
-// An upper bound of |float(d) - d| for round-to-nearest: 0 when d is a float
-// (its low 29 significand bits are zero and it lies in the normal float
-// range), else one float ulp at d's exponent; 2^-149 below the normal range,
-// infinity from 2^127 up.  Integer operations only.
+// Conversions of doubles to float from their bits (integer operations only:
+// on this GPU the conversion instructions share the narrow FP64 pipe).
+// d2f_near: nearest, ties away from zero (error at most half an ulp); below
+// the normal float range 0, from 2^128 up infinity.
+__device__ __forceinline__ float d2f_near(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7FF) - 1023;
+  if (E < -126) return __uint_as_float(sign);
+  if (E > 127) return __uint_as_float(sign | 0x7F800000u);
+  // round the 52-bit fraction to 23 bits; a carry out of the fraction raises
+  // the exponent (to infinity from the top binade)
+  const unsigned frac = (unsigned)(((b & 0x000FFFFFFFFFFFFFull) + (1ull << 28)) >> 29);
+  return __uint_as_float(sign | (((unsigned)(E + 127) << 23) + frac));
+}
+// d2f_up / d2f_down for d >= 0: the float at or above / at or below d.
+__device__ __forceinline__ float d2f_up(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  if (b == 0) return 0.f;
+  const int E = (int)(b >> 52) - 1023;
+  if (E < -126) return 0x1p-126f;
+  if (E > 127) return __int_as_float(0x7F800000);
+  const unsigned long long f = b & 0x000FFFFFFFFFFFFFull;
+  const unsigned up = (f & ((1ull << 29) - 1)) != 0 ? 1u : 0u;
+  return __uint_as_float(((unsigned)(E + 127) << 23) + (unsigned)(f >> 29) + up);
+}
+__device__ __forceinline__ float d2f_down(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)(b >> 52) - 1023;
+  if (E < -126) return 0.f;
+  if (E > 127) return __int_as_float(0x7F7FFFFF);
+  return __uint_as_float(((unsigned)(E + 127) << 23) + (unsigned)((b & 0x000FFFFFFFFFFFFFull) >> 29));
+}
+
+// An upper bound of |d2f_near(d) - d|: 0 when d is a float (its low 29
+// significand bits are zero and it lies in the normal float range), else one
+// float ulp at d's exponent; 2^-126 below the normal range (d2f_near gives 0
+// there), infinity from 2^127 up.  Integer operations only.
 __device__ __forceinline__ float to_float_error(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull;
   if (b == 0) return 0.f;
   const int E = (int)(b >> 52) - 1023;
   if (E > 126) return __int_as_float(0x7F800000);   // may round to infinity
-  if (E < -126) return 0x1p-149f;
+  if (E < -126) return 0x1p-126f;
   if ((b & ((1ull << 29) - 1)) == 0) return 0.f;
   const int fe = E - 23;   // float ulp at exponent E
   return fe >= -126 ? __int_as_float((fe + 127) << 23) : __int_as_float(1 << (fe + 149));
@@ -132,7 +166,7 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     float s32 = 0.f, cc0 = 0.f, cdc = 0.f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const float cf = __double2float_rn(Q.c0[j][x]), df = __double2float_rn(Q.dc[j][x]);
+      const float cf = d2f_near(Q.c0[j][x]), df = d2f_near(Q.dc[j][x]);
       const float ec = to_float_error(Q.c0[j][x]), ed = to_float_error(Q.dc[j][x]);
       Q.c0f[j][x] = cf;
       Q.dcf[j][x] = df;
@@ -145,11 +179,11 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     Q.cdc[x] = cdc;
     s32 = fmaxf(s32, 0x1p-100f);
     const float e32 = __fmul_ru(s32, 8.0f * 0x1p-24f);
-    const float eps32 = __double2float_ru(eps), e_32 = __double2float_ru(e);
+    const float eps32 = d2f_up(eps), e_32 = d2f_up(e);
     const float e64 = __fmaf_ru(s32, 0x1p-51f, 0x1p-149f);
-    Q.tn[x] = __fsub_rd(__double2float_rd(e), e64);
+    Q.tn[x] = __fsub_rd(d2f_down(e), e64);
     Q.tm[x] = __fadd_ru(__fadd_ru(e_32, eps32), e32);
-    const float d32 = __fmul_ru(__double2float_ru(delta), 1.0f + 0x1p-23f);
+    const float d32 = __fmul_ru(d2f_up(delta), 1.0f + 0x1p-23f);
     const float wn = __fadd_ru(__fadd_ru(d32, __fmul_ru(2.0f, eps32)), __fmul_ru(2.0f, e32));
     Q.wn[x] = __fmul_ru(wn, 1.0f + 0x1p-23f);
     double st = __dadd_rn(dabs_int(Q.dc[0][x]), dabs_int(Q.dc[1][x]));
@@ -737,8 +771,8 @@ constexpr int kRefresh = 8;            // iterations between reads of the shared
 // decided for the whole warp (ballots and broadcasts), and the per-lane work
 // sits in structured branches, so the lanes of a warp reconverge every
 // iteration and the FP64 instructions of an interval issue once per warp.
-__global__ void __launch_bounds__(kNarrowThreads, 3)
-k_narrow(NarrowArgs A) {
+template <bool kRecords>
+__device__ __forceinline__ void narrow_body(NarrowArgs A) {
   DevCtl *ctl = A.ctl;
   if (A.only_if_rerun && ctl->rerun == 0) return;
   if (A.counts_from_ctl) {
@@ -799,7 +833,7 @@ k_narrow(NarrowArgs A) {
   uint32_t s_base = 0, n_base = 0;           // query indices are below 2^32
   unsigned long long c_reg = 0;
   bool claims_done = false;                  // warp-uniform: a claim came back empty
-  const bool staged = A.qrec != nullptr;
+  const bool staged = kRecords;
   if (staged) {
     unsigned long long b0 = 0, b1 = 0;
     if (lane == 0) {
@@ -1038,12 +1072,14 @@ k_narrow(NarrowArgs A) {
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
       QueryData Q;
-      if (slot >= 0) {
-        load_record_stage(Q, vf, ST[sbuf], slot);
-        sid = A.mode == 2 ? ST[sbuf].sid[slot] : 0;
-      } else if (A.qrec) {
-        load_record(Q, vf, A.qrec, A.rec_stride, q);
-        sid = A.mode == 2 ? A.qsid[q] : 0;
+      if constexpr (kRecords) {
+        if (slot >= 0) {
+          load_record_stage(Q, vf, ST[sbuf], slot);
+          sid = A.mode == 2 ? ST[sbuf].sid[slot] : 0;
+        } else {
+          load_record(Q, vf, A.qrec, A.rec_stride, q);
+          sid = A.mode == 2 ? A.qsid[q] : 0;
+        }
       } else {
         int ids[4];
         query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
@@ -1364,6 +1400,13 @@ k_narrow(NarrowArgs A) {
   if (lane == 0) atomicMax(&ctl->t_end, globaltimer());
 }
 #undef ST
+
+// The narrow phase on query records (k_prepare_queries), and the same loop
+// with each lane setting its queries up itself (no record buffer: the
+// allocation-free entry point).  Two kernels, so that neither carries the
+// other's code.
+__global__ void __launch_bounds__(kNarrowThreads, 3) k_narrow(NarrowArgs A) { narrow_body<true>(A); }
+__global__ void __launch_bounds__(kNarrowThreads, 3) k_narrow_setup(NarrowArgs A) { narrow_body<false>(A); }
 
 // One thread per query: gather the 4 vertices at t = 0 and t = 1 and store the
 // query's set-up as a record, so that the narrow kernel's lanes set up a unit

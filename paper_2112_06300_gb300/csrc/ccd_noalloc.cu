@@ -81,7 +81,7 @@ int setup_device(int dev, cudaStream_t s, DeviceState **out) {
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return CCD_ECUDA;
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CCD_ECUDA;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow, kNarrowThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow_setup, kNarrowThreads, 0) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     k_noalloc_init<<<64, 256, 0, s>>>((unsigned char *)p);
@@ -148,7 +148,7 @@ extern "C" int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t
   A.qiters = (unsigned long long *)(base + kCtlBytes + kFlagsBytes);
   A.ring = (RingCell *)(base + kCtlBytes + kFlagsBytes + kItersBytes);
   A.ring_mask = kRingCells - 1;
-  k_narrow<<<st->blocks, kNarrowThreads, 0, s>>>(A);
+  k_narrow_setup<<<st->blocks, kNarrowThreads, 0, s>>>(A);
   if (mode == 0 && n_vf + n_ee > 0)
     k_flags_out<<<64, 256, 0, s>>>(A.qflags, n_vf, n_ee, flags_vf, flags_ee, ctl);
   if (cudaMemcpyAsync(toi_min, &ctl->toi_bits, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)

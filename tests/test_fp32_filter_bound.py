@@ -161,13 +161,14 @@ def test_bound_is_local_not_global():
 
 def to_float_error(d: float) -> Q:
     """The bound the set-up uses for |float(d) - d|: 0 for a float, one
-    float ulp at d's exponent otherwise, 2^-149 below the normal range."""
+    float ulp at d's exponent otherwise, 2^-126 below the normal range (where
+    the set-up's conversion gives 0)."""
     if d == 0:
         return Q(0)
     m, E = np.frexp(abs(d))          # abs(d) = m 2^E, m in [0.5, 1)
     E = int(E) - 1                   # unbiased exponent
     if E < -126:
-        return Q(1, 2 ** 149)
+        return Q(1, 2 ** 126)
     assert E <= 126
     if float(np.float32(d)) == d:
         return Q(0)
