@@ -800,6 +800,14 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   int64_t q = 0;
   Node N{0, 0, 0, 0, 0, 0};
   int depth = 0, root_depth = 0;
+  // the path as bit masks over depths 1..63: pend bit d is set while the path
+  // node at depth d is a left child whose right sibling is still owed, and
+  // bit d of (AX[1], AX[0]) (shared, per lane) is the axis that was split to
+  // reach depth d; a unit that goes deeper (`deep`) backtracks by walking the
+  // path instead
+  __shared__ unsigned long long AX[2][kNarrowThreads];
+  unsigned long long pend = 0;
+  bool deep = false;
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
   long long cnt = 0, cap_left = 0, since = 0;   // since: evaluations since the last hand-off
   unsigned flags = 0;
@@ -1032,6 +1040,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
             vf = vfv != 0;
             N = Node{s0, s1, s2, l0, l1, l2};
             depth = root_depth = N.depth();
+            pend = 0;
+            deep = depth > 63;
             tq = tqv;
             cap_left = capv;
             cnt = since = 0;
@@ -1103,6 +1113,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         K[x] = Q.K[x];
       }
       depth = root_depth = N.depth();
+      pend = 0;
+      deep = depth > 63;
       cnt = since = 0;
       flags = 0;
       tq = kInfBits;
@@ -1298,12 +1310,51 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           N.down_left(a);
           depth += 1;
           node_done = false;
+          if (depth < 64) {
+            const unsigned long long bit = 1ull << depth;
+            pend |= bit;
+            AX[0][tid] = (a & 1) ? (AX[0][tid] | bit) : (AX[0][tid] & ~bit);
+            AX[1][tid] = (a & 2) ? (AX[1][tid] | bit) : (AX[1][tid] & ~bit);
+          } else {
+            deep = true;
+          }
         }
       }
     }
 
     // ---- 5. next node: backtrack to the deepest pending right sibling ------
-    if (have && node_done && !unit_end) {
+    if (have && node_done && !unit_end && !deep) {
+      // jump to the deepest owed sibling: undo the splits below it per axis
+      // (popcounts of the axis masks), take the right sibling, and go on
+      // while the sibling is pruned or outside the simplex
+      const unsigned long long above_root = root_depth >= 63 ? 0ull : ~0ull << (root_depth + 1);
+      while (true) {
+        const unsigned long long m = pend & above_root;
+        if (m == 0) {
+          unit_end = true;
+          break;
+        }
+        const int ds = 63 - __clzll((long long)m);
+        const unsigned long long axlo = AX[0][tid], axhi = AX[1][tid];
+        const unsigned long long r =
+            (depth >= 63 ? ~0ull : (2ull << depth) - 1) & (ds >= 63 ? 0ull : ~0ull << (ds + 1));
+        const int c1 = __popcll(r & axlo & ~axhi), c2 = __popcll(r & axhi);
+        const int c0 = depth - ds - c1 - c2;
+        N.n0 >>= c0;
+        N.l0 -= c0;
+        N.n1 >>= c1;
+        N.l1 -= c1;
+        N.n2 >>= c2;
+        N.l2 -= c2;
+        const int a = (int)((axlo >> ds) & 1ull) | ((int)((axhi >> ds) & 1ull) << 1);
+        N.add(a, 1);
+        depth = ds;
+        pend &= ~(~0ull << ds);
+        const bool pruned = s53(N.n0, N.l0) >= cut53;
+        const bool outside = vf && outside_simplex(N);
+        if (!pruned && !outside) break;
+      }
+    } else if (have && node_done && !unit_end) {
       while (true) {
         if (depth == root_depth) {
           unit_end = true;

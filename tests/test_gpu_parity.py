@@ -139,6 +139,30 @@ def test_narrow_stress_mix_matches_oracle(ctx, ccd, n, seed):
     _assert_per_pair(r, o)
 
 
+def test_narrow_deep_trees_match_oracle(ctx, ccd):
+    """delta = 1e-10 takes the bisection past 63 levels in total (most of the
+    evaluations here), the depth the kernel's path masks cover; deeper units
+    backtrack by walking the path.  The reference is the oracle without an
+    iteration cap: the GPU result equals it wherever the GPU did not cap the
+    query, and is never later where it did (a query split across lanes can
+    reach the cap in a different place; capped results are conservative)."""
+    sc, vf, ee = _stress(2000, 9)
+    delta = 1e-10
+    r, _ = _narrow_both(ctx, ccd, sc, vf, ee, delta=delta)
+    ox = O.narrow(vf, ee, sc.V0, sc.V1, sc.E, sc.F, delta, 0.0, 10 ** 8, 0)
+    t = np.concatenate([ox[0], ox[1]])
+    assert not np.concatenate([ox[2], ox[3]]).any()
+    g = np.concatenate([r.toi_vf.cpu().numpy(), r.toi_ee.cpu().numpy()])
+    gf = np.concatenate([r.flags_vf.cpu().numpy(), r.flags_ee.cpu().numpy()])
+    assert (gf == 0).mean() > 0.99
+    np.testing.assert_array_equal(g[gf == 0].view(np.uint64), t[gf == 0].view(np.uint64))
+    assert (g[gf != 0] <= t[gf != 0]).all()
+    r1, _ = _narrow_both(ctx, ccd, sc, vf, ee, delta=delta, mode=1)
+    assert r1.toi_min <= ox[4]
+    if not gf.any():
+        assert r1.toi_min == ox[4]
+
+
 def test_narrow_min_sep_matches_oracle(ctx, ccd):
     sc, vf, ee = _stress(600, 8)
     r, o = _narrow_both(ctx, ccd, sc, vf, ee, ms=1e-4, max_iter=20000)
