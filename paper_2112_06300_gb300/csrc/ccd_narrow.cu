@@ -302,6 +302,33 @@ __device__ __forceinline__ int shallowest_pending(const unsigned long long K[3],
   return found;
 }
 
+// shallowest_pending on the path masks of the narrow kernel (units no deeper
+// than 63): pend bit d marks an owed right sibling at depth d, (axhi, axlo)
+// bit d the axis split to reach depth d.  The owed siblings are visited from
+// the shallowest; the first that starts before `cut` is returned.
+__device__ __forceinline__ int shallowest_owed(const Node &N, int depth, int root_depth, unsigned long long pend,
+                                               unsigned long long axlo, unsigned long long axhi,
+                                               unsigned long long cut, Node &S) {
+  const uint64_t cut53 = ceil53(cut);
+  unsigned long long m = pend & (root_depth >= 63 ? 0ull : ~0ull << (root_depth + 1));
+  const unsigned long long upto = depth >= 63 ? ~0ull : (2ull << depth) - 1;
+  while (m) {
+    const int d = __ffsll((long long)m) - 1;
+    const unsigned long long r = upto & (d >= 63 ? 0ull : ~0ull << (d + 1));
+    const int c1 = __popcll(r & axlo & ~axhi), c2 = __popcll(r & axhi);
+    const int c0 = depth - d - c1 - c2;
+    Node W{N.n0 >> c0, N.n1 >> c1, N.n2 >> c2, N.l0 - c0, N.l1 - c1, N.l2 - c2};
+    const int a = (int)((axlo >> d) & 1ull) | ((int)((axhi >> d) & 1ull) << 1);
+    if (s53(a == 0 ? W.n0 + 1 : W.n0, W.l0) < cut53) {
+      S = W;
+      S.add(a, 1);
+      return d;
+    }
+    m &= m - 1;
+  }
+  return 0;
+}
+
 struct Box3 {
   double lo[3], hi[3];
 };
@@ -988,7 +1015,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           unsigned long long c = tq;
           if (A.mode == 1) c = min(c, pf_toi_b);
           if (A.mode == 2) c = min(c, pf_scene);
-          dS = shallowest_pending(K, N, depth, root_depth, c, S);
+          dS = deep ? shallowest_pending(K, N, depth, root_depth, c, S)
+                    : shallowest_owed(N, depth, root_depth, pend, AX[0][tid], AX[1][tid], c, S);
         }
         const unsigned donors = __ballot_sync(FULL, dS > 0);
         const int pairs = min(__popc(donors), __popc(idle));
@@ -1382,7 +1410,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
         if (want_exp) {
-          dS = shallowest_pending(K, N, depth, root_depth, cut, S);
+          dS = deep ? shallowest_pending(K, N, depth, root_depth, cut, S)
+                    : shallowest_owed(N, depth, root_depth, pend, AX[0][tid], AX[1][tid], cut, S);
           since = 0;
         }
         const unsigned xm = __ballot_sync(FULL, dS > 0);
