@@ -913,18 +913,59 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_tiled(SweepArgs A) {
   }
 }
 
-// Strip sweep (single-precision form).  Tiled like k_sweep_tiled, over the
-// sorted box copies: a copy's sweep range ends at the first copy whose key
-// exceeds (its strip segment, its maximum on the sweep axis), so it never
-// leaves its strip, and a pair is kept only when one of its two copies lies
-// in its box's first strip.  A thread owns two adjacent copies, so a warp's
-// 64 copies and their short in-strip ranges cover a narrow window of each
-// shared tile, and the warp walks only that window.  Candidates (vertex-face
-// or edge-edge, no shared vertex) collect in a per-warp shared buffer that is
-// flushed with one atomic per 256 pairs; the exact FP64 test runs afterwards
-// over the whole list (k_exact_filter).  The grid is persistent: the number
-// of copies is known only on the device.
+// Cell sweep (single-precision form), over the sorted box copies: a copy's
+// sweep range ends at the first copy whose key exceeds (its cell, its maximum
+// on the sweep axis), so it never leaves its cell, and a pair is kept only in
+// the cell where, on each cell axis, one of its two copies lies in its box's
+// first cell.  One thread per copy walks its own range (a few dozen copies):
+// neighbouring lanes read neighbouring copies, so the loads coalesce and are
+// served from L1, and a warp runs as many steps as its longest range.
+// Candidates (vertex-face or edge-edge, no shared vertex) collect in a
+// per-warp shared buffer that is flushed with one atomic per 256 pairs; the
+// exact FP64 test runs afterwards over the whole list (k_exact_filter).  The
+// grid is persistent: the number of copies is known only on the device.
 constexpr int kSupBuf = 256;
+
+// End of a copy's sweep range: the first index after i whose sorted key
+// exceeds the target.  The ranges are short, so the search gallops from i + 1
+// (probes i+1, i+2, i+4, ...) and bisects only the last gap: a handful of
+// neighbouring loads instead of a bisection over the whole array.
+__device__ __forceinline__ int64_t range_end(const unsigned long long *__restrict__ key, int64_t i, int64_t n,
+                                             unsigned long long target) {
+  int64_t lo = i + 1, hi = i + 1, step = 1;   // keys in [i + 1, lo) are <= target
+  while (hi < n && key[hi] <= target) {
+    lo = hi + 1;
+    hi += step;
+    step <<= 1;
+  }
+  hi = hi < n ? hi : n;                        // key[hi] > target, or hi == n
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (key[mid] <= target) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// The same on (cell, ordered FP64 minimum) pairs, compared lexicographically.
+__device__ __forceinline__ int64_t range_end64(const uint32_t *__restrict__ seg_of, const long long *__restrict__ key,
+                                               int64_t i, int64_t n, uint32_t seg, long long target) {
+  auto le = [&](int64_t j) {
+    const uint32_t sj = seg_of[j];
+    return sj < seg || (sj == seg && key[j] <= target);
+  };
+  int64_t lo = i + 1, hi = i + 1, step = 1;
+  while (hi < n && le(hi)) {
+    lo = hi + 1;
+    hi += step;
+    step <<= 1;
+  }
+  hi = hi < n ? hi : n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (le(mid)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
 
 __device__ __forceinline__ void sup_flush(const SweepArgs &A, uint2 *buf, int &cnt) {
   const int lane = threadIdx.x & 31;
@@ -938,230 +979,132 @@ __device__ __forceinline__ void sup_flush(const SweepArgs &A, uint2 *buf, int &c
 }
 
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
-  __shared__ float4 sh_oth[kTJ];
-  __shared__ int4 sh_vid[kTJ];
   __shared__ uint2 sh_sup[kSweepThreads / 32][kSupBuf];
-  __shared__ unsigned long long sh_end;
   const int64_t n = (int64_t)*A.n_dev;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  uint2 *buf = sh_sup[wid];
+  const int lane = threadIdx.x & 31;
+  uint2 *buf = sh_sup[threadIdx.x >> 5];
   int nbuf = 0;   // warp-uniform
   const int64_t ie = min(n, A.i_end);
-  for (int64_t i0 = A.i_begin + (int64_t)blockIdx.x * kTI; i0 < ie; i0 += (int64_t)gridDim.x * kTI) {
-    float ahi[2];
-    float4 oi[2];
-    int4 vi[2];
-    int ki[2];
-    unsigned fi[2];
-    const int li[2] = {2 * tid, 2 * tid + 1};   // local indices of the thread's two copies
-    int endl[2] = {li[0] + 1, li[1] + 1};      // no copy: empty range
-    int64_t end_max = i0;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int64_t i = i0 + li[r];
-      ahi[r] = -__int_as_float(0x7F800000);
-      oi[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-      vi[r] = make_int4(-1, -1, -1, 0);
-      fi[r] = 0u;
-      if (i < ie) {
-        ahi[r] = A.s_ahi[i];
-        oi[r] = A.s_oth[i];
-        vi[r] = A.s_vid[i];
-        fi[r] = ((uint32_t)vi[r].w >> 30) & 3u;   // first cell on each axis
-        vi[r].w &= 0x3FFFFFFF;
-        const unsigned long long target = (A.s_key[i] & 0xFFFFFFFF00000000ull) | f32_sort_key(ahi[r]);
-        int64_t lo = i + 1, hi = n;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (A.s_key[mid] <= target) lo = mid + 1; else hi = mid;
-        }
-        endl[r] = (int)(lo - i0);
-        end_max = lo > end_max ? lo : end_max;
-      }
-      ki[r] = box_kind(vi[r].w, A.nV, A.nE);
+  const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+  // a warp takes 32 consecutive copies per round (warp-uniform loop)
+  for (int64_t base = A.i_begin + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ie;
+       base += wstride) {
+    const int64_t i = base + lane;
+    float4 oi = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 vi = make_int4(-1, -1, -1, 0);
+    unsigned fi = 0u;
+    int64_t end = i + 1;   // no copy: empty range
+    if (i < ie) {
+      oi = A.s_oth[i];
+      vi = A.s_vid[i];
+      fi = ((uint32_t)vi.w >> 30) & 3u;   // first cell on each axis
+      vi.w &= 0x3FFFFFFF;
+      const unsigned long long target = (A.s_key[i] & 0xFFFFFFFF00000000ull) | f32_sort_key(A.s_ahi[i]);
+      end = range_end(A.s_key, i, n, target);
     }
-    // the warp's window of local j indices: [64 w + 1, largest end)
-    int wend = max(endl[0], endl[1]);
+    const int ki = box_kind(vi.w, A.nV, A.nE);
+    // the copy's range (i, end), 4 copies a step: neighbouring lanes read
+    // neighbouring copies, so the loads coalesce and mostly hit L1; ids are
+    // loaded for overlapping pairs only, one per lane per round
+    for (int64_t j0 = i + 1; __any_sync(0xFFFFFFFFu, j0 < end); j0 += 4) {
+      unsigned hits = 0;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) wend = max(wend, __shfl_xor_sync(0xFFFFFFFFu, wend, o));
-    const int wbeg = 64 * wid + 1;
-    if (tid == 0) sh_end = (unsigned long long)i0;
-    __syncthreads();
-    atomicMax(&sh_end, (unsigned long long)end_max);
-    __syncthreads();
-    const int64_t jend = (int64_t)sh_end;
-    const unsigned span0 = (unsigned)(endl[0] - li[0] - 1), span1 = (unsigned)(endl[1] - li[1] - 1);
-    for (int64_t jt = i0 + 1; jt < jend; jt += kTJ) {
-      __syncthreads();
-      for (int k = tid; k < kTJ; k += kSweepThreads) {
-        const int64_t j = jt + k;
-        if (j < n) {
-          sh_oth[k] = A.s_oth[j];
-          sh_vid[k] = A.s_vid[j];
+      for (int u = 0; u < 4; ++u) {
+        if (j0 + u < end) {
+          const float4 oj = A.s_oth[j0 + u];
+          hits |= ((oj.x <= oi.y) & (oi.x <= oj.y) & (oj.z <= oi.w) & (oi.z <= oj.w)) ? 1u << u : 0u;
         }
       }
-      __syncthreads();
-      const int jl0 = (int)(jt - i0);
-      const int kb = max(0, wbeg - jl0) & ~3;
-      const int ke = (int)min((int64_t)min(kTJ, wend - jl0), jend - jt);
-      for (int k = kb; k < ke; k += 4) {
-        unsigned bits = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 oj = sh_oth[k + u];
-          const unsigned fj = ((uint32_t)sh_vid[k + u].w >> 30) & 3u;
-          const int jl = jl0 + k + u;
-          const bool h0 = ((unsigned)(jl - li[0] - 1) < span0) & ((fi[0] | fj) == 3u) & (oj.x <= oi[0].y) &
-                          (oi[0].x <= oj.y) & (oj.z <= oi[0].w) & (oi[0].z <= oj.w);
-          const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & ((fi[1] | fj) == 3u) & (oj.x <= oi[1].y) &
-                          (oi[1].x <= oj.y) & (oj.z <= oi[1].w) & (oi[1].z <= oj.w);
-          bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
-        }
-        if (__any_sync(0xFFFFFFFFu, bits)) {
-#pragma unroll
-          for (int bb = 0; bb < 8; ++bb) {
-            bool keep = false;
-            uint2 pr = make_uint2(0u, 0u);
-            if ((bits >> bb) & 1u) {
-              const int r = bb & 1;
-              int4 vj = sh_vid[k + (bb >> 1)];
-              vj.w &= 0x3FFFFFFF;
-              bool vf;
-              int p0, p1;
-              if (candidate(vi[r], ki[r], vj, A.nV, A.nE, vf, p0, p1)) {
-                keep = true;
-                pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)p1);
-              }
-            }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
-            if (m) {
-              if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
-              if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
-              nbuf += __popc(m);
-              __syncwarp();
-            }
+      while (__any_sync(0xFFFFFFFFu, hits)) {
+        bool keep = false;
+        uint2 pr = make_uint2(0u, 0u);
+        if (hits) {
+          const int u = __ffs((int)hits) - 1;
+          hits &= hits - 1u;
+          int4 vj = A.s_vid[j0 + u];
+          const unsigned fj = ((uint32_t)vj.w >> 30) & 3u;
+          vj.w &= 0x3FFFFFFF;
+          bool vf;
+          int p0, p1;
+          if ((fi | fj) == 3u && candidate(vi, ki, vj, A.nV, A.nE, vf, p0, p1)) {
+            keep = true;
+            pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)p1);
           }
         }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+        if (m) {
+          if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
+          if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
+          nbuf += __popc(m);
+          __syncwarp();
+        }
       }
     }
-    __syncthreads();
   }
   if (nbuf) sup_flush(A, buf, nbuf);
 }
 
-// FP64 strip sweep: k_sweep_strips on the FP64 extents (ordered int64 keys,
+// FP64 cell sweep: k_sweep_strips on the FP64 extents (ordered int64 keys,
 // exact comparisons).  A copy's range ends at the first copy with a larger
-// (segment, minimum) than (its segment, its maximum).
+// (cell, minimum) than (its cell, its maximum).
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
-  __shared__ longlong2 sh_oth[kTJ][2];
-  __shared__ int4 sh_vid[kTJ];
   __shared__ uint2 sh_sup[kSweepThreads / 32][kSupBuf];
-  __shared__ unsigned long long sh_end;
   const int64_t n = (int64_t)*A.n_dev;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  uint2 *buf = sh_sup[wid];
-  int nbuf = 0;
+  const int lane = threadIdx.x & 31;
+  uint2 *buf = sh_sup[threadIdx.x >> 5];
+  int nbuf = 0;   // warp-uniform
   const int64_t ie = min(n, A.i_end);
-  for (int64_t i0 = A.i_begin + (int64_t)blockIdx.x * kTI; i0 < ie; i0 += (int64_t)gridDim.x * kTI) {
-    long long ahi[2];
-    longlong2 o1[2], o2[2];
-    int4 vi[2];
-    int ki[2];
-    unsigned fi[2];
-    const int li[2] = {2 * tid, 2 * tid + 1};
-    int endl[2] = {li[0] + 1, li[1] + 1};
-    int64_t end_max = i0;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int64_t i = i0 + li[r];
-      ahi[r] = (long long)0x8000000000000000ull;   // no copy: every test fails
-      o1[r] = o2[r] = make_longlong2(0, 0);
-      vi[r] = make_int4(-1, -1, -1, 0);
-      fi[r] = 0u;
-      if (i < ie) {
-        ahi[r] = A.s_ahi64c[i];
-        o1[r] = A.s_oth64c[2 * i];
-        o2[r] = A.s_oth64c[2 * i + 1];
-        vi[r] = A.s_vid[i];
-        fi[r] = ((uint32_t)vi[r].w >> 30) & 3u;   // first cell on each axis
-        vi[r].w &= 0x3FFFFFFF;
-        const uint32_t seg = A.s_seg[i];
-        int64_t lo = i + 1, hi = n;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          const uint32_t sm = A.s_seg[mid];
-          if (sm < seg || (sm == seg && A.s_key64[mid] <= ahi[r])) lo = mid + 1; else hi = mid;
-        }
-        endl[r] = (int)(lo - i0);
-        end_max = lo > end_max ? lo : end_max;
-      }
-      ki[r] = box_kind(vi[r].w, A.nV, A.nE);
+  const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = A.i_begin + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ie;
+       base += wstride) {
+    const int64_t i = base + lane;
+    longlong2 o1 = make_longlong2(0, 0), o2 = make_longlong2(0, 0);
+    int4 vi = make_int4(-1, -1, -1, 0);
+    unsigned fi = 0u;
+    int64_t end = i + 1;
+    if (i < ie) {
+      o1 = A.s_oth64c[2 * i];
+      o2 = A.s_oth64c[2 * i + 1];
+      vi = A.s_vid[i];
+      fi = ((uint32_t)vi.w >> 30) & 3u;   // first cell on each axis
+      vi.w &= 0x3FFFFFFF;
+      end = range_end64(A.s_seg, A.s_key64, i, n, A.s_seg[i], A.s_ahi64c[i]);
     }
-    int wend = max(endl[0], endl[1]);
+    const int ki = box_kind(vi.w, A.nV, A.nE);
+    for (int64_t j0 = i + 1; __any_sync(0xFFFFFFFFu, j0 < end); j0 += 4) {
+      unsigned hits = 0;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) wend = max(wend, __shfl_xor_sync(0xFFFFFFFFu, wend, o));
-    const int wbeg = 64 * wid + 1;
-    if (tid == 0) sh_end = (unsigned long long)i0;
-    __syncthreads();
-    atomicMax(&sh_end, (unsigned long long)end_max);
-    __syncthreads();
-    const int64_t jend = (int64_t)sh_end;
-    const unsigned span0 = (unsigned)(endl[0] - li[0] - 1), span1 = (unsigned)(endl[1] - li[1] - 1);
-    for (int64_t jt = i0 + 1; jt < jend; jt += kTJ) {
-      __syncthreads();
-      for (int k = tid; k < kTJ; k += kSweepThreads) {
-        const int64_t j = jt + k;
-        if (j < n) {
-          sh_oth[k][0] = A.s_oth64c[2 * j];
-          sh_oth[k][1] = A.s_oth64c[2 * j + 1];
-          sh_vid[k] = A.s_vid[j];
+      for (int u = 0; u < 4; ++u) {
+        if (j0 + u < end) {
+          const longlong2 p1 = A.s_oth64c[2 * (j0 + u)], p2 = A.s_oth64c[2 * (j0 + u) + 1];
+          hits |= ((p1.x <= o1.y) & (o1.x <= p1.y) & (p2.x <= o2.y) & (o2.x <= p2.y)) ? 1u << u : 0u;
         }
       }
-      __syncthreads();
-      const int jl0 = (int)(jt - i0);
-      const int kb = max(0, wbeg - jl0) & ~3;
-      const int ke = (int)min((int64_t)min(kTJ, wend - jl0), jend - jt);
-      for (int k = kb; k < ke; k += 4) {
-        unsigned bits = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const longlong2 p1 = sh_oth[k + u][0], p2 = sh_oth[k + u][1];
-          const unsigned fj = ((uint32_t)sh_vid[k + u].w >> 30) & 3u;
-          const int jl = jl0 + k + u;
-          const bool h0 = ((unsigned)(jl - li[0] - 1) < span0) & ((fi[0] | fj) == 3u) & (p1.x <= o1[0].y) &
-                          (o1[0].x <= p1.y) & (p2.x <= o2[0].y) & (o2[0].x <= p2.y);
-          const bool h1 = ((unsigned)(jl - li[1] - 1) < span1) & ((fi[1] | fj) == 3u) & (p1.x <= o1[1].y) &
-                          (o1[1].x <= p1.y) & (p2.x <= o2[1].y) & (o2[1].x <= p2.y);
-          bits |= ((unsigned)h0 << (2 * u)) | ((unsigned)h1 << (2 * u + 1));
-        }
-        if (__any_sync(0xFFFFFFFFu, bits)) {
-#pragma unroll
-          for (int bb = 0; bb < 8; ++bb) {
-            bool keep = false;
-            uint2 pr = make_uint2(0u, 0u);
-            if ((bits >> bb) & 1u) {
-              const int r = bb & 1;
-              int4 vj = sh_vid[k + (bb >> 1)];
-              vj.w &= 0x3FFFFFFF;
-              bool vf;
-              int p0, p1;
-              if (candidate(vi[r], ki[r], vj, A.nV, A.nE, vf, p0, p1)) {
-                keep = true;
-                pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)p1);
-              }
-            }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
-            if (m) {
-              if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
-              if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
-              nbuf += __popc(m);
-              __syncwarp();
-            }
+      while (__any_sync(0xFFFFFFFFu, hits)) {
+        bool keep = false;
+        uint2 pr = make_uint2(0u, 0u);
+        if (hits) {
+          const int u = __ffs((int)hits) - 1;
+          hits &= hits - 1u;
+          int4 vj = A.s_vid[j0 + u];
+          const unsigned fj = ((uint32_t)vj.w >> 30) & 3u;
+          vj.w &= 0x3FFFFFFF;
+          bool vf;
+          int p0, q1;
+          if ((fi | fj) == 3u && candidate(vi, ki, vj, A.nV, A.nE, vf, p0, q1)) {
+            keep = true;
+            pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)q1);
           }
         }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+        if (m) {
+          if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
+          if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
+          nbuf += __popc(m);
+          __syncwarp();
+        }
       }
     }
-    __syncthreads();
   }
   if (nbuf) sup_flush(A, buf, nbuf);
 }
