@@ -194,32 +194,88 @@ __device__ __forceinline__ void pick_axes(const double var[3], int &a, int &a1) 
     if (k != a && var[k] > var[a1]) a1 = k;
 }
 
+// Float-float sums (a float and its rounding error) for the statistics: the
+// reduction runs on the FP32 pipe (this GPU's FP64 pipe is narrow), with
+// about twice float precision, ample for an axis choice and a cell size.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF x, float yh, float yl) {
+  const float s = x.hi + yh;
+  const float bb = s - x.hi;
+  float e = (x.hi - (s - bb)) + (yh - bb);   // exact error of s (two-sum)
+  e += x.lo + yl;
+  const float h = s + e;
+  return FF{h, e - (h - s)};
+}
+
 __global__ void k_axis_select(const float *partials, int nblocks, int64_t nB, DevCtl *ctl, StripParam *sp,
                               float strip_factor) {
-  __shared__ double acc[kStatWords][32];
-  double s[kStatWords];
-  for (int j = 0; j < 9; ++j) s[j] = 0.0;
-  for (int j = 9; j < 12; ++j) s[j] = __int_as_float(0x7F800000);
-  for (int j = 12; j < 15; ++j) s[j] = -__int_as_float(0x7F800000);
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
-    for (int j = 0; j < 9; ++j) s[j] += (double)partials[kStatWords * i + j];
-    for (int j = 9; j < 12; ++j) s[j] = fmin(s[j], (double)partials[kStatWords * i + j]);
-    for (int j = 12; j < 15; ++j) s[j] = fmax(s[j], (double)partials[kStatWords * i + j]);
+  __shared__ float acc[24][32];   // per warp: 9 sums (high, low parts), 3 minima, 3 maxima
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  FF s[9];
+  float mn[3], mx[3];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) s[j] = FF{0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mn[a] = __int_as_float(0x7F800000);
+    mx[a] = -__int_as_float(0x7F800000);
   }
-  for (int j = 0; j < kStatWords; ++j)
-    for (int o = 16; o; o >>= 1) {
-      const double y = __shfl_xor_sync(0xFFFFFFFFu, s[j], o);
-      s[j] = j < 9 ? s[j] + y : (j < 12 ? fmin(s[j], y) : fmax(s[j], y));
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) s[j] = ff_add(s[j], partials[kStatWords * i + j], 0.f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      mn[a] = fminf(mn[a], partials[kStatWords * i + 9 + a]);
+      mx[a] = fmaxf(mx[a], partials[kStatWords * i + 12 + a]);
     }
-  if ((threadIdx.x & 31) == 0)
-    for (int j = 0; j < kStatWords; ++j) acc[j][threadIdx.x >> 5] = s[j];
-  __syncthreads();
+  }
+  // within each warp, then across the warps (warp 0)
+  for (int round = 0; round < 2; ++round) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j)
+        s[j] = ff_add(s[j], __shfl_xor_sync(0xFFFFFFFFu, s[j].hi, o), __shfl_xor_sync(0xFFFFFFFFu, s[j].lo, o));
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        mn[a] = fminf(mn[a], __shfl_xor_sync(0xFFFFFFFFu, mn[a], o));
+        mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xFFFFFFFFu, mx[a], o));
+      }
+    }
+    if (round == 1) break;
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        acc[j][w] = s[j].hi;
+        acc[9 + j][w] = s[j].lo;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        acc[18 + a][w] = mn[a];
+        acc[21 + a][w] = mx[a];
+      }
+    }
+    __syncthreads();
+    if (w != 0) return;
+    const bool have = lane < (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) s[j] = have ? FF{acc[j][lane], acc[9 + j][lane]} : FF{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      mn[a] = have ? acc[18 + a][lane] : __int_as_float(0x7F800000);
+      mx[a] = have ? acc[21 + a][lane] : -__int_as_float(0x7F800000);
+    }
+  }
   if (threadIdx.x == 0) {
     double t[kStatWords];
-    for (int j = 0; j < kStatWords; ++j) {
-      t[j] = acc[j][0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-        t[j] = j < 9 ? t[j] + acc[j][w] : (j < 12 ? fmin(t[j], acc[j][w]) : fmax(t[j], acc[j][w]));
+#pragma unroll
+    for (int j = 0; j < 9; ++j) t[j] = (double)s[j].hi + (double)s[j].lo;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      t[9 + a] = mn[a];
+      t[12 + a] = mx[a];
     }
     double inv = nB > 0 ? 1.0 / (double)nB : 0.0;
     double var[3];
