@@ -966,7 +966,11 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
                             : 0;
         if (lane == 0 && got) atomicAdd(&ctl->pending, (unsigned long long)got);
       }
-      if (exhausted && __any_sync(FULL, !have) && __shfl_sync(FULL, pf_occ, 0) > 0) {
+      // Only a warp with no work at all takes from the ring: a warp with busy
+      // lanes fills its idle ones by donation below (shuffles and shared
+      // memory), which costs none of the ring's L2 round trips that would
+      // otherwise sit on the path of the tail's long queries.
+      if (exhausted && __ballot_sync(FULL, have) == 0 && __shfl_sync(FULL, pf_occ, 0) > 0) {
         // pop up to one cell per idle lane: lanes test the cells' sequence
         // numbers in parallel, lane 0 claims the ready prefix with one CAS
         const unsigned m = __ballot_sync(FULL, !have);
@@ -999,8 +1003,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           whole = false;
         }
       }
-      // Intra-warp donation: lanes still idle (no query left, nothing ready in
-      // the ring) take the shallowest pending sibling of a busy lane of their
+      // Intra-warp donation: lanes still idle (no query left; the ring is for
+      // idle warps) take the shallowest pending sibling of a busy lane of their
       // own warp; the query data moves by shuffles, the donor keeps the rest
       // of its subtree (its root moves down to the donated sibling's depth).
       const unsigned idle = __ballot_sync(FULL, !have);
