@@ -75,8 +75,10 @@ typedef struct {
     int64_t pair_capacity;   /* initial pair-buffer capacity used by ccd_step
                                 (0 = auto); grows on demand in synchronous calls */
     int64_t queue_capacity;  /* interval-queue slots, a power of two (0 = auto) */
-    int32_t export_budget;   /* intervals a lane processes before handing its
-                                remaining intervals to the queue (0 = auto) */
+    int32_t export_budget;   /* tail phase: every 32 x export_budget intervals a
+                                warp evaluates, its busy lanes hand their
+                                shallowest pending siblings to the queue
+                                (0 = 16) */
     int32_t profile_stages;  /* 1: record CUDA events around the stages of each
                                 call (read with ccd_stage_times); default 0 */
     int32_t no_zero_toi;     /* 1: ccd_step applies the zero-TOI rule of the appendix
@@ -239,7 +241,8 @@ int ccd_step_batch(ccd_ctx *ctx, int32_t n_scenes, const int64_t *vert_off, cons
 /* Settings chosen by ccd_autotune. */
 typedef struct {
     int32_t sweep_kernel;    /* 0 cells or 2 tiled */
-    int32_t export_budget;   /* intervals between hand-offs in the tail phase */
+    int32_t export_budget;   /* tail phase: a warp hands off every 32 x this many
+                                evaluations */
     double strip_width;      /* cell width in mean box widths (cell sweep) */
     int64_t queue_capacity;  /* interval-queue slots */
     double broad_ms;         /* median broad-phase time with the chosen settings */

@@ -535,7 +535,7 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   A.min_sep = min_sep;
   A.max_iter = max_iter;
   A.mode = mode;
-  A.budget = c->opts.export_budget > 0 ? c->opts.export_budget : 64;
+  A.budget = c->opts.export_budget > 0 ? c->opts.export_budget : 16;
   A.no_zero = zero_rule_pass ? 1 : 0;
   A.only_if_rerun = zero_rule_pass ? 1 : 0;
   A.toi_vf_bits = toi_vf_bits;
@@ -1081,11 +1081,11 @@ int autotune_impl(ccd_ctx *c, const SceneSpec &sc, const double *V0, const doubl
   c->opts.strip_width = best_w;
   timed(false);   // pairs of the chosen sweep for the narrow trials
   // 2. narrow: intervals between hand-offs in the tail phase
-  const int budgets[] = {16, 32, 64, 128, 256};
+  const int budgets[] = {8, 16, 32, 64};
   c->opts.export_budget = saved.export_budget;
   const double base_n = timed(true);
   double best_n = 1e30;
-  int best_budget = 64;
+  int best_budget = 16;
   long long peak = 0;
   for (int b : budgets) {
     c->opts.export_budget = b;

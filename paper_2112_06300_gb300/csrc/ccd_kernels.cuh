@@ -71,7 +71,8 @@ struct NarrowArgs {
   double delta, min_sep;
   long long max_iter;
   int mode;                      // 0 per pair, 1 earliest only, 2 earliest per scene
-  int budget;                    // intervals before a lane hands out its work
+  int budget;                    // tail phase: every 32 x budget evaluations of a warp, its busy
+                                 // lanes hand out their shallowest pending siblings
   int no_zero;                   // zero-TOI rule: intervals with t_lo = 0 are always split
   int only_if_rerun;             // return at once unless ctl->rerun is set
   unsigned long long *toi_vf_bits, *toi_ee_bits;   // mode 0 outputs (bits of doubles)

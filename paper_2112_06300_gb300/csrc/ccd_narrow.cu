@@ -836,10 +836,11 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   unsigned long long pend = 0;
   bool deep = false;
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
-  long long cnt = 0, cap_left = 0, since = 0;   // since: evaluations since the last hand-off
+  long long cnt = 0, cap_left = 0;
   unsigned flags = 0;
   long long n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0, n_eval64 = 0;
   int idle_rounds = 0;
+  long long wsince = 0;   // warp-uniform: evaluations of the warp in the tail since its last hand-off
   unsigned ended_acc = 0;                    // warp-uniform: ended units not yet subtracted from pending
   unsigned nap = kNapMin;                    // warp-uniform: idle back-off (ns)
   // Shared values (global t*, next query, the scene's t*) are read from L2
@@ -1076,7 +1077,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
             deep = depth > 63;
             tq = tqv;
             cap_left = capv;
-            cnt = since = 0;
+            cnt = 0;
             flags = 0;
             have = true;
             whole = false;
@@ -1147,7 +1148,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       depth = root_depth = N.depth();
       pend = 0;
       deep = depth > 63;
-      cnt = since = 0;
+      cnt = 0;
       flags = 0;
       tq = kInfBits;
       cap_left = A.max_iter;
@@ -1228,7 +1229,6 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       const double tl = dyadic(N.n0, N.l0);
       ++n_eval;
       n_eval_tail += tail_phase;
-      ++since;
       // Single-precision filter: when every level is <= 24 the interval's
       // ends are exact floats and the FP32 hull is within e32 of the FP64
       // hull, its certified ends L, H bound R's; a miss, or a split (no miss,
@@ -1409,14 +1409,16 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     // ---- 6. in the tail phase, hand the shallowest pending sibling to the
     //         ring every `budget` evaluations; one reservation per warp -------
     {
-      const bool want_exp = have && !unit_end && tail_phase && since >= A.budget;
+      if (tail_phase) wsince += __popc(__ballot_sync(FULL, evaluate));
+      const bool trig = wsince >= 32ll * A.budget;   // (tail phase only)
+      if (trig) wsince = 0;
+      const bool want_exp = trig && have && !unit_end;
       if (__any_sync(FULL, want_exp)) {
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
         if (want_exp) {
           dS = deep ? shallowest_pending(K, N, depth, root_depth, cut, S)
                     : shallowest_owed(N, depth, root_depth, pend, AX[0][tid], AX[1][tid], cut, S);
-          since = 0;
         }
         const unsigned xm = __ballot_sync(FULL, dS > 0);
         if (xm) {

@@ -201,8 +201,8 @@ def test_narrow_earliest_mode(ctx, ccd):
 
 @pytest.mark.parametrize("budget,qcap", [(1, 0), (4, 0), (2, 64)])
 def test_narrow_handoff_paths_keep_results(ccd, budget, qcap):
-    # export after every interval (everything goes through the ring), and a
-    # ring too small to take most hand-offs: results must not change
+    # hand-offs every 32 evaluations of a warp (most work goes through the
+    # ring), and a ring too small to take most hand-offs: results must not change
     c = ccd.CCD(0, export_budget=budget, queue_capacity=qcap)
     try:
         s = scenes.folded_cloth(40, seed=1)
