@@ -838,7 +838,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
   long long cnt = 0, cap_left = 0;
   unsigned flags = 0;
-  long long n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0, n_eval64 = 0;
+  unsigned n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0, n_eval64 = 0;   // per lane, per launch
   int idle_rounds = 0;
   long long wsince = 0;   // warp-uniform: evaluations of the warp in the tail since its last hand-off
   unsigned ended_acc = 0;                    // warp-uniform: ended units not yet subtracted from pending
