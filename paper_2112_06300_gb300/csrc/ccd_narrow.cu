@@ -484,11 +484,9 @@ __device__ __forceinline__ double f2d_exact(float f) {
 
 // n / 2^l as a float, exact for n <= 2^24 and l <= 24, assembled from bits.
 __device__ __forceinline__ float dyadic32(uint64_t n, int l) {
-  if (n == 0) return 0.f;
-  const unsigned v = (unsigned)n;
-  const int msb = 31 - __clz((int)v);
-  const unsigned frac = (msb <= 23 ? (v << (23 - msb)) : (v >> (msb - 23))) & 0x7FFFFFu;
-  return __uint_as_float(((unsigned)(msb - l + 127) << 23) | frac);
+  // n <= 2^24 converts exactly; scaling by 2^-l moves the exponent only
+  const float f = __uint2float_rn((unsigned)n);
+  return n == 0 ? 0.f : __int_as_float(__float_as_int(f) - (l << 23));
 }
 
 // The FP64 part of a lane's query, kept in shared memory (structure of
@@ -1228,7 +1226,6 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       }
     }
     if (evaluate) {
-      const double tl = dyadic(N.n0, N.l0);
       ++n_eval;
       n_eval_tail += tail_phase;
       // Single-precision filter: when every level is <= 24 the interval's
@@ -1314,7 +1311,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
         const double vl = dyadic(N.n2, N.l2), vr = dyadic(N.n2 + 1, N.l2);
         Box3 B;
-        inclusion_shared(SQ, tid, vf, tl, tr, ul, ur, vl, vr, B);
+        inclusion_shared(SQ, tid, vf, dyadic(N.n0, N.l0), tr, ul, ur, vl, vr, B);
         bool inside = true, narrow = true;
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
@@ -1337,7 +1334,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           }
         }
         if (accept) {
-          tq = dbits(tl);
+          tq = dbits(dyadic(N.n0, N.l0));
           if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);
           if (A.mode == 2) atomicMin(&A.toi_scene[sid], tq);
         } else {
