@@ -303,28 +303,27 @@ __device__ __forceinline__ int shallowest_pending(const unsigned long long K[3],
 }
 
 // shallowest_pending on the path masks of the narrow kernel (units no deeper
-// than 63): pend bit d marks an owed right sibling at depth d, (axhi, axlo)
+// than 31): pend bit d marks an owed right sibling at depth d, (axhi, axlo)
 // bit d the axis split to reach depth d.  The owed siblings are visited from
 // the shallowest; the first that starts before `cut` is returned.
-__device__ __forceinline__ int shallowest_owed(const Node &N, int depth, int root_depth, unsigned long long pend,
-                                               unsigned long long axlo, unsigned long long axhi,
-                                               unsigned long long cut, Node &S) {
+__device__ __forceinline__ int shallowest_owed(const Node &N, int depth, int root_depth, unsigned pend,
+                                               unsigned axlo, unsigned axhi, unsigned long long cut, Node &S) {
   const uint64_t cut53 = ceil53(cut);
-  unsigned long long m = pend & (root_depth >= 63 ? 0ull : ~0ull << (root_depth + 1));
-  const unsigned long long upto = depth >= 63 ? ~0ull : (2ull << depth) - 1;
+  unsigned m = pend & (root_depth >= 31 ? 0u : ~0u << (root_depth + 1));
+  const unsigned upto = depth >= 31 ? ~0u : (2u << depth) - 1u;
   while (m) {
-    const int d = __ffsll((long long)m) - 1;
-    const unsigned long long r = upto & (d >= 63 ? 0ull : ~0ull << (d + 1));
-    const int c1 = __popcll(r & axlo & ~axhi), c2 = __popcll(r & axhi);
+    const int d = __ffs((int)m) - 1;
+    const unsigned r = upto & (d >= 31 ? 0u : ~0u << (d + 1));
+    const int c1 = __popc(r & axlo & ~axhi), c2 = __popc(r & axhi);
     const int c0 = depth - d - c1 - c2;
     Node W{N.n0 >> c0, N.n1 >> c1, N.n2 >> c2, N.l0 - c0, N.l1 - c1, N.l2 - c2};
-    const int a = (int)((axlo >> d) & 1ull) | ((int)((axhi >> d) & 1ull) << 1);
+    const int a = (int)((axlo >> d) & 1u) | ((int)((axhi >> d) & 1u) << 1);
     if (s53(a == 0 ? W.n0 + 1 : W.n0, W.l0) < cut53) {
       S = W;
       S.add(a, 1);
       return d;
     }
-    m &= m - 1;
+    m &= m - 1u;
   }
   return 0;
 }
@@ -827,13 +826,11 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   int64_t q = 0;
   Node N{0, 0, 0, 0, 0, 0};
   int depth = 0, root_depth = 0;
-  // the path as bit masks over depths 1..63: pend bit d is set while the path
+  // the path as bit masks over depths 1..31: pend bit d is set while the path
   // node at depth d is a left child whose right sibling is still owed, and
-  // bit d of (AX[1], AX[0]) (shared, per lane) is the axis that was split to
-  // reach depth d; a unit that goes deeper (`deep`) backtracks by walking the
-  // path instead
-  __shared__ unsigned long long AX[2][kNarrowThreads];
-  unsigned long long pend = 0;
+  // bit d of (axhi, axlo) is the axis that was split to reach depth d; a unit
+  // that goes deeper (`deep`) backtracks by walking the path instead
+  unsigned pend = 0, axlo = 0, axhi = 0;
   bool deep = false;
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
   long long cnt = 0, cap_left = 0;
@@ -1021,7 +1018,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           if (A.mode == 1) c = min(c, pf_toi_b);
           if (A.mode == 2) c = min(c, pf_scene);
           dS = deep ? shallowest_pending(K, N, depth, root_depth, c, S)
-                    : shallowest_owed(N, depth, root_depth, pend, AX[0][tid], AX[1][tid], c, S);
+                    : shallowest_owed(N, depth, root_depth, pend, axlo, axhi, c, S);
         }
         const unsigned donors = __ballot_sync(FULL, dS > 0);
         const int pairs = min(__popc(donors), __popc(idle));
@@ -1074,7 +1071,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
             N = Node{s0, s1, s2, l0, l1, l2};
             depth = root_depth = N.depth();
             pend = 0;
-            deep = depth > 63;
+            deep = depth > 31;
             tq = tqv;
             cap_left = capv;
             cnt = 0;
@@ -1147,7 +1144,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       }
       depth = root_depth = N.depth();
       pend = 0;
-      deep = depth > 63;
+      deep = depth > 31;
       cnt = 0;
       flags = 0;
       tq = kInfBits;
@@ -1341,11 +1338,11 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           N.down_left(a);
           depth += 1;
           node_done = false;
-          if (depth < 64) {
-            const unsigned long long bit = 1ull << depth;
+          if (depth < 32) {
+            const unsigned bit = 1u << depth;
             pend |= bit;
-            AX[0][tid] = (a & 1) ? (AX[0][tid] | bit) : (AX[0][tid] & ~bit);
-            AX[1][tid] = (a & 2) ? (AX[1][tid] | bit) : (AX[1][tid] & ~bit);
+            axlo = (a & 1) ? (axlo | bit) : (axlo & ~bit);
+            axhi = (a & 2) ? (axhi | bit) : (axhi & ~bit);
           } else {
             deep = true;
           }
@@ -1358,18 +1355,16 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       // jump to the deepest owed sibling: undo the splits below it per axis
       // (popcounts of the axis masks), take the right sibling, and go on
       // while the sibling is pruned or outside the simplex
-      const unsigned long long above_root = root_depth >= 63 ? 0ull : ~0ull << (root_depth + 1);
+      const unsigned above_root = root_depth >= 31 ? 0u : ~0u << (root_depth + 1);
       while (true) {
-        const unsigned long long m = pend & above_root;
+        const unsigned m = pend & above_root;
         if (m == 0) {
           unit_end = true;
           break;
         }
-        const int ds = 63 - __clzll((long long)m);
-        const unsigned long long axlo = AX[0][tid], axhi = AX[1][tid];
-        const unsigned long long r =
-            (depth >= 63 ? ~0ull : (2ull << depth) - 1) & (ds >= 63 ? 0ull : ~0ull << (ds + 1));
-        const int c1 = __popcll(r & axlo & ~axhi), c2 = __popcll(r & axhi);
+        const int ds = 31 - __clz((int)m);
+        const unsigned r = (depth >= 31 ? ~0u : (2u << depth) - 1u) & (ds >= 31 ? 0u : ~0u << (ds + 1));
+        const int c1 = __popc(r & axlo & ~axhi), c2 = __popc(r & axhi);
         const int c0 = depth - ds - c1 - c2;
         N.n0 >>= c0;
         N.l0 -= c0;
@@ -1377,10 +1372,10 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         N.l1 -= c1;
         N.n2 >>= c2;
         N.l2 -= c2;
-        const int a = (int)((axlo >> ds) & 1ull) | ((int)((axhi >> ds) & 1ull) << 1);
+        const int a = (int)((axlo >> ds) & 1u) | ((int)((axhi >> ds) & 1u) << 1);
         N.add(a, 1);
         depth = ds;
-        pend &= ~(~0ull << ds);
+        pend &= ~(~0u << ds);
         const bool pruned = s53(N.n0, N.l0) >= cut53;
         const bool outside = vf && outside_simplex(N);
         if (!pruned && !outside) break;
@@ -1417,7 +1412,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         int dS = 0;
         if (want_exp) {
           dS = deep ? shallowest_pending(K, N, depth, root_depth, cut, S)
-                    : shallowest_owed(N, depth, root_depth, pend, AX[0][tid], AX[1][tid], cut, S);
+                    : shallowest_owed(N, depth, root_depth, pend, axlo, axhi, cut, S);
         }
         const unsigned xm = __ballot_sync(FULL, dS > 0);
         if (xm) {

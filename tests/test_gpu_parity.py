@@ -140,8 +140,8 @@ def test_narrow_stress_mix_matches_oracle(ctx, ccd, n, seed):
 
 
 def test_narrow_deep_trees_match_oracle(ctx, ccd):
-    """delta = 1e-10 takes the bisection past 63 levels in total (most of the
-    evaluations here), the depth the kernel's path masks cover; deeper units
+    """delta = 1e-10 takes the bisection past 31 and 63 levels in total (most
+    of the evaluations here), beyond the depth the kernel's path masks cover; deeper units
     backtrack by walking the path.  The reference is the oracle without an
     iteration cap: the GPU result equals it wherever the GPU did not cap the
     query, and is never later where it did (a query split across lanes can
