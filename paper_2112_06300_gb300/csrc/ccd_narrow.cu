@@ -409,7 +409,10 @@ __device__ __forceinline__ void inclusion(const QueryData &Q, bool vf, double tl
 struct Box3f {
   float lo[3], hi[3];   // the FP32 hull
   float L[3], H[3];     // upper bound of R's low end, lower bound of its high end
-  unsigned tb;          // bit x: L[x] came from the t = tr end, bit 3 + x: H[x] did
+  unsigned tb;          // t end of the FP64 corner check, bit x for a low end, bit 3 + x for a
+                        // high end (1: right end).  Left end throughout: taking the end the
+                        // certified bound came from settled no more ends on the cloth and cost
+                        // more.
 };
 
 __device__ __forceinline__ void inclusion32(const float c0f[3][3], const float dcf[3][3], const float cc0[3],
@@ -460,7 +463,6 @@ __device__ __forceinline__ void inclusion32(const float c0f[3][3], const float d
       }
       Lt = __fadd_ru(Lt, conv);
       Ht = __fsub_rd(Ht, conv);
-      if (it) B.tb |= (Lt < L ? 1u << x : 0u) | (Ht > H ? 8u << x : 0u);
       lo = it ? fminf(lo, fmin) : fmin;
       hi = it ? fmaxf(hi, fmax) : fmax;
       L = it ? fminf(L, Lt) : Lt;
@@ -1263,8 +1265,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       }
       // Not narrow and not inside, and "no miss" settled on every end but a
       // few: each remaining end is checked on one FP64 corner, the one the FP64
-      // hull selects at the t end FP32 points to, computed with the FP64
-      // hull's own operations.  The FP64 low end is the smaller of its two
+      // hull selects at the t end tb names, computed with the FP64 hull's own
+      // operations.  The FP64 low end is the smaller of its two
       // t ends, so a low corner at or below e means no miss on that side, as
       // the full evaluation would find; likewise a high corner at or above -e.
       // An end the corner leaves open goes to the full FP64 evaluation.
