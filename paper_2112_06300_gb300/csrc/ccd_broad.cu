@@ -1,21 +1,30 @@
 // Broad phase: boxes (Section "Construction of the Boxes") and
 // sweep-and-prune (Section "Broad-Phase", Algorithm 2).
 //
-//   k_build_boxes   one thread per box: FP64 extents over t = 0 and t = 1 of
-//                   the box's 1-3 vertices, single-precision box by directed
-//                   rounding (round-down / round-up, the same float the paper's
-//                   round-to-nearest-then-nextafterf rule gives), order-
-//                   preserving integer keys of the FP64 extents for the exact
-//                   test, and per-block sums for the centre variance.
-//   k_axis_select   axis of largest centre variance (affects speed only).
-//   k_radix_*       stable LSD radix sort of (key = ordered bits of the
-//                   minimum on the sweep axis, value = box id), 4 x 8 bits.
-//   k_gather_sorted box data in sorted order, structure of arrays.
-//   k_sweep         one warp per sorted box i: lanes test i against
-//                   j = i+1, i+2, ... while min_a(j) <= max_a(i), with the two
-//                   other axes, the vertex-face / edge-edge rule, the
-//                   shared-vertex filter and the exact FP64 box test fused;
-//                   surviving pairs are appended with one atomic per warp.
+//   k_build_boxes    one thread per box: FP64 extents over t = 0 and t = 1 of
+//                    the box's 1-3 vertices, single-precision box by directed
+//                    rounding (round-down / round-up, the same float the
+//                    paper's round-to-nearest-then-nextafterf rule gives),
+//                    order-preserving integer keys of the FP64 extents for the
+//                    exact test, and per-block statistics (centre variance,
+//                    mean widths, extents).
+//   k_axis_select    sweep axis (largest centre variance) and the cell layout
+//                    on the two other axes (both affect speed only).
+//   k_*_copies       one copy of each box per cell it overlaps, keyed by
+//                    (cell, ordered bits of the minimum on the sweep axis).
+//   k_radix_*        stable LSD radix sort of the keys, 8 bits per pass.
+//   k_sweep_strips   the cell sweep (default): one thread per sorted copy
+//                    walks its range in its cell; a pair is reported in one
+//                    cell only; candidates go to a list for the exact filter.
+//   k_exact_filter   the FP64 box test, vertex-face / edge-edge split and
+//                    compaction of the candidate list.
+//   k_sweep          Algorithm 2 as printed (sweep_kernel = 1): one warp per
+//                    sorted box i, lanes test i against j = i+1, i+2, ... while
+//                    min_a(j) <= max_a(i), with the two other axes, the
+//                    vertex-face / edge-edge rule, the shared-vertex filter and
+//                    the exact FP64 box test fused.
+//   k_sweep_tiled    one sorted list, tiles staged in shared memory
+//                    (sweep_kernel = 2).
 
 #include "ccd_common.cuh"
 #include "ccd_kernels.cuh"

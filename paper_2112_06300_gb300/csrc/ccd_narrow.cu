@@ -6,21 +6,25 @@
 //     or a subtree of one) and walks it depth first, left half first.  The
 //     split axis depends only on the interval's levels (see split_axis), so
 //     every node at a given depth has the same levels and the DFS needs no
-//     stack: the path is the binary expansion of the three numerators.
-//   * Load balance at interval granularity: after `budget` intervals a lane
-//     hands its live intervals (the current one and the pending right
-//     siblings) to a device-wide bounded MPMC ring and takes new work; idle
-//     lanes drain the ring before fetching new queries.  A single
-//     near-degenerate query (tens of thousands of intervals) is thus spread
-//     over many lanes, which is the point of the paper's per-interval
-//     parallelism, without its level-synchronous launches.
-//   * FP64 is the scarce unit on this GPU.  Per interval: 18 DFMA for the two
-//     time ends (w, e1, e2 per axis), 24 DFMA for the corner hull and 3 DADD
-//     for the width test.  The hull needs only 2 of the 4 (u, v) corners per
-//     time end and axis: rounding is monotone, so the minimum of the computed
-//     corners is the corner picked by the signs of the computed edge vectors,
-//     bit for bit the same as the minimum over all corners.  Comparisons,
-//     min/max, dyadic endpoints and the split rule run on the integer pipes.
+//     stack: the path is the binary expansion of the three numerators, kept
+//     as bit masks of owed siblings and split axes for depths up to 31.
+//   * Load balance at interval granularity: once every query has been
+//     claimed, idle lanes take the shallowest owed sibling of a busy lane of
+//     their warp, and every 32 x `budget` evaluations a warp hands its lanes'
+//     shallowest owed siblings to a device-wide bounded MPMC ring, which idle
+//     warps drain.  A near-degenerate query (tens of thousands of intervals)
+//     is thus spread over many lanes, which is the point of the paper's
+//     per-interval parallelism, without its level-synchronous launches.
+//   * FP64 is the scarce unit on this GPU.  A full evaluation is 18 DFMA for
+//     the two time ends (w, e1, e2 per axis), 24 DFMA for the corner hull and
+//     3 DADD for the width test.  The hull needs only 2 of the 4 (u, v)
+//     corners per time end and axis: rounding is monotone, so the minimum of
+//     the computed corners is the corner picked by the signs of the computed
+//     edge vectors, bit for bit the same as the minimum over all corners.
+//     Almost every interval is decided without it, by the single-precision
+//     filter, its certified ends and single FP64 corners (see inclusion32 and
+//     the evaluation below).  Comparisons, min/max, interval ends and the
+//     split rule run on the integer pipes.
 //   * Earliest-TOI mode: one shared t* (ordered FP64 bits, atomicMin) prunes
 //     every query; per-pair mode keeps t* per query.  Either way the result
 //     for a query that hits no cap is independent of the traversal order: a
@@ -1403,7 +1407,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     }
 
     // ---- 6. in the tail phase, hand the shallowest pending sibling to the
-    //         ring every `budget` evaluations; one reservation per warp -------
+    //         ring every 32 x `budget` evaluations of the warp, in one
+    //         reservation ---------------------------------------------------
     {
       if (tail_phase) wsince += __popc(__ballot_sync(FULL, evaluate));
       const bool trig = wsince >= 32ll * A.budget;   // (tail phase only)
