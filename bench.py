@@ -177,15 +177,16 @@ FLOPS_PER_UNIT = 27 + 3 + 3 + 6 + 6
 def stage_algorithmic(st, nV, nE, nF):
     nB = nV + nE + nF
     pairs = st["n_vf"] + st["n_ee"]
-    nc = st.get("n_box_copies", nB)          # boxes placed in strips (strip sweep)
+    nc = st.get("n_box_copies", nB)          # box copies, one per overlapped cell
     return {
         # V0, V1 (48 B per vertex), topology (8 B per edge, 12 B per face);
         # out: float box (24 B), ordered FP64 extents (48 B), ids (16 B)
         "boxes": ("hbm", 48 * nV + 8 * nE + 12 * nF + 88 * nB),
-        # strip counts (8 B per box in), keys and values of the copies (12 B
-        # out), 6 passes of key + value in and out (24 B per copy), gather
+        # cell counts (8 B per box in), keys and values of the copies (12 B
+        # out), 7 passes (8-bit digits of the 56-bit key)
+        # of key + value in and out (24 B per copy), gather
         # to sorted order (12 B key/value + 36 B box data in, 36 B out)
-        "sort": ("hbm", 8 * nB + 12 * nc + 6 * 24 * nc + 84 * nc),
+        "sort": ("hbm", 8 * nB + 12 * nc + 7 * 24 * nc + 84 * nc),
         # sorted copies once (44 B with the key), 8 B per candidate written,
         # then the exact filter: 8 B read + 96 B of FP64 extents per
         # candidate, 8 B per pair written

@@ -396,7 +396,7 @@ class CCD:
         return out.cpu().numpy()
 
     def autotune(self, V0, V1, E, F, reps=3, stream=None):
-        """Pick the sweep, strip width, hand-off budget and queue capacity for
+        """Pick the sweep, cell width, hand-off budget and queue capacity for
         this mesh (kept in the context)."""
         return ccd_autotune(self.ctx, V0, V1, E, F, reps, stream)
 
