@@ -84,6 +84,27 @@ def test_broad_empty_and_vertices_only(ctx, ccd):
     assert vf.shape[0] == 0 and ee.shape[0] == 0
 
 
+@pytest.mark.parametrize("offset", [2.0 ** 20, -(2.0 ** 24)])
+def test_broad_far_from_origin_matches_oracle(ctx, ccd, offset):
+    """A scene moved far from the origin: the outward-rounded float boxes grow
+    to the float spacing there (1/8 at 2^20, 2 at 2^24, where every box
+    overlaps every other and the cell grid collapses to one cell), so the
+    single-precision superset grows (1.5x and 3.6x the exact set here) and
+    the exact FP64 filter alone brings it back to the oracle's set."""
+    s = random_scene(7, nv=200, nf=160)
+    s = scenes.Scene(s.V0 + offset, s.V1 + offset, s.E, s.F, {"name": "far"})
+    V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
+    vf, ee = ctx.broad(V0, V1, E, F)
+    ovf, oee = O.broad(s.V0, s.V1, s.E, s.F)
+    np.testing.assert_array_equal(sorted_pairs(vf), ovf)
+    np.testing.assert_array_equal(sorted_pairs(ee), oee)
+    rc, st = ctx.status()
+    assert rc == 0
+    v32, e32 = O.broad(s.V0, s.V1, s.E, s.F, fp32=True)
+    assert st["n_superset"] == len(v32) + len(e32)
+    assert len(v32) + len(e32) > len(ovf) + len(oee)
+
+
 def test_broad_truncation_reports_totals(ctx, ccd):
     s = scenes.icosphere_on_plane(0)
     V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
@@ -136,6 +157,25 @@ def _stress(n, seed):
 def test_narrow_stress_mix_matches_oracle(ctx, ccd, n, seed):
     sc, vf, ee = _stress(n, seed)
     r, o = _narrow_both(ctx, ccd, sc, vf, ee)
+    _assert_per_pair(r, o)
+
+
+@pytest.mark.parametrize("scale,offset", [(1.0, 2.0 ** 16), (1.0, 2.0 ** 30), (2.0 ** -13, 0.0),
+                                          (2.0 ** -100, 0.0), (2.0 ** 20, -3.0), (2.0 ** -40, 1.0)])
+def test_narrow_stress_scaled_matches_oracle(ctx, ccd, scale, offset):
+    """The stress mix shrunk, grown and moved away from the origin, with delta
+    scaled alike.  The single-precision filter's thresholds follow the
+    coordinates (bounds relative to the per-axis sums of |c0| + |dc|, floors
+    near the bottom of the float range at 2^-100); far from the origin the
+    error box outgrows delta (2^30) or the 2^-60 grid rounds away (2^-40 at
+    1.0), leaving degenerate, noisy queries.  Every decision the filter takes
+    must still be the FP64 one.  A few of these queries take over 10^6
+    intervals, so the cap is 10^7, which no query reaches on either side (a
+    query split across lanes reaches a cap elsewhere than the oracle does)."""
+    X0, X1, is_vf, kind = scenes.narrow_stress_queries(1500, 11)
+    sc, vf, ee, order = scenes.pack_queries(X0 * scale + offset, X1 * scale + offset, is_vf)
+    r, o = _narrow_both(ctx, ccd, sc, vf, ee, delta=1e-6 * scale, max_iter=10 ** 7)
+    assert not np.concatenate([o[2], o[3]]).any()
     _assert_per_pair(r, o)
 
 
