@@ -319,6 +319,17 @@ enum { CCD_STAGE_BOXES = 0, CCD_STAGE_SORT = 1, CCD_STAGE_SWEEP = 2, CCD_STAGE_N
  * Synchronizes the stream.  Returns CCD_EINVAL unless profile_stages was set. */
 int ccd_stage_times(ccd_ctx *ctx, double ms[CCD_NSTAGES]);
 
+/* Self-test of the narrow phase's failure detection, with no GPU fault:
+ * runs the narrow-phase kernel on no queries with one unit counted as
+ * pending that no lane will ever take.  Every warp idles until its idle
+ * limit (about half a second) and leaves; the last one to leave finds the
+ * count above zero and raises CCD_ETIMEOUT, as it would for work lost in a
+ * real call.  *status (host memory) receives the device status the kernel
+ * left: CCD_ETIMEOUT when detection works.  Synchronous on `stream`; the
+ * context stays usable (the next call resets its status).  Returns CCD_OK,
+ * or CCD_EINVAL / CCD_ENOMEM / CCD_ECUDA if it could not run. */
+int ccd_selftest_unfinished_work(ccd_ctx *ctx, int32_t *status, void *stream);
+
 /* Human-readable text of a CCD_* status (static storage). */
 const char *ccd_status_str(int status);
 

@@ -124,6 +124,8 @@ def lib():
     L.ccd_autotune_batch.restype = ctypes.c_int
     L.ccd_status_async.argtypes = [P, P, P]
     L.ccd_status_async.restype = ctypes.c_int
+    L.ccd_selftest_unfinished_work.argtypes = [P, ctypes.POINTER(ctypes.c_int32), P]
+    L.ccd_selftest_unfinished_work.restype = ctypes.c_int
     L.ccd_get_memory_model.argtypes = [ctypes.POINTER(ccd_opts), ctypes.POINTER(ccd_memory_model)]
     L.ccd_get_memory_model.restype = ctypes.c_int
     L.ccd_pair_capacity_for.argtypes = [ctypes.POINTER(ccd_opts), i64, i64, i32]
@@ -274,6 +276,14 @@ def ccd_get_status(ctx) -> Tuple[int, dict]:
     st = ccd_stats()
     rc = lib().ccd_get_status(ctx, ctypes.byref(st))
     return rc, st.as_dict()
+
+
+def ccd_selftest_unfinished_work(ctx, stream=None) -> int:
+    """Device status the narrow kernel leaves when one unit can never
+    finish (CCD_ETIMEOUT when detection works); synchronous."""
+    st = ctypes.c_int32()
+    _check(lib().ccd_selftest_unfinished_work(ctx, ctypes.byref(st), _stream(stream)), "ccd_selftest_unfinished_work")
+    return st.value
 
 
 STAGES = ("boxes", "sort", "sweep", "narrow")

@@ -114,8 +114,10 @@ __global__ void k_reset_narrow(DevCtl *c, int keep_toi) {
   c->n_donated = 0;
   c->n_intervals_tail = 0;
   c->n_intervals_fp64 = 0;
+  c->n_left = 0;
 }
 __global__ void k_reset_status(DevCtl *c) { c->status = CCD_OK; }
+__global__ void k_add_pending(DevCtl *c, unsigned long long n) { c->pending += n; }
 
 // Pair counts of the broad phase clamped to the buffer capacities (ccd_step:
 // the narrow phase reads them on the device, no host round trip).
@@ -510,7 +512,8 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
                   const int32_t *F, double delta, double min_sep, int64_t max_iter, int mode,
                   unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s,
                   bool zero_rule_pass = false, int n_scenes = 0, const int64_t *voff = nullptr,
-                  unsigned long long *toi_scene = nullptr, int64_t ee_end = 0, bool keep_toi = false) {
+                  unsigned long long *toi_scene = nullptr, int64_t ee_end = 0, bool keep_toi = false,
+                  unsigned long long phantom_units = 0) {
   const int64_t nq = counts_from_ctl && ee_end > 0 ? ee_end : n_vf + n_ee;
   int rc = ensure_narrow(c, nq, s);
   if (rc) return rc;
@@ -518,6 +521,7 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
     k_nozero_prepare<<<1, 1, 0, s>>>(c->ctl);
   else
     k_reset_narrow<<<1, 1, 0, s>>>(c->ctl, keep_toi ? 1 : 0);
+  if (phantom_units) k_add_pending<<<1, 1, 0, s>>>(c->ctl, phantom_units);   // self-test only
   NarrowArgs A;
   A.ctl = c->ctl;
   A.vf = vf;
@@ -1171,6 +1175,24 @@ int ccd_status_async(ccd_ctx *c, int32_t *status, void *stream) {
   if (!c || !status) return CCD_EINVAL;
   CK(cudaSetDevice(c->device));
   CK(cudaMemcpyAsync(status, &c->ctl->status, sizeof(int32_t), cudaMemcpyDefault, (cudaStream_t)stream));
+  return CCD_OK;
+}
+
+int ccd_selftest_unfinished_work(ccd_ctx *c, int32_t *status, void *stream) {
+  if (!c || !status) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+  // no queries, and one unit counted as pending that no lane will ever take
+  const int rc = launch_narrow(c, nullptr, 0, nullptr, 0, 0, nullptr, nullptr, 0, nullptr, nullptr, c->opts.delta,
+                               c->opts.min_sep, c->opts.max_iter, 1, nullptr, nullptr, s, false, 0, nullptr, nullptr,
+                               0, false, 1);
+  if (rc) return rc;
+  int32_t h = CCD_OK;
+  CK(cudaMemcpyAsync(&h, &c->ctl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *status = h;
   return CCD_OK;
 }
 

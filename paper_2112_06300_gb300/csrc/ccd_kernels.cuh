@@ -32,7 +32,7 @@ struct DevCtl {
   unsigned long long n_intervals_tail;  // intervals evaluated after the query list ran out
   unsigned long long n_intervals_fp64;  // intervals the FP32 filter could not decide
   int rerun;                     // zero-TOI rule: 1 when the second pass must run
-  int pad_;
+  unsigned n_left;               // warps of the narrow launch that have left it
   // strip sweep
   unsigned long long n_copies;   // boxes placed in strips (with repeats)
   int strip_fallback;            // 1: the copies did not fit; one cell per scene

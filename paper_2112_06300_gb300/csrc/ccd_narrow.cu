@@ -1478,6 +1478,16 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     }
   }
 
+  // A warp also leaves after kIdleRounds idle rounds, so a unit that can
+  // never finish (a pending count that does not return to zero) ends the
+  // launch instead of holding the GPU; the last warp to leave then records
+  // CCD_ETIMEOUT.  (A warp leaves a finished launch only after the count it
+  // read was zero, and the count cannot rise again once every query is out.)
+  if (lane == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->n_left, 1u) == gridDim.x * (blockDim.x >> 5) - 1 && ld_relaxed_u64(&ctl->pending) != 0)
+      atomicCAS(&ctl->status, CCD_OK, CCD_ETIMEOUT);
+  }
   if (n_eval) atomicAdd(&ctl->n_intervals, (unsigned long long)n_eval);
   if (n_exp) atomicAdd(&ctl->n_exported, (unsigned long long)n_exp);
   if (n_cap) atomicAdd(&ctl->n_capped, (unsigned long long)n_cap);
@@ -1527,6 +1537,7 @@ __global__ void k_nozero_prepare(DevCtl *ctl) {
     ctl->pending = 0;
     ctl->toi_bits = kInfBits;
     ctl->t_start = ctl->t_exhausted = ctl->t_end = 0;
+    ctl->n_left = 0;
   }
 }
 

@@ -67,6 +67,7 @@ __global__ void k_noalloc_reset(DevCtl *ctl) {
   ctl->n_donated = 0;
   ctl->n_intervals_tail = 0;
   ctl->n_intervals_fp64 = 0;
+  ctl->n_left = 0;
 }
 
 __global__ void k_noalloc_status(const DevCtl *ctl, int32_t *status) { *status = ctl->status; }
