@@ -31,6 +31,8 @@
 //     pruned interval starts at or after a t* that is already >= the final t*.
 //
 // Every wait is bounded; on expiry the kernel records CCD_ETIMEOUT and returns.
+// Warps that find nothing to do for long enough leave, and the last one to
+// leave records CCD_ETIMEOUT if any unit is still counted as unfinished.
 
 #include "ccd_common.cuh"
 #include "ccd_kernels.cuh"
@@ -1484,9 +1486,11 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   // CCD_ETIMEOUT.  (A warp leaves a finished launch only after the count it
   // read was zero, and the count cannot rise again once every query is out.)
   if (lane == 0) {
-    __threadfence();
-    if (atomicAdd(&ctl->n_left, 1u) == gridDim.x * (blockDim.x >> 5) - 1 && ld_relaxed_u64(&ctl->pending) != 0)
-      atomicCAS(&ctl->status, CCD_OK, CCD_ETIMEOUT);
+    __threadfence();   // this warp's updates of the count before its departure
+    if (atomicAdd(&ctl->n_left, 1u) == gridDim.x * (blockDim.x >> 5) - 1) {
+      __threadfence();   // every other warp's updates before the count is read
+      if (ld_relaxed_u64(&ctl->pending) != 0) atomicCAS(&ctl->status, CCD_OK, CCD_ETIMEOUT);
+    }
   }
   if (n_eval) atomicAdd(&ctl->n_intervals, (unsigned long long)n_eval);
   if (n_exp) atomicAdd(&ctl->n_exported, (unsigned long long)n_exp);
