@@ -183,9 +183,9 @@ def stage_algorithmic(st, nV, nE, nF):
         # out: float box (24 B), ordered FP64 extents (48 B), ids (16 B)
         "boxes": ("hbm", 48 * nV + 8 * nE + 12 * nF + 88 * nB),
         # cell counts (8 B per box in), keys and values of the copies (12 B
-        # out), 7 passes (8-bit digits of the 56-bit key)
-        # of key + value in and out (24 B per copy), gather
-        # to sorted order (12 B key/value + 36 B box data in, 36 B out)
+        # out), 7 passes (8-bit digits of the 56-bit key) of key + value in
+        # and out (24 B per copy), gather to sorted order (12 B key/value +
+        # 36 B box data in, 36 B out)
         "sort": ("hbm", 8 * nB + 12 * nc + 7 * 24 * nc + 84 * nc),
         # sorted copies once (44 B with the key), 8 B per candidate written,
         # then the exact filter: 8 B read + 96 B of FP64 extents per
