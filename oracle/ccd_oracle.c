@@ -582,6 +582,17 @@ void oracle_inclusion(int vf, const int64_t ids[4], const double *V0, const doub
     for (int x = 0; x < 3; ++x) ebox[x] = q.ebox[x];
 }
 
+/* The split weights L_t, L_u, L_v of one query (the reading of "split" that
+ * the paper leaves open), so that the tests can check them against values
+ * worked out by hand. */
+void oracle_split_weights(int vf, const int64_t ids[4], const double *V0, const double *V1,
+                          double L[3])
+{
+    query q;
+    setup_query(&q, vf, V0, V1, ids, 0.0);
+    for (int k = 0; k < 3; ++k) L[k] = q.L[k];
+}
+
 int oracle_has_openmp(void)
 {
 #ifdef _OPENMP

@@ -60,6 +60,8 @@ def _configure(L):
     L.oracle_narrow.restype = None
     L.oracle_inclusion.argtypes = [ctypes.c_int, P, P, P, ctypes.c_double, P, P, P, P, P]
     L.oracle_inclusion.restype = None
+    L.oracle_split_weights.argtypes = [ctypes.c_int, P, P, P, P]
+    L.oracle_split_weights.restype = None
     L.oracle_has_openmp.argtypes = []
     L.oracle_has_openmp.restype = ctypes.c_int
     return L
@@ -217,6 +219,17 @@ def inclusion(vf, x0, x1, n, l, min_sep=0.0):
     lib().oracle_inclusion(int(vf), _p(ids), _p(V0), _p(V1), float(min_sep), _p(nn),
                            _p(ll), _p(bmin), _p(bmax), _p(ebox))
     return bmin, bmax, ebox
+
+
+def split_weights(vf, x0, x1):
+    """Split weights (L_t, L_u, L_v) of one query given by its 4 points at
+    t = 0 and t = 1 (vertex-face: P, T0, T1, T2; edge-edge: A0, A1, B0, B1)."""
+    V0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(4, 3)
+    V1 = np.ascontiguousarray(x1, dtype=np.float64).reshape(4, 3)
+    ids = np.arange(4, dtype=np.int64)
+    L = np.empty(3)
+    lib().oracle_split_weights(int(vf), _p(ids), _p(V0), _p(V1), _p(L))
+    return L
 
 
 def openmp_threads() -> int:

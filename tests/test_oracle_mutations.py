@@ -1,8 +1,9 @@
 """The oracle's pins must catch plausible mistakes.  Each test plants one
 mistake in a copy of the oracle source (a dropped term, a flipped sign, a
 transposed operand, a wrong index, a missing error box, a wrong comparison,
-a missing rounding step, a missing filter), builds it on the CPU, and checks
-that a pin fails on it while the same pin passes on the real oracle.
+a missing rounding step, a missing filter, a wrong split rule or split
+weight), builds it on the CPU, and checks that a pin fails on it while the
+same pin passes on the real oracle.
 
 Also here: the error-box pin itself (the C_eps derivation), checked against
 exact rational corner values."""
@@ -17,6 +18,7 @@ import pytest
 from oracle import exact as X
 from oracle import oracle as O
 from paper_2112_06300_gb300 import scenes
+from tests.test_oracle_split import pin_split_order, pin_split_weights
 
 SRC = os.path.join(os.path.dirname(O.__file__), "ccd_oracle.c")
 
@@ -127,6 +129,23 @@ MUTATIONS = [
      "if ((double)f > x) f = nextafterf(f, -INFINITY);", "(void)0;", pin_tight_rounding),
     ("shared-vertex filter missing",
      "if (shares_vertex(a, na, b, nb)) return 0;", "(void)shares_vertex;", pin_definition_pairs),
+    ("split the axis of the smallest weight",
+     "if (val > bestval) { best = k; bestval = val; }",
+     "if (best < 0 || val < bestval) { best = k; bestval = val; }", pin_split_order),
+    ("split weight without the 2^-l factor",
+     "double val = ldexp(q->L[k], -I->l[k]);", "double val = q->L[k];", pin_split_order),
+    ("ties go to the later axis",
+     "if (val > bestval) { best = k; bestval = val; }",
+     "if (val >= bestval) { best = k; bestval = val; }", pin_split_order),
+    ("L_u built from e2",
+     "double su = fmax(fabs(q->c0[1][x]), fabs(c1u));",
+     "double su = fmax(fabs(q->c0[2][x]), fabs(c1v));", pin_split_weights),
+    ("L_u at t = 0 only",
+     "double su = fmax(fabs(q->c0[1][x]), fabs(c1u));",
+     "double su = fabs(q->c0[1][x]); (void)c1u;", pin_split_weights),
+    ("L_t from the positions instead of the displacements",
+     "double st = fabs(q->dc[0][x]) + fabs(q->dc[1][x]);",
+     "double st = fabs(q->c0[0][x]) + fabs(q->c0[1][x]);", pin_split_weights),
 ]
 
 
