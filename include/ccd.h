@@ -198,16 +198,20 @@ int ccd_step(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV,
  * Narrow phase without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc where they
  * need the query (under an allocator they do not own, in hosts that forbid
- * allocation, in loops that must not allocate).  Same computation and
- * arguments as ccd_narrow, but no context: the scratch is one fixed array in
- * the library's device memory (about 1.4 MB per GPU, kept until the process
- * exits).  Limit: n_vf + n_ee <= 65536; larger calls return CCD_EINVAL.
+ * allocation, in loops that must not allocate).  Same computation, results
+ * and arguments as ccd_narrow, but no context: the scratch is one fixed array
+ * in the library's device memory (about 1.4 MB per GPU, kept until the
+ * process exits).  Limit: n_vf + n_ee <= 65536; larger calls return
+ * CCD_EINVAL.  Its interval ring is smaller than ccd_narrow's (2^14 cells);
+ * that changes only how much tail work can move between warps, not results.
  * status: device int32 [1], receives the kernels' CCD_* status.
- * The first call on a device sets the array up (looks up its device address,
- * initialises the interval ring) on `stream` from the current device; make
- * that first call before any stream capture.  Every call shares the array and
- * it keeps the last call's contents (each call clears what must start at
- * zero); calls that overlap on the GPU race.  Asynchronous.
+ * The first call on a device sets it up from the current device (occupancy
+ * query for the grid size); make that first call before any stream capture.
+ * Every call looks up the array's device address (a host-side lookup) and
+ * first resets all of the array that the kernels read (counters, status,
+ * t*, interval ring), so no state of an earlier call -- finished, failed or
+ * cut off -- reaches it.  Calls share the array: calls that overlap on the
+ * GPU race.  Asynchronous.
  */
 int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee,
                        const double *V0, const double *V1, int64_t nV,
@@ -384,6 +388,10 @@ typedef struct {
     int64_t n_batches;       /* batches launched */
     int64_t max_batch_scenes;  /* largest batch */
     double sum_latency_ms;   /* sum of completed scenes' latencies */
+    int64_t max_batch_bytes; /* largest device-memory need of one batch (memory
+                                model) that was admitted */
+    int64_t max_inflight_bytes;  /* largest sum of those needs over the batches
+                                    in flight at one time (at most memory_cap) */
 } ccd_server_stats;
 
 void ccd_server_default_opts(ccd_server_opts *o);

@@ -65,7 +65,8 @@ class ccd_server_opts(ctypes.Structure):
 
 class ccd_server_stats(ctypes.Structure):
     _fields_ = [("n_submitted", ctypes.c_int64), ("n_done", ctypes.c_int64), ("n_batches", ctypes.c_int64),
-                ("max_batch_scenes", ctypes.c_int64), ("sum_latency_ms", ctypes.c_double)]
+                ("max_batch_scenes", ctypes.c_int64), ("sum_latency_ms", ctypes.c_double),
+                ("max_batch_bytes", ctypes.c_int64), ("max_inflight_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -11,10 +11,19 @@
 // exits.
 //
 // The array is shared by every call on a device and keeps the last call's
-// contents; each call clears what must start at zero (counters, status, the
-// shared t*).  Calls that overlap on the GPU (two streams, or two host
-// threads) race on it.
+// contents.  Each call first puts all of it that the kernel reads back into
+// the state of a first call: counters, status and the shared t* cleared, the
+// ring's positions zeroed and every ring cell's sequence number rewritten.  So
+// nothing an earlier call left behind -- finished, failed with CCD_ETIMEOUT,
+// or cut off with intervals still in the ring -- reaches the next call.
+// Calls that overlap on the GPU (two streams, or two host threads) race on it.
+//
+// Deliberate differences from ccd_narrow: the interval ring holds 2^14 cells
+// (ccd_narrow: 2^21 by default), so fewer subtrees can wait in it during the
+// tail (a hand-off that does not fit stays with its lane; results are the
+// same); the hand-off budget is ccd_narrow's default (16).
 
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -34,64 +43,58 @@ constexpr size_t kRingBytes = kRingCells * sizeof(RingCell);
 constexpr size_t kScratchBytes = kCtlBytes + kFlagsBytes + kItersBytes + kRingBytes;   // ~1.4 MB
 
 static_assert(sizeof(DevCtl) % 8 == 0, "the control block is cleared as 8-byte words");
+static_assert(offsetof(DevCtl, toi_bits) % 8 == 0, "t* is one 8-byte word of the control block");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 struct DeviceState {
   bool ready = false;
-  unsigned char *base = nullptr;   // device address of g_scratch on this device
-  int blocks = 0;
+  int blocks = 0;                  // persistent grid of the narrow kernel
 };
 
 constexpr int kMaxDevices = 64;
 DeviceState g_state[kMaxDevices];
 std::mutex g_mutex;
 
-__global__ void k_noalloc_init(unsigned char *base) {
+// Every call: the control block back to zero (t* to +inf), the ring's
+// positions to 0 and each cell's sequence number to its index, as for the
+// first call on the device.
+__global__ void k_noalloc_reset(unsigned char *base) {
   DevCtl *ctl = (DevCtl *)base;
   RingCell *ring = (RingCell *)(base + kCtlBytes + kFlagsBytes + kItersBytes);
   const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  // DevCtl is a whole number of 8-byte words; one thread writes each
+  constexpr unsigned long long kToiWord = offsetof(DevCtl, toi_bits) / sizeof(unsigned long long);
   if (tid < sizeof(DevCtl) / sizeof(unsigned long long))
-    ((unsigned long long *)ctl)[tid] = 0;   // DevCtl is a whole number of 8-byte words
+    ((unsigned long long *)ctl)[tid] = tid == kToiWord ? 0x7FF0000000000000ull : 0ull;
   for (unsigned long long i = tid; i < kRingCells; i += (unsigned long long)gridDim.x * blockDim.x)
-    ring[i].seq = i;   // ring positions start at 0
-}
-
-__global__ void k_noalloc_reset(DevCtl *ctl) {
-  ctl->status = CCD_OK;
-  ctl->q_next = 0;
-  ctl->pending = 0;
-  ctl->toi_bits = 0x7FF0000000000000ull;
-  ctl->n_intervals = ctl->n_exported = ctl->n_capped = ctl->queue_peak = 0;
-  ctl->t_start = ctl->t_exhausted = ctl->t_end = 0;
-  ctl->n_donated = 0;
-  ctl->n_intervals_tail = 0;
-  ctl->n_intervals_fp64 = 0;
-  ctl->n_left = 0;
+    ring[i].seq = i;
 }
 
 __global__ void k_noalloc_status(const DevCtl *ctl, int32_t *status) { *status = ctl->status; }
 
-// One-time set-up on the current device: device address of the array,
-// ring initialisation, persistent grid size.
-int setup_device(int dev, cudaStream_t s, DeviceState **out) {
+// Set-up on the current device: the persistent grid size, once per device,
+// and the array's device address.  In host code g_scratch names a host-side
+// stand-in, not device memory, so the kernels get the address that
+// cudaGetSymbolAddress returns for the current device.  The address is looked
+// up again on every call (a host-side table lookup, no device work), so a
+// cudaDeviceReset between calls, which reloads the module, is handled.
+int setup_device(int dev, DeviceState **out, unsigned char **base) {
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return CCD_ECUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
   DeviceState &st = g_state[dev];
   if (!st.ready) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return CCD_ECUDA;
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CCD_ECUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow_setup, kNarrowThreads, 0) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
-    k_noalloc_init<<<64, 256, 0, s>>>((unsigned char *)p);
-    if (cudaGetLastError() != cudaSuccess) return CCD_ECUDA;
-    st.base = (unsigned char *)p;
     st.blocks = per_sm * sms;
     st.ready = true;
   }
   *out = &st;
+  *base = (unsigned char *)p;
   return CCD_OK;
 }
 
@@ -112,11 +115,11 @@ extern "C" int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CCD_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
   DeviceState *st = nullptr;
-  int rc = setup_device(dev, s, &st);
+  unsigned char *base = nullptr;
+  int rc = setup_device(dev, &st, &base);
   if (rc) return rc;
-  unsigned char *base = st->base;
   DevCtl *ctl = (DevCtl *)base;
-  k_noalloc_reset<<<1, 1, 0, s>>>(ctl);
+  k_noalloc_reset<<<64, 256, 0, s>>>(base);
   NarrowArgs A;
   std::memset(&A, 0, sizeof(A));
   A.ctl = ctl;
@@ -134,7 +137,7 @@ extern "C" int ccd_narrow_noalloc(const int32_t *vf, int64_t n_vf, const int32_t
   A.min_sep = min_sep;
   A.max_iter = max_iter;
   A.mode = mode;
-  A.budget = 64;
+  A.budget = 16;   // ccd_narrow's default hand-off budget
   A.no_zero = 0;
   A.only_if_rerun = 0;
   A.qrec = nullptr;   // no record buffer: lanes set their queries up themselves

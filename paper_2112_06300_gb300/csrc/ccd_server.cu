@@ -111,6 +111,7 @@ struct Slot;
 struct Batch {
   std::vector<Request *> reqs;
   int64_t arena_end = 0;       // arena position after the batch's last block
+  int64_t bytes = 0;           // device-memory need by the memory model
   std::atomic<bool> done{false};   // set by the stream callback (or a failed launch)
   bool delivered = false;      // results handed to the scenes, slot released
   Slot *slot = nullptr;
@@ -182,6 +183,7 @@ struct ccd_server {
   std::deque<Request *> queue;                   // in arrival (= arena) order
   std::unordered_map<uint64_t, Request *> reqs;
   std::deque<Batch *> inflight;                  // in arena order
+  int64_t inflight_bytes = 0;                    // memory-model need of the batches on slots
   std::vector<Slot> slots;
   std::thread sched;
   bool stop = false;
@@ -222,6 +224,7 @@ void finish_batches(ccd_server *S) {
     sl->busy = false;
     sl->batch = nullptr;
     b->delivered = true;
+    S->inflight_bytes -= b->bytes;
     any = true;
   }
   while (!S->inflight.empty() && S->inflight.front()->delivered) {
@@ -339,6 +342,12 @@ void scheduler(ccd_server *S) {
       S->queue.pop_front();
     }
     b->arena_end = b->reqs.back()->blk.off + b->reqs.back()->blk.bytes;
+    // admission by memory: each slot holds at most its share of the cap, so
+    // the batches in flight together stay within memory_cap
+    b->bytes = est_bytes(S, boxes, (int64_t)b->reqs.size());
+    S->inflight_bytes += b->bytes;
+    S->st.max_batch_bytes = std::max<int64_t>(S->st.max_batch_bytes, b->bytes);
+    S->st.max_inflight_bytes = std::max<int64_t>(S->st.max_inflight_bytes, S->inflight_bytes);
     b->slot = free_slot;
     free_slot->busy = true;
     free_slot->batch = b;
@@ -360,6 +369,7 @@ void scheduler(ccd_server *S) {
       }
       b->delivered = true;
       b->done.store(true);
+      S->inflight_bytes -= b->bytes;
       free_slot->busy = false;
       free_slot->batch = nullptr;
       S->error = rc;

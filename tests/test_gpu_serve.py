@@ -104,3 +104,56 @@ def test_memory_model_matches_allocation(ccd):
     assert 0.9 * model <= used <= 1.15 * model + (64 << 20), (used, model)
     # the capacity the model grants for that budget is the one used above
     assert abs(ccd.ccd_pair_capacity_for(model, nB) - pairs) <= 1
+
+
+def test_memory_cap_binds(ccd):
+    """A memory cap that fits two scenes per slot: scenes submitted at once
+    are held until a slot and its memory share free up, every batch stays
+    within the share, the batches in flight together stay within the cap,
+    the device memory the server's contexts hold stays near it, and every
+    result equals the oracle's bit for bit."""
+    batch = [scenes.folded_cloth(64, seed=10 + k) for k in range(7)]
+    ref = np.array([O.step(s.V0, s.V1, s.E, s.F) for s in batch])
+    m = ccd.ccd_get_memory_model()
+    ppb = 64.0
+    nb = batch[0].n_boxes
+
+    def need(k):   # the server's memory-model estimate of a batch of k scenes
+        boxes = k * nb
+        return (m["bytes_fixed"] + max(boxes, 1024) * m["bytes_per_box"] + k * m["bytes_per_scene"]
+                + max(1 << 20, int(ppb * boxes)) * m["bytes_per_pair"])
+
+    assert need(2) < need(3)
+    n_slots = 2
+    share = (need(2) + need(3)) // 2
+    cap = n_slots * share
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    srv = ccd.Server(0, n_slots=n_slots, max_scenes=256, arena_bytes=64 << 20, memory_cap=cap,
+                     pairs_per_box=ppb)
+    try:
+        # write every scene first and queue them last-first: the scheduler
+        # takes scenes in request order, so nothing starts before the first
+        # one is queued and all seven are waiting at once
+        tickets = []
+        for s in batch:
+            t, a, b, e, f = srv.request(len(s.V0), len(s.E), len(s.F))
+            a[...] = s.V0.T
+            b[...] = s.V1.T
+            e[...] = s.E
+            f[...] = s.F
+            tickets.append(t)
+        for t in reversed(tickets):
+            srv.submit(t)
+        got = [srv.wait(t) for t in tickets]
+        torch.cuda.synchronize()
+        used = free0 - torch.cuda.mem_get_info()[0]
+        st = srv.stats()
+    finally:
+        srv.close()
+    toi = np.array([g[0] for g in got])
+    np.testing.assert_array_equal(toi.view(np.uint64), ref.view(np.uint64))
+    assert st["max_batch_scenes"] == 2, st
+    assert st["n_batches"] >= 4, st
+    assert st["max_batch_bytes"] <= share and st["max_inflight_bytes"] <= cap, st
+    assert used <= 1.15 * cap + (64 << 20), (used, cap)

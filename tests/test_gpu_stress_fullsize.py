@@ -3,19 +3,20 @@
 collide at a seeded dyadic time / coplanar-or-parallel / touching at t = 0 or
 1 / near miss at 2^-30..2^-40), per-pair times on the GPU.
 
-Checked on seeded samples: bit-identical to the FP64 oracle on 50,000 queries
-neither side flagged; against the exact rational oracle on 4,000 queries,
-no false negative and never later than the exact time.  The false-positive
-rate on that sample (a collision reported where the exact time says none) is
-printed."""
-import multiprocessing as mp
+Checked: bit-identical to the FP64 oracle on a seeded sample of 50,000
+queries neither side flagged; against the exact rational oracle on the
+100,000-query subset stored in tests/golden/stress_exact_1e5.txt.gz (exact
+times computed by make_stress_exact.py with oracle/exact.py only): no false
+negative and never later than the exact time.  The false-positive count (a
+collision reported where the exact oracle finds none) and the distribution
+of t_exact - t_gpu are printed."""
 
 import numpy as np
 import pytest
 
-from oracle import exact as X
 from oracle import oracle as O
 from paper_2112_06300_gb300 import scenes
+from tests.golden import make_stress_exact as G
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -23,25 +24,11 @@ torch = pytest.importorskip("torch")
 N = 1 << 24
 
 
-def _exact_one(args):
-    vf, x0, x1 = args
-    r = X.toi(vf, x0, x1)
-    return r
-
-
-@pytest.fixture(scope="module")
-def exact_pool():
-    # processes for the exact oracle, started before any GPU work
-    with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
-        yield pool
-
-
-def test_stress_full_size_sampled(exact_pool):
+def test_stress_full_size_sampled():
     rng = np.random.default_rng(0)
     X0, X1, is_vf, kind = scenes.narrow_stress_queries(N, 2)
-    exact_idx = rng.choice(N, size=4000, replace=False)
-    jobs = [(bool(is_vf[q]), X0[q].tolist(), X1[q].tolist()) for q in exact_idx]
-    ex_async = exact_pool.map_async(_exact_one, jobs, chunksize=50)
+    head, exact_idx, exact_rd = G.read()
+    assert head["sha256"] == G.fingerprint(X0, X1, is_vf, exact_idx), "stress generator changed"
 
     from paper_2112_06300_gb300 import build
     build.build()
@@ -83,14 +70,10 @@ def test_stress_full_size_sampled(exact_pool):
     assert both.mean() > 0.99
     np.testing.assert_array_equal(toi[s][both].view(np.uint64), otoi[both].view(np.uint64))
 
-    # exact oracle on a sample: conservative, no false negative
-    ex = ex_async.get()
-    fp = 0
-    for q, e in zip(exact_idx, ex):
-        if e is None:
-            fp += int(np.isfinite(toi[q]))
-        else:
-            assert np.isfinite(toi[q]), f"false negative on query {q}"
-            assert X.le_float(float(toi[q]), e), f"late time of impact on query {q}"
-    print(f"exact-oracle sample: {len(exact_idx)} queries, {fp} false positives "
-          f"({fp / len(exact_idx):.2%})")
+    # exact oracle on the stored 1e5 subset: conservative, no false negative
+    r = G.summarize(toi[exact_idx], flags[exact_idx], exact_rd)
+    print(f"exact-oracle subset: {r['n']} queries, {r['n_collide']} collide; false negatives {r['fn']}, "
+          f"late {r['late']}, false positives {r['fp']} ({r['fp_rate']:.3%} of non-colliding); "
+          f"t_exact - t_gpu: median {r['err_median']:.3g}, mean {r['err_mean']:.3g}, max {r['err_max']:.3g}")
+    assert r["fn"] == 0 and r["late"] == 0
+

@@ -33,7 +33,7 @@ def _worker(rank, world, port, out):
 
 def test_aggregate_two_ranks_gloo():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a process that has threads
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     for r in range(world):
