@@ -12,18 +12,27 @@ whole job: narrow-phase candidate pairs of every rank / max-over-ranks step
 time.  The reference arm times the CPU oracle (C, OpenMP) on the same scene.
 Multi-GPU: independent replicas, one per rank, no collective on the data path.
 
-The other workloads (one GPU) measure the batched, serving and precision
-forms:
-  batch      4,096 rigid environments (500-50,000 triangles, log-uniform),
-             stepped in batches sized by the memory model for a 64 GiB budget;
-             plus one batch stepped repeatedly under a captured CUDA graph.
-  serve      the same environments arriving as a Poisson stream at a given
-             rate (default 2e4 steps/s) into the serving runtime; p50/p99
-             latency and completed scenes per second.
-  precision  the folded cloth plus 1,000 rigid bodies (4.1M triangles):
-             single-precision broad phase with the exact FP64 filter against
-             the all-FP64 broad phase -- candidate counts, final-set
-             equality, time.
+With no --workload, the line also carries a "forms" object with every other
+configuration, each in this library's form and against the plain FP64 form
+(FP64 broad phase throughout, same narrow phase), with queries/s and
+fractions of roofline:
+  cloth_min_sep_1e-4  the same cloth step with min_sep = 1e-4;
+  icosphere_plane     icosphere on a plane (21,635 boxes), also per pair;
+  stress_2^24         2^24 standalone narrow-phase queries, per-pair times,
+                      and the stored exact-oracle subset (100,000 queries):
+                      false negatives, late times, false positives;
+  precision           the folded cloth plus 1,000 rigid bodies (4.1M
+                      triangles): single-precision broad phase with the exact
+                      FP64 filter against the all-FP64 broad phase --
+                      candidate counts, final-set equality, time;
+  batched             4,096 rigid environments (500-50,000 triangles,
+                      log-uniform) stepped in batches sized by the memory
+                      model for a 64 GiB budget, plus one batch stepped
+                      repeatedly under a captured CUDA graph;
+  serving             the same environments arriving as a Poisson stream
+                      (2e4 steps/s) into the serving runtime; p50/p99 latency
+                      from arrival (client write included) to completion.
+--workload batch|serve|precision prints that form alone as its own line.
 """
 from __future__ import annotations
 
@@ -64,6 +73,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=512, help="cloth grid size")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the other configurations and forms")
     p.add_argument("--workload", choices=["cloth", "batch", "serve", "precision"], default="cloth")
     p.add_argument("--envs", type=int, default=4096, help="batch/serve: environments")
     p.add_argument("--rate", type=float, default=2e4, help="serve: arrivals per second")
@@ -351,6 +361,9 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s)
+    if world == 1 and not args.no_forms:
+        c.close()
+        line["forms"] = run_forms(args, flush, fp64, float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS)))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -402,11 +415,142 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-# Batched, serving and precision forms (one GPU).
+# The other configurations and forms (one GPU): each returns a dict that goes
+# into the "forms" object of the default line, or alone with --workload.
 # ---------------------------------------------------------------------------
 
 BUDGET = 64 << 30          # device memory budget of the batched and serving forms
 PAIRS_PER_BOX = 1.0        # candidate pairs per box budgeted (rigid environments: ~0.63)
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _roof(st, stages, nV, nE, nF, fp64_gflops, hbm_gbs):
+    """Fractions of roofline of the broad phase (HBM, its three stages'
+    algorithmic bytes over their summed time) and of the narrow phase (FP64
+    pipe, FP64-equivalent flops over its time)."""
+    algo = stage_algorithmic(st, nV, nE, nF)
+    out = {}
+    broad_ms = sum(stages.get(k, 0.0) for k in ("boxes", "sort", "sweep"))
+    if broad_ms > 0:
+        by = sum(algo[k][1] for k in ("boxes", "sort", "sweep"))
+        out["broad_hbm_frac"] = by / (broad_ms * 1e-3) / 1e9 / hbm_gbs
+    if stages.get("narrow", 0.0) > 0:
+        out["narrow_fp64_frac"] = algo["narrow"][1] / (stages["narrow"] * 1e-3) / (fp64_gflops * 1e9)
+    return out
+
+
+def time_steps(c, d, min_sep, steps, flush):
+    """Median device time of ccd_step (device output), its stages and the
+    counters of the last step; the pair buffers are sized by one synchronous
+    step first."""
+    import torch
+    from paper_2112_06300_gb300 import ccd
+    stream = torch.cuda.current_stream()
+    out = torch.empty(1, dtype=torch.float64, device=d[0].device)
+    t_ref = c.step(*d, min_sep=min_sep)
+    for _ in range(2):
+        ccd.ccd_step(c.ctx, *d, 1e-6, min_sep, 10 ** 6, out)
+    ms, stages = [], {k: [] for k in ccd.STAGES}
+    for _ in range(steps):
+        flush.zero_()
+        a, b = _events()
+        a.record(stream)
+        ccd.ccd_step(c.ctx, *d, 1e-6, min_sep, 10 ** 6, out)
+        b.record(stream)
+        for k, v in c.stage_times().items():     # synchronizes
+            stages[k].append(v)
+        ms.append(a.elapsed_time(b))
+    rc, st = c.status()
+    assert rc == 0, ccd.ccd_status_str(rc)
+    assert float(out.item()) == t_ref
+    return {"ms": float(np.median(ms)), "stages": {k: float(np.median(v)) for k, v in stages.items()},
+            "stats": st, "toi": t_ref}
+
+
+def form_scene(name, s, min_sep, steps, flush, fp64_gflops, hbm_gbs, per_pair=False):
+    """One scene: the step in this library's form (FP32 broad + exact filter,
+    FP64 narrow) and in the plain FP64 form (FP64 broad throughout, same
+    narrow phase), queries/s and fractions of roofline of each."""
+    from paper_2112_06300_gb300 import ccd
+    d = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F, "cuda:0")
+    nV, nE, nF = len(s.V0), len(s.E), len(s.F)
+    res = {"workload": name, "boxes": nV + nE + nF, "min_sep": min_sep}
+    for form, o in (("fp32_broad", {}), ("plain_fp64", {"broad_fp64": 1})):
+        c = ccd.CCD(0, profile_stages=1, **o)
+        r = time_steps(c, d, min_sep, steps, flush)
+        st = r["stats"]
+        q = st["n_vf"] + st["n_ee"]
+        res[form] = {"ms_per_step": r["ms"], "queries": q, "queries_per_s": q / (r["ms"] * 1e-3),
+                     "stages_ms": r["stages"], "toi": r["toi"], "intervals": st["n_intervals"],
+                     "capped": st["n_capped"], "superset_fp32": st["n_superset"],
+                     **_roof(st, r["stages"], nV, nE, nF, fp64_gflops, hbm_gbs)}
+        if per_pair and form == "fp32_broad":
+            # the configuration's output: sorted pair lists and per-pair times
+            import torch
+            vf, ee = c.broad(*d)
+            a, b = _events()
+            a.record()
+            nr = c.narrow(vf, ee, *d, 1e-6, min_sep, 10 ** 6, 0)
+            b.record()
+            torch.cuda.synchronize()
+            res[form]["per_pair_narrow_ms"] = a.elapsed_time(b)
+            res[form]["per_pair_toi_min"] = nr.toi_min
+        c.close()
+    res["step_speedup_vs_plain_fp64"] = res["plain_fp64"]["ms_per_step"] / res["fp32_broad"]["ms_per_step"]
+    assert res["plain_fp64"]["toi"] == res["fp32_broad"]["toi"]
+    return res
+
+
+def form_stress(steps, fp64_gflops):
+    """The narrow-phase stress workload: 2^24 standalone queries, per-pair
+    times, and the exact-oracle subset of 100,000 stored queries (false
+    negatives, late times, false positives).  The exact times were written by
+    tests/golden/make_stress_exact.py; here they are only read."""
+    import torch
+    from paper_2112_06300_gb300 import ccd, scenes
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_stress_exact as G
+    n = G.N_QUERIES
+    X0, X1, is_vf, kind = scenes.narrow_stress_queries(n, G.GEN_SEED)
+    head, idx, rd = G.read()
+    same = head.get("sha256") == G.fingerprint(X0, X1, is_vf, idx)
+    sc, vf, ee, order = scenes.pack_queries(X0, X1, is_vf)
+    del X0, X1
+    d = ccd.mesh_to_device(sc.V0, sc.V1, sc.E, sc.F, "cuda:0")
+    vfd, eed = torch.from_numpy(vf).cuda(), torch.from_numpy(ee).cuda()
+    c = ccd.CCD(0, profile_stages=1)
+    ms = []
+    for k in range(1 + steps):
+        a, b = _events()
+        a.record()
+        r = c.narrow(vfd, eed, *d, 1e-6, 0.0, 10 ** 6, 0)
+        b.record()
+        torch.cuda.synchronize()
+        if k:
+            ms.append(a.elapsed_time(b))
+    rc, st = c.status()
+    toi = np.empty(n)
+    flags = np.empty(n, np.uint8)
+    toi[order] = np.concatenate([r.toi_vf.cpu().numpy(), r.toi_ee.cpu().numpy()])
+    flags[order] = np.concatenate([r.flags_vf.cpu().numpy(), r.flags_ee.cpu().numpy()])
+    c.close()
+    m = float(np.median(ms))
+    flops = FLOPS_PER_INTERVAL * st["n_intervals"] + FLOPS_PER_UNIT * (n + st["n_exported"])
+    out = {"workload": "2^24 standalone queries, 50/50 VF/EE, 2^-20 grid, mix 40/20/10/10/20, delta=1e-6, "
+                       "max_iter=1e6, per-pair times", "queries": n, "ms": m, "queries_per_s": n / (m * 1e-3),
+           "intervals": st["n_intervals"], "capped": st["n_capped"], "flagged": int((flags != 0).sum()),
+           "collisions": int(np.isfinite(toi).sum()),
+           "narrow_fp64_frac": flops / (m * 1e-3) / (fp64_gflops * 1e9),
+           "vs_plain_fp64": "same kernel (no broad phase in this workload)"}
+    if same:
+        out["exact_subset"] = G.summarize(toi[idx], flags[idx], rd)
+    else:
+        out["exact_subset"] = "generator output differs from the stored subset; not compared"
+    return out
 
 
 def environments(n):
@@ -433,13 +577,14 @@ def chunks_by_memory(envs, ccd):
     return out
 
 
-def run_batch(args):
+def form_batch(envs, steps, warmup):
+    """Batched form: every environment in batches sized by the memory model
+    for a 64 GiB budget, one batched step per batch; a sample of scenes is
+    stepped alone (FP32 form and plain FP64 form) for parity and for the
+    per-scene comparison."""
     import torch
-    from oracle import oracle as O
-    from paper_2112_06300_gb300 import build, ccd, scenes
-    build.build()
+    from paper_2112_06300_gb300 import ccd, scenes
     torch.cuda.set_device(0)
-    envs = environments(args.envs)
     groups = chunks_by_memory(envs, ccd)
     nb_max = max(sum(e.n_boxes for e in g) for g in groups)
     cap = int(PAIRS_PER_BOX * nb_max) + (1 << 20)
@@ -452,30 +597,50 @@ def run_batch(args):
         offs = [torch.from_numpy(a).to(dev) for a in (vo, eo, fo)]
         prepared.append((d, offs, torch.empty(len(g), dtype=torch.float64, device=dev)))
     stream = torch.cuda.current_stream()
-    for (d, offs, out) in prepared[:1] * max(1, args.warmup):
+    for (d, offs, out) in prepared[:1] * max(1, warmup):
         ccd.ccd_step_batch(c.ctx, *offs, *d, 1e-6, 0.0, 10 ** 6, out)
     torch.cuda.synchronize()
-    ms_all = []
-    for _ in range(args.steps):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in prepared]
+    ms_all, pairs = [], 0
+    for _ in range(steps):
+        ev = [_events() for _ in prepared]
+        pairs = 0
         for (d, offs, out), (a, b) in zip(prepared, ev):
             a.record(stream)
             ccd.ccd_step_batch(c.ctx, *offs, *d, 1e-6, 0.0, 10 ** 6, out)
             b.record(stream)
+            rc, st = c.status()
+            assert rc == 0, ccd.ccd_status_str(rc)
+            pairs += st["n_vf"] + st["n_ee"]
         torch.cuda.synchronize()
         ms_all.append(sum(a.elapsed_time(b) for a, b in ev))
-        rc, st = c.status()
-        assert rc == 0, ccd.ccd_status_str(rc)
     toi = np.concatenate([out.cpu().numpy() for (_, _, out) in prepared])
-    # parity on a seeded sample of environments
-    rng = np.random.default_rng(0)
-    sample = rng.choice(len(envs), size=min(16, len(envs)), replace=False)
-    for k in sample:
-        e = envs[k]
-        assert toi[k] == O.step(e.V0, e.V1, e.E, e.F), k
+    c.close()
     ms = float(np.median(ms_all))
-    # one batch of 512 environments stepped repeatedly: launch sequence vs
-    # captured graph
+    # a sample of environments stepped alone: the same time (parity of the
+    # batch against single-scene steps), and the per-scene time of the plain
+    # FP64 form for the comparison
+    rng = np.random.default_rng(0)
+    sample = rng.choice(len(envs), size=min(64, len(envs)), replace=False)
+    alone_ms = {}
+    for form, o in (("fp32_broad", {}), ("plain_fp64", {"broad_fp64": 1})):
+        ca = ccd.CCD(0)
+        tot = 0.0
+        for k in sample:
+            e = envs[k]
+            d = ccd.mesh_to_device(e.V0, e.V1, e.E, e.F, dev)
+            t = ca.step(*d)
+            assert t == toi[k], (form, k, t, toi[k])
+            out = torch.empty(1, dtype=torch.float64, device=dev)
+            a, b = _events()
+            a.record(stream)
+            ccd.ccd_step(ca.ctx, *d, 1e-6, 0.0, 10 ** 6, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        ca.close()
+        alone_ms[form] = tot / len(sample) * len(envs)
+    # one batch of 512 environments stepped repeatedly: launch sequence
+    # against the captured CUDA graph
     sub = envs[:512]
     V0, V1, E, F, vo, eo, fo = scenes.concat_scenes(sub)
     d = ccd.mesh_to_device(V0, V1, E, F, dev)
@@ -487,7 +652,7 @@ def run_batch(args):
         for _ in range(3):
             ccd.ccd_step_batch(cg.ctx, *offs, *d, 1e-6, 0.0, 10 ** 6, out)
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a, b = _events()
         a.record(stream)
         for _ in range(10):
             ccd.ccd_step_batch(cg.ctx, *offs, *d, 1e-6, 0.0, 10 ** 6, out)
@@ -498,106 +663,143 @@ def run_batch(args):
         cg.close()
     tri = sum(len(e.F) for e in envs)
     boxes = sum(e.n_boxes for e in envs)
-    line = {"metric": "environments/s (batched earliest-TOI step)", "value": len(envs) / (ms * 1e-3),
-            "unit": "envs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded rigid environments)",
-            "config": {"workload": f"{len(envs)} rigid environments, 500-50,000 triangles (log-uniform), "
-                                   f"|v| <= 0.05, delta=1e-6", "triangles": tri, "boxes": boxes,
-                       "batches": len(groups), "pair_capacity": cap, "memory_budget_bytes": BUDGET,
-                       "pairs": int(st["n_vf"] + st["n_ee"]),
-                       "collisions": int(np.isfinite(toi).sum()), "parity_sample": len(sample)},
-            "boxes_per_s": boxes / (ms * 1e-3),
+    return {"workload": f"{len(envs)} rigid environments, 500-50,000 triangles (log-uniform), |v| <= 0.05, "
+                        f"delta=1e-6, batches sized for a 64 GiB budget",
+            "envs": len(envs), "triangles": tri, "boxes": boxes, "batches": len(groups), "ms": ms,
+            "envs_per_s": len(envs) / (ms * 1e-3), "queries": int(pairs), "queries_per_s": pairs / (ms * 1e-3),
+            "collisions": int(np.isfinite(toi).sum()),
+            "one_scene_per_call_ms": {"fp32_broad": alone_ms["fp32_broad"], "plain_fp64": alone_ms["plain_fp64"],
+                                      "note": f"extrapolated from {len(sample)} environments stepped alone"},
+            "speedup_vs_plain_fp64_one_scene_per_call": alone_ms["plain_fp64"] / ms,
+            "parity_sample": f"{len(sample)} environments: batched time == the scene stepped alone",
             "batch512_ms": rep}
-    print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
-    from paper_2112_06300_gb300 import build, ccd
-    build.build()
-    envs = environments(args.envs)
-    srv = ccd.Server(0, n_slots=2, max_scenes=256, memory_cap=BUDGET, arena_bytes=4 << 30,
+def form_serve(envs, rate, n_slots=2, verify=32):
+    """Serving form: the environments arrive as a Poisson stream; at its
+    arrival time a client writes the scene into the server's arena and
+    submits it.  Latency runs from the arrival (before the write) to the
+    completion; a sample of results is compared with the scene stepped
+    alone."""
+    from paper_2112_06300_gb300 import ccd
+    srv = ccd.Server(0, n_slots=n_slots, max_scenes=256, memory_cap=BUDGET, arena_bytes=4 << 30,
                      pairs_per_box=PAIRS_PER_BOX, autotune=1)
     for e in envs[:64]:                              # warm-up: contexts and buffers grow
         srv.wait(srv.submit_scene(e.V0, e.V1, e.E, e.F))
     rng = np.random.default_rng(3)
-    gaps = rng.exponential(1.0 / args.rate, len(envs))
-    arrive = np.cumsum(gaps)
-    # every scene is written into the server's arena before the clock starts
-    # (the clients' own work); the clock covers submissions at the Poisson
-    # arrival times and the server's batching, transfers and steps
-    tickets = []
-    for e in envs:
-        t, a, b, ee, ff = srv.request(len(e.V0), len(e.E), len(e.F))
-        if len(e.V0):
-            a[...] = e.V0.T
-            b[...] = e.V1.T
-        if len(e.E):
-            ee[...] = e.E
-        if len(e.F):
-            ff[...] = e.F
-        tickets.append(t)
+    arrive = np.cumsum(rng.exponential(1.0 / rate, len(envs)))
+    tickets, write_ms = [], np.empty(len(envs))
     t0 = time.perf_counter()
-    for k, t in enumerate(tickets):
+    for k, e in enumerate(envs):
         while time.perf_counter() - t0 < arrive[k]:
             pass
-        srv.submit(t)
+        tw = time.perf_counter()
+        tickets.append(srv.submit_scene(e.V0, e.V1, e.E, e.F))
+        write_ms[k] = (time.perf_counter() - tw) * 1e3
     t_sub = time.perf_counter() - t0
     res = [srv.wait(t) for t in tickets]
     t_all = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
-    lat = np.array([r[1] for r in res])
+    lat_srv = np.array([r[1] for r in res])       # submission -> completion
+    lat = lat_srv + write_ms                       # arrival -> completion
     toi = np.array([r[0] for r in res])
-    line = {"metric": "served CCD steps/s and p50/p99 latency (ms), Poisson arrivals",
-            "value": len(envs) / t_all, "unit": "steps/s", "n_gpus": 1, "steps": len(envs), "warmup": 64,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded rigid environments)",
-            "config": {"workload": f"{len(envs)} rigid environments arriving as a Poisson stream at "
-                                   f"{args.rate:g}/s (scenes written to the arena beforehand), 2 slots "
-                                   f"autotuned on their first batch, <= 256 scenes per batch, 64 GiB cap",
-                       "offered_rate": len(envs) / t_sub, "target_rate": args.rate},
+    c = ccd.CCD(0)
+    pick = np.random.default_rng(4).choice(len(envs), size=min(verify, len(envs)), replace=False)
+    for k in pick:
+        e = envs[k]
+        assert c.step(*ccd.mesh_to_device(e.V0, e.V1, e.E, e.F, "cuda:0")) == toi[k], k
+    c.close()
+    return {"workload": f"{len(envs)} rigid environments arriving as a Poisson stream at {rate:g}/s, {n_slots} slots "
+                        f"autotuned on their first batch, <= 256 scenes per batch, 64 GiB cap",
+            "steps_per_s": len(envs) / t_all, "offered_rate": len(envs) / t_sub, "target_rate": rate,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "mean": float(lat.mean()), "max": float(lat.max())},
+                           "mean": float(lat.mean()), "max": float(lat.max()),
+                           "client_write_p50": float(np.percentile(write_ms, 50)),
+                           "server_p50": float(np.percentile(lat_srv, 50)),
+                           "server_p99": float(np.percentile(lat_srv, 99))},
             "batches": st["n_batches"], "max_batch_scenes": st["max_batch_scenes"],
-            "collisions": int(np.isfinite(toi).sum())}
+            "max_inflight_bytes": st["max_inflight_bytes"], "collisions": int(np.isfinite(toi).sum()),
+            "parity_sample": f"{len(pick)} served results == the scene stepped alone"}
+
+
+def form_precision(n, steps, flush, fp64_gflops, hbm_gbs):
+    """Precision form: the folded cloth plus 1,000 rigid bodies.  Broad phase
+    in single precision (outward-rounded boxes) then the exact FP64 filter,
+    against the all-FP64 broad phase (same cell sweep on FP64 extents);
+    superset size, final-set equality, broad and whole-step times."""
+    import torch
+    from paper_2112_06300_gb300 import ccd, scenes
+    s = scenes.cloth_and_bodies(n)
+    d = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F, "cuda:0")
+    out = form_scene(f"folded cloth {n}x{n} + 500 icospheres (5,120 tri) + 500 tori (3,072 tri) in [0,10]^3, "
+                     "placed without interpenetration", s, 0.0, steps, flush, fp64_gflops, hbm_gbs)
+    key = lambda t: torch.sort(t[:, 0].long() * (1 << 32) + t[:, 1].long())[0]
+    sets = {}
+    for form, o in (("fp32_broad", {}), ("plain_fp64", {"broad_fp64": 1})):
+        c = ccd.CCD(0)
+        vf, ee = c.broad(*d)
+        sets[form] = (key(vf), key(ee))
+        c.close()
+    out["final_sets_equal"] = bool(torch.equal(sets["fp32_broad"][0], sets["plain_fp64"][0]) and
+                                   torch.equal(sets["fp32_broad"][1], sets["plain_fp64"][1]))
+    out["broad_ms"] = {f: sum(out[f]["stages_ms"][k] for k in ("boxes", "sort", "sweep"))
+                       for f in ("fp32_broad", "plain_fp64")}
+    out["broad_speedup_vs_plain_fp64"] = out["broad_ms"]["plain_fp64"] / out["broad_ms"]["fp32_broad"]
+    return out
+
+
+def run_forms(args, flush, fp64_gflops, hbm_gbs):
+    """Every other configuration of the benchmark, for the "forms" object."""
+    from paper_2112_06300_gb300 import scenes
+    forms = {}
+    t0 = time.perf_counter()
+    forms["cloth_min_sep_1e-4"] = form_scene(workload_name(args.n).replace("min_sep=0", "min_sep=1e-4"),
+                                             scenes.folded_cloth(args.n, seed=1), 1e-4, 3, flush,
+                                             fp64_gflops, hbm_gbs)
+    forms["icosphere_plane"] = form_scene("icosphere (2,562 V) on a 33x33 plane, dz=-0.1, N(0,1e-3) jitter, "
+                                          "delta=1e-6", scenes.icosphere_on_plane(0), 0.0, 10, flush,
+                                          fp64_gflops, hbm_gbs, per_pair=True)
+    forms["stress_2^24"] = form_stress(2, fp64_gflops)
+    forms["precision"] = form_precision(args.n, 3, flush, fp64_gflops, hbm_gbs)
+    envs = environments(args.envs)
+    forms["batched"] = form_batch(envs, 3, 2)
+    forms["serving"] = form_serve(envs, args.rate)
+    forms["seconds"] = time.perf_counter() - t0
+    return forms
+
+
+def run_batch(args):
+    line = {"metric": "environments/s (batched earliest-TOI step)", "unit": "envs/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic (seeded rigid environments)"}
+    r = form_batch(environments(args.envs), args.steps, args.warmup)
+    line.update({"value": r["envs_per_s"], "ms_per_step": r["ms"], "config": {"workload": r["workload"]}, **r})
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    from paper_2112_06300_gb300 import build
+    build.build()
+    r = form_serve(environments(args.envs), args.rate)
+    line = {"metric": "served CCD steps/s and p50/p99 latency (ms), Poisson arrivals", "value": r["steps_per_s"],
+            "unit": "steps/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic (seeded rigid environments)", "config": {"workload": r["workload"]}, **r}
     print(json.dumps(line), flush=True)
 
 
 def run_precision(args):
     import torch
-    from paper_2112_06300_gb300 import build, ccd, scenes
+    from paper_2112_06300_gb300 import build, ccd
     build.build()
     torch.cuda.set_device(0)
-    s = scenes.cloth_and_bodies(args.n)
-    V0, V1, E, F = ccd.mesh_to_device(s.V0, s.V1, s.E, s.F)
-    res = {}
-    sets = {}
-    for name, o in (("fp32_strips", {}), ("fp64_strips", {"broad_fp64": 1}), ("fp32_tiled", {"sweep_kernel": 2}),
-                    ("fp64_warp_per_box", {"broad_fp64": 1, "sweep_kernel": 1})):
-        c = ccd.CCD(0, profile_stages=1, **o)
-        vf, ee = c.broad(V0, V1, E, F)
-        times = []
-        for _ in range(max(1, args.steps // 4)):
-            c.broad(V0, V1, E, F)
-            t = c.stage_times()
-            times.append(t["boxes"] + t["sort"] + t["sweep"])
-        rc, st = c.status()
-        t_step = c.step(V0, V1, E, F)
-        res[name] = {"broad_ms": float(np.median(times)), "candidates_fp32": int(st["n_superset"]),
-                     "pairs": int(len(vf) + len(ee)), "toi": t_step}
-        key = lambda t: torch.sort(t[:, 0].long() * (1 << 32) + t[:, 1].long())[0]
-        sets[name] = (key(vf), key(ee))
-        c.close()
-    eq = all(torch.equal(sets[n][0], sets["fp64_strips"][0]) and torch.equal(sets[n][1], sets["fp64_strips"][1])
-             for n in sets)
-    line = {"metric": "broad-phase ms: FP32 outward-rounded + exact FP64 filter vs all-FP64 (same strip sweep)",
-            "value": res["fp64_strips"]["broad_ms"] / res["fp32_strips"]["broad_ms"],
-            "unit": "x (FP64 ms / FP32 ms)",
-            "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64 / f64", "data": "synthetic (seeded)",
-            "config": {"workload": f"folded cloth {args.n}x{args.n} + 500 icospheres (5,120 tri) + 500 tori "
-                                   f"(3,072 tri) in [0,10]^3", "boxes": s.n_boxes},
-            "forms": res, "final_sets_equal": bool(eq)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:0")
+    peaks, _ = measured_peaks()
+    r = form_precision(args.n, max(3, args.steps // 4), flush, ccd.ccd_measure_fp64_peak(0),
+                       float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS)))
+    line = {"metric": "broad-phase ms: FP32 outward-rounded + exact FP64 filter vs all-FP64 (same cell sweep)",
+            "value": r["broad_speedup_vs_plain_fp64"], "unit": "x (FP64 ms / FP32 ms)", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32+f64 / f64", "data": "synthetic (seeded)",
+            "config": {"workload": r["workload"]}, **r}
     print(json.dumps(line), flush=True)
 
 

@@ -800,6 +800,31 @@ constexpr int kIdleRounds = 1 << 14;   // idle warp rounds before a warp retires
 // slow the busy warps of the tail (measured: 0.25-2 us worse, 1-32 us best)
 constexpr unsigned kNapMin = 1000, kNapMax = 32000;
 constexpr int kRefresh = 8;            // iterations between reads of the shared values
+// A query whose work is split over several units (donation, hand-off) shares
+// one iteration budget: each unit counts its evaluations in windows of at
+// most kBudgetWindow and adds them to the query's counter at the end of each
+// window, where it also learns whether the query has passed max_iter.  A
+// query kept by one lane counts privately and is capped exactly at max_iter.
+constexpr long long kBudgetWindow = 64;
+
+// End of a budget window of a unit of a split query (cnt = cap_left + 1: the
+// evaluation about to run is the first past the window): add the window's
+// evaluations to the query's counter; if the query is still within max_iter,
+// open the next window with this evaluation counted and return true.  A unit
+// that owns its whole query has no windows (its budget is max_iter itself).
+__device__ __forceinline__ bool next_budget_window(const NarrowArgs &A, int64_t q, bool whole, long long &cnt,
+                                                   long long &cap_left) {
+  if (whole) return false;
+  const unsigned long long done = (unsigned long long)(cnt - 1);
+  const unsigned long long tot = atomicAdd(&A.qiters[q], done) + done;
+  if (tot < (unsigned long long)A.max_iter) {
+    cnt = 1;
+    cap_left = min(kBudgetWindow, A.max_iter - (long long)tot);
+    return true;
+  }
+  cnt = 1;   // flushed; the cap path below takes the attempted evaluation back out
+  return false;
+}
 
 // Control flow is warp-uniform at the loop level: refill, idling and exit are
 // decided for the whole warp (ballots and broadcasts), and the per-lane work
@@ -839,6 +864,9 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   // bit d of (axhi, axlo) is the axis that was split to reach depth d; a unit
   // that goes deeper (`deep`) backtracks by walking the path instead
   unsigned pend = 0, axlo = 0, axhi = 0;
+  // bit d of tright: the path node at depth d is the right child of a split
+  // along t (the path's t_lo grows exactly at those depths)
+  unsigned tright = 0;
   bool deep = false;
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
   long long cnt = 0, cap_left = 0;
@@ -1070,7 +1098,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           const int sidv = __shfl_sync(FULL, sid, src);
           const int vfv = __shfl_sync(FULL, (int)vf, src);
           const unsigned long long tqv = __shfl_sync(FULL, tq, src);
-          const long long capv = __shfl_sync(FULL, cap_left - cnt, src);
+
           if (recv) {
             q = qv;
             sid = sidv;
@@ -1078,10 +1106,10 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
             vf = vfv != 0;
             N = Node{s0, s1, s2, l0, l1, l2};
             depth = root_depth = N.depth();
-            pend = 0;
+            pend = tright = 0;
             deep = depth > 31;
             tq = tqv;
-            cap_left = capv;
+            cap_left = min(kBudgetWindow, A.max_iter);   // the query's shared budget, in windows
             cnt = 0;
             flags = 0;
             have = true;
@@ -1090,6 +1118,14 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           if (give) {
             root_depth = dS;   // the donated sibling is no longer ours
             ++n_don;
+            if (whole) {
+              // the query's budget becomes shared: publish the evaluations so
+              // far (the counter was 0 while this lane owned the query)
+              atomicAdd(&A.qiters[q], (unsigned long long)cnt);
+              cap_left = min(kBudgetWindow, cap_left - cnt);
+              cnt = 0;
+              whole = false;
+            }
           }
         }
       }
@@ -1151,7 +1187,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         K[x] = Q.K[x];
       }
       depth = root_depth = N.depth();
-      pend = 0;
+      pend = tright = 0;
       deep = depth > 31;
       cnt = 0;
       flags = 0;
@@ -1167,7 +1203,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         }
       } else {
         if (A.mode == 0) tq = ld_relaxed_u64(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf]);
-        cap_left = A.max_iter - (long long)ld_relaxed_u64(&A.qiters[q]);
+        const long long used = (long long)ld_relaxed_u64(&A.qiters[q]);
+        cap_left = used >= A.max_iter ? 0 : min(kBudgetWindow, A.max_iter - used);
       }
       fresh = false;
     }
@@ -1207,7 +1244,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         // pruned: starts at or after the current t*
       } else if (vf && outside_simplex(N)) {
         // vertex-face: u_lo > 1 - v_lo, the interval lies outside the simplex
-      } else if (!(A.no_zero && N.n0 == 0) && ++cnt > cap_left) {
+      } else if (!(A.no_zero && N.n0 == 0) && ++cnt > cap_left && !next_budget_window(A, q, whole, cnt, cap_left)) {
         // iteration cap: t* = min(t*, earliest left end among the live intervals)
         unsigned long long m = dbits(dyadic(N.n0, N.l0));
         Node W = N;
@@ -1342,13 +1379,31 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           tq = dbits(dyadic(N.n0, N.l0));
           if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);
           if (A.mode == 2) atomicMin(&A.toi_scene[sid], tq);
+          // Every owed sibling that starts at or after T = this node's t_lo is
+          // now pruned; drop them from the path at once instead of visiting
+          // them one by one.  A t-sibling starts after T (T lies in its left
+          // neighbour); a u- or v-sibling at depth d starts at the t_lo of
+          // the path node at depth d - 1, which is below T only if the path
+          // went right along t somewhere at depth >= d.
+          const int D = tright ? 31 - __clz((int)tright) : 0;
+          pend &= (axlo | axhi) & (D >= 31 ? ~0u : (2u << D) - 1u);
         } else {
           N.down_left(a);
           depth += 1;
           node_done = false;
           if (depth < 32) {
             const unsigned bit = 1u << depth;
-            pend |= bit;
+            // the right child is owed unless it is already pruned (t* only
+            // falls) or lies outside the vertex-face simplex
+            bool owe = true;
+            if (a == 0) {
+              owe = s53(N.n0 + 1, N.l0) < cut53;
+            } else if (vf) {
+              owe = !(a == 1 ? s53(N.n1 + 1, N.l1) + s53(N.n2, N.l2) > (1ull << 53)
+                             : s53(N.n1, N.l1) + s53(N.n2 + 1, N.l2) > (1ull << 53));
+            }
+            pend = owe ? (pend | bit) : (pend & ~bit);
+            tright &= ~bit;
             axlo = (a & 1) ? (axlo | bit) : (axlo & ~bit);
             axhi = (a & 2) ? (axhi | bit) : (axhi & ~bit);
           } else {
@@ -1384,6 +1439,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         N.add(a, 1);
         depth = ds;
         pend &= ~(~0u << ds);
+        tright = (tright & ~(~0u << ds)) | (a == 0 ? 1u << ds : 0u);
         const bool pruned = s53(N.n0, N.l0) >= cut53;
         const bool outside = vf && outside_simplex(N);
         if (!pruned && !outside) break;
@@ -1447,8 +1503,9 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
                 atomicMin(&ctl->toi_bits, tq);
             }
             atomicAdd(&A.qiters[q], (unsigned long long)cnt);
-            cap_left -= cnt;
+            cap_left = min(kBudgetWindow, cap_left - cnt);   // (the query's budget is shared from now on)
             cnt = 0;
+            whole = false;
             ring_write(A.ring, A.ring_mask, pos0 + __popc(xm & lt_mask), (uint32_t)q, S, &ctl->status);
             root_depth = dS;
             ++n_exp;
