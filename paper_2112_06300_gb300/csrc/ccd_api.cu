@@ -38,6 +38,8 @@ struct ccd_ctx {
   unsigned long long *qiters = nullptr;
   unsigned long long *qrec = nullptr;          // query records, 24 x cap_q words
   int *qsid = nullptr;                         // scene of each query (batched scenes)
+  double *prims = nullptr;                     // per-primitive set-up records of the narrow phase
+  int64_t cap_prims = 0;                       // (words)
   // batched scenes
   int64_t cap_bsid = 0, cap_scenes = 0;
   int *bsid = nullptr, *saxis = nullptr;
@@ -219,6 +221,18 @@ int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
   CK(cudaMalloc(&c->qrec, cap * (24 * sizeof(unsigned long long) + 33 * sizeof(float))));
   CK(cudaMalloc(&c->qsid, cap * sizeof(int)));
   c->cap_q = cap;
+  return CCD_OK;
+}
+
+// Per-primitive set-up records of the narrow phase for a mesh of nV, nE, nF.
+int ensure_prims(ccd_ctx *c, int64_t nV, int64_t nE, int64_t nF) {
+  const int64_t pw = narrow_prim_words(nV, nE, nF);
+  if (pw <= c->cap_prims) return CCD_OK;
+  if (c->prims) CK(cudaFree(c->prims));
+  c->prims = nullptr;
+  c->cap_prims = 0;
+  CK(cudaMalloc(&c->prims, pw * sizeof(double)));
+  c->cap_prims = pw;
   return CCD_OK;
 }
 
@@ -509,7 +523,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
 
 int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee,
                   int counts_from_ctl, const double *V0, const double *V1, int64_t nV, const int32_t *E,
-                  const int32_t *F, double delta, double min_sep, int64_t max_iter, int mode,
+                  int64_t nE, const int32_t *F, int64_t nF, double delta, double min_sep, int64_t max_iter, int mode,
                   unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s,
                   bool zero_rule_pass = false, int n_scenes = 0, const int64_t *voff = nullptr,
                   unsigned long long *toi_scene = nullptr, int64_t ee_end = 0, bool keep_toi = false,
@@ -517,6 +531,12 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   const int64_t nq = counts_from_ctl && ee_end > 0 ? ee_end : n_vf + n_ee;
   int rc = ensure_narrow(c, nq, s);
   if (rc) return rc;
+  const int64_t nP = nV + nE + nF;
+  if (narrow_prim_words(nV, nE, nF) > c->cap_prims) {
+    if (c->capturing) return CCD_EINVAL;   // (buffers are sized before a capture)
+    rc = ensure_prims(c, nV, nE, nF);
+    if (rc) return rc;
+  }
   if (zero_rule_pass)
     k_nozero_prepare<<<1, 1, 0, s>>>(c->ctl);
   else
@@ -533,8 +553,11 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   A.V0 = V0;
   A.V1 = V1;
   A.nV = nV;
+  A.nE = nE;
+  A.nF = nF;
   A.E = E;
   A.F = F;
+  A.prims = c->prims;
   A.delta = delta;
   A.min_sep = min_sep;
   A.max_iter = max_iter;
@@ -555,13 +578,19 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   A.toi_scene = toi_scene;
   A.qsid = c->qsid;
   if (!zero_rule_pass) mark(c, CCD_STAGE_NARROW, true, s);
-  // query records: one dense pass (the zero-TOI pass has min_sep = 0: redo it)
+  // per-primitive set-up (independent of min_sep: the zero-TOI pass reuses
+  // it), then the query records in one dense pass (the zero-TOI pass has
+  // min_sep = 0: redo them)
+  const bool prims = !zero_rule_pass && nP > 0;
+  if (prims)
+    k_prepare_prims<<<(unsigned)std::min<int64_t>(cdiv(nP, 256), (int64_t)c->sm_count * 16), 256, 0, s>>>(A);
   k_prepare_queries<<<(unsigned)std::min<int64_t>(cdiv(std::max<int64_t>(nq, 1), 256), (int64_t)c->sm_count * 16),
                       256, 0, s>>>(A);
   k_narrow<<<c->narrow_blocks, kNarrowThreads, kNarrowDynSmem, s>>>(A);
   if (zero_rule_pass) k_nozero_finish<<<1, 1, 0, s>>>(c->ctl);
   mark(c, CCD_STAGE_NARROW, false, s);
-  c->n_launches += zero_rule_pass ? 4 : 3;    // reset/prepare, records, narrow, finish
+  // reset/prepare, primitives, records, narrow, finish
+  c->n_launches += (zero_rule_pass ? 4 : 3) + (prims ? 1 : 0);
   CK(cudaGetLastError());
   return CCD_OK;
 }
@@ -696,6 +725,7 @@ int ccd_destroy(ccd_ctx *c) {
   cudaFree(c->qiters);
   cudaFree(c->qrec);
   cudaFree(c->qsid);
+  cudaFree(c->prims);
   cudaFree(c->bsid);
   cudaFree(c->ssum);
   cudaFree(c->saxis);
@@ -765,7 +795,7 @@ int ccd_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee, i
   unsigned long long *tv = mode == 0 ? (unsigned long long *)toi_vf : nullptr;
   unsigned long long *te = mode == 0 ? (unsigned long long *)toi_ee : nullptr;
   const int g = (int)std::min<int64_t>(cdiv(std::max<int64_t>(n_vf + n_ee, 1), 256), (int64_t)c->sm_count * 8);
-  rc = launch_narrow(c, vf, n_vf, ee, n_ee, 0, V0, V1, nV, E, F, delta, min_sep, max_iter, mode, tv, te, s);
+  rc = launch_narrow(c, vf, n_vf, ee, n_ee, 0, V0, V1, nV, E, nE, F, nF, delta, min_sep, max_iter, mode, tv, te, s);
   if (rc) return rc;
   if (mode == 0 && n_vf + n_ee > 0) {
     k_flags_out<<<g, 256, 0, s>>>(c->qflags, n_vf, n_ee, flags_vf, flags_ee, c->ctl);
@@ -826,7 +856,7 @@ int ranged_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, cons
     }
     k_counts_from_broad<<<1, 1, 0, s>>>(c->ctl, cap);
     c->n_launches += 1;
-    rc = launch_narrow(c, c->vf, cap, c->ee, cap, 1, V0, V1, nV, E, F, delta, min_sep, max_iter, 1, nullptr,
+    rc = launch_narrow(c, c->vf, cap, c->ee, cap, 1, V0, V1, nV, E, nE, F, nF, delta, min_sep, max_iter, 1, nullptr,
                        nullptr, s, false, 0, nullptr, nullptr, cap, !first);
     if (rc) return rc;
     first = false;
@@ -873,12 +903,12 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     if (r) return r;
     k_counts_from_broad<<<1, 1, 0, st>>>(c->ctl, c->pair_cap);
     c->n_launches += 2;
-    r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep, max_iter, 1,
+    r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, nE, F, nF, delta, min_sep, max_iter, 1,
                       nullptr, nullptr, st, false, 0, nullptr, nullptr, c->pair_cap);
     if (r) return r;
     if (c->opts.no_zero_toi) {
       // second pass only when the first found t* = 0 (decided on the device)
-      r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, 0.0, max_iter, 1,
+      r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, nE, F, nF, delta, 0.0, max_iter, 1,
                         nullptr, nullptr, st, true, 0, nullptr, nullptr, c->pair_cap);
       if (r) return r;
     }
@@ -891,6 +921,8 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     int rc = ensure_pairs(c, want);
     if (rc) return rc;
     rc = ensure_narrow(c, c->pair_cap, s);
+    if (rc) return rc;
+    rc = ensure_prims(c, nV, nE, nF);
     if (rc) return rc;
     rc = ensure_broad(c, nV + nE + nF);
     if (rc) return rc;
@@ -955,6 +987,8 @@ int ccd_step_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const 
   if (rc) return rc;
   rc = ensure_narrow(c, c->pair_cap, s);
   if (rc) return rc;
+  rc = ensure_prims(c, nV, nE, nF);
+  if (rc) return rc;
   rc = ensure_broad(c, nB);
   if (rc) return rc;
   rc = ensure_scenes(c, nB, n_scenes);
@@ -969,7 +1003,7 @@ int ccd_step_batch(ccd_ctx *c, int32_t n_scenes, const int64_t *vert_off, const 
     k_fill_u64<<<(unsigned)std::min<int64_t>(cdiv(n_scenes, 256), 1024), 256, 0, st>>>(
         (unsigned long long *)toi_out, n_scenes, 0x7FF0000000000000ull);
     c->n_launches += 3;
-    return launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F, delta, min_sep, max_iter,
+    return launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, nE, F, nF, delta, min_sep, max_iter,
                          2, nullptr, nullptr, st, false, n_scenes, vert_off, (unsigned long long *)toi_out,
                          c->pair_cap);
   };
@@ -1041,7 +1075,7 @@ int autotune_impl(ccd_ctx *c, const SceneSpec &sc, const double *V0, const doubl
       if (narrow && sc.n > 0)
         k_fill_u64<<<(unsigned)std::min<int64_t>(cdiv(sc.n, 256), 1024), 256, 0, s>>>(toi_sc, sc.n,
                                                                                      0x7FF0000000000000ull);
-      int r2 = narrow ? launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, F,
+      int r2 = narrow ? launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, nE, F, nF,
                                       c->opts.delta, c->opts.min_sep, c->opts.max_iter, sc.n > 0 ? 2 : 1, nullptr,
                                       nullptr, s, false, sc.n, sc.voff, toi_sc, c->pair_cap)
                       : launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, s, sc,
@@ -1185,7 +1219,7 @@ int ccd_selftest_unfinished_work(ccd_ctx *c, int32_t *status, void *stream) {
   c->last_stream = s;
   k_reset_status<<<1, 1, 0, s>>>(c->ctl);
   // no queries, and one unit counted as pending that no lane will ever take
-  const int rc = launch_narrow(c, nullptr, 0, nullptr, 0, 0, nullptr, nullptr, 0, nullptr, nullptr, c->opts.delta,
+  const int rc = launch_narrow(c, nullptr, 0, nullptr, 0, 0, nullptr, nullptr, 0, nullptr, 0, nullptr, 0, c->opts.delta,
                                c->opts.min_sep, c->opts.max_iter, 1, nullptr, nullptr, s, false, 0, nullptr, nullptr,
                                0, false, 1);
   if (rc) return rc;
@@ -1205,6 +1239,8 @@ int ccd_get_memory_model(const ccd_opts *o, ccd_memory_model *m) {
   // sort keys and values and the sorted arrays for 3 copies per box (strip
   // sweep), the one-list sorted arrays, copy offsets; plus the scene index
   m->bytes_per_box = 24 + 48 + 16 + 3 * (16 + 8) + 2 + 4 + 3 * (4 + 16 + 16) + (8 + 8 + 32) + 4 + 4;
+  // and the narrow phase's per-primitive set-up record (at most a face's)
+  m->bytes_per_box += narrow_prim_words(0, 0, 1) * 8;
   // per pair slot: the pair (8), two candidate slots (16), and the narrow
   // phase's per-query flags (4), counter (8), record (24 words + 33 floats)
   // and scene (4)

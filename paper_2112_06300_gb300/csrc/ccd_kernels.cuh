@@ -66,8 +66,10 @@ struct NarrowArgs {
                                  // from the front (vf), edge-edge from the back: the edge-edge
                                  // list is the last n_ee pairs (with counts_from_ctl)
   const double *V0, *V1;         // [3][nV]
-  int64_t nV;
+  int64_t nV, nE, nF;
   const int32_t *E, *F;
+  double *prims;                 // per-primitive set-up records (k_prepare_prims): vertices,
+                                 // then edges, then faces; narrow_prim_words(nV, nE, nF) words
   double delta, min_sep;
   long long max_iter;
   int mode;                      // 0 per pair, 1 earliest only, 2 earliest per scene
@@ -92,7 +94,10 @@ struct NarrowArgs {
 
 __global__ void k_narrow(NarrowArgs A);         // on query records (A.qrec required)
 __global__ void k_narrow_setup(NarrowArgs A);   // lanes set queries up themselves (A.qrec unused)
-__global__ void k_prepare_queries(NarrowArgs A);
+__global__ void k_prepare_queries(NarrowArgs A);   // needs A.prims from k_prepare_prims
+__global__ void k_prepare_prims(NarrowArgs A);
+// words of the per-primitive records: 4 per vertex, 10 per edge, 18 per face
+constexpr int64_t narrow_prim_words(int64_t nV, int64_t nE, int64_t nF) { return 4 * nV + 10 * nE + 18 * nF; }
 __global__ void k_ring_init(RingCell *ring, unsigned long long cap, unsigned long long base);
 __global__ void k_nozero_prepare(DevCtl *ctl);
 __global__ void k_nozero_finish(DevCtl *ctl);

@@ -110,47 +110,32 @@ __device__ __forceinline__ float to_float_error(double d) {
   return fe >= -126 ? __int_as_float((fe + 127) << 23) : __int_as_float(1 << (fe + 149));
 }
 
-// Per-query set-up; the reading of the error box and split weights matches the
-// oracle's setup_query.  ids: VF (P, T0, T1, T2), EE (A0, A1, B0, B1).
-__device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const double *__restrict__ V0,
-                            const double *__restrict__ V1, int64_t nV, double min_sep, double delta) {
-  double x0[4][3], x1[4][3];
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      x0[k][x] = __ldg(&V0[x * nV + ids[k]]);
-      x1[k][x] = __ldg(&V1[x * nV + ids[k]]);
-    }
-  // vector j = X - Y: VF (P - T0, T1 - T0, T2 - T0); EE (A0 - B0, A1 - A0, B1 - B0)
-#pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    const double X0[3] = {x0[0][x], vf ? x0[2][x] : x0[1][x], x0[3][x]};
-    const double Y0[3] = {vf ? x0[1][x] : x0[2][x], vf ? x0[1][x] : x0[0][x], vf ? x0[1][x] : x0[2][x]};
-    const double X1[3] = {x1[0][x], vf ? x1[2][x] : x1[1][x], x1[3][x]};
-    const double Y1[3] = {vf ? x1[1][x] : x1[2][x], vf ? x1[1][x] : x1[0][x], vf ? x1[1][x] : x1[2][x]};
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      double a = __dsub_rn(X0[j], Y0[j]);
-      double b = __dsub_rn(X1[j], Y1[j]);
-      Q.c0[j][x] = a;
-      Q.dc[j][x] = __dsub_rn(b, a);
-    }
-  }
-  unsigned long long Lt = 0, Lu = 0, Lv = 0;
+// The error-box term of one coordinate pair: bits of max(|x0|, |x1|) (the
+// magnitudes of finite doubles order like their bits).
+__device__ __forceinline__ unsigned long long abs_max_bits(double a, double b) {
+  const unsigned long long x = dbits(a) & 0x7FFFFFFFFFFFFFFFull, y = dbits(b) & 0x7FFFFFFFFFFFFFFFull;
+  return x > y ? x : y;
+}
+constexpr unsigned long long kM0 = 0x03F0000000000000ull;   // 2^-960, floor of the coordinate bound m
+// eps = m * 48 * 2^-53 from the bits of m
+__device__ __forceinline__ double eps_of(unsigned long long m) {
+  return __dmul_rn(__longlong_as_double((long long)m), 0x1.8p-48);
+}
+
+// Second half of the per-query set-up, from c0, dc (already in Q), the error
+// term eps = 48 * 2^-53 m per axis and the split weights L_u, L_v (bits):
+// the error box e = eps + min_sep moved one ulp up, the time weight L_t, the
+// split keys and the single-precision filter data.  Rounding of eps + min_sep
+// is monotone, so the box of a query is the largest box of its primitives
+// when eps comes as the largest of theirs.
+__device__ void setup_tail(QueryData &Q, const double eps_x[3], unsigned long long Lu, unsigned long long Lv,
+                           double min_sep, double delta) {
+  unsigned long long Lt = 0;
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
-    unsigned long long m = 0x03F0000000000000ull;  // 2^-960
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      unsigned long long a = dbits(x0[k][x]) & 0x7FFFFFFFFFFFFFFFull;
-      unsigned long long b = dbits(x1[k][x]) & 0x7FFFFFFFFFFFFFFFull;
-      m = a > m ? a : m;
-      m = b > m ? b : m;
-    }
-    double eps = __dmul_rn(__longlong_as_double((long long)m), 0x1.8p-48);  // 48 * 2^-53
-    double e = __dadd_rn(eps, min_sep);
-    e = __longlong_as_double(__double_as_longlong(e) + 1);                   // one ulp up
+    const double eps = eps_x[x];
+    double e = min_sep == 0.0 ? eps : __dadd_rn(eps, min_sep);   // eps + 0 is eps (eps > 0)
+    e = __longlong_as_double(__double_as_longlong(e) + 1);       // one ulp up
     Q.ebox_p[x] = f64_ord(e);
     Q.ebox_n[x] = f64_ord(-e);
     // FP32 filter bounds (derivations at inclusion32).  With S the sum over
@@ -194,21 +179,176 @@ __device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const doubl
     Q.wn[x] = __fmul_ru(wn, 1.0f + 0x1p-23f);
     double st = __dadd_rn(dabs_int(Q.dc[0][x]), dabs_int(Q.dc[1][x]));
     st = __dadd_rn(st, dabs_int(Q.dc[2][x]));
-    unsigned long long sb = dbits(st);
+    const unsigned long long sb = dbits(st);
     Lt = sb > Lt ? sb : Lt;
-    unsigned long long u0 = dbits(dabs_int(Q.c0[1][x]));
-    unsigned long long u1 = dbits(dabs_int(__dadd_rn(Q.c0[1][x], Q.dc[1][x])));
-    unsigned long long v0 = dbits(dabs_int(Q.c0[2][x]));
-    unsigned long long v1 = dbits(dabs_int(__dadd_rn(Q.c0[2][x], Q.dc[2][x])));
-    u0 = u1 > u0 ? u1 : u0;
-    v0 = v1 > v0 ? v1 : v0;
-    Lu = u0 > Lu ? u0 : Lu;
-    Lv = v0 > Lv ? v0 : Lv;
   }
   const unsigned long long kFloor = 0x0DF0000000000000ull;  // 2^-800
   Q.K[0] = Lt < kFloor ? 0 : Lt;
   Q.K[1] = Lu < kFloor ? 0 : Lu;
   Q.K[2] = Lv < kFloor ? 0 : Lv;
+}
+
+// Bits of max over axes and t in {0, 1} of |c0 + t dc| for one vector (the
+// value at t = 1 as c0 + dc, rounded): the split weight L_u or L_v.
+__device__ __forceinline__ unsigned long long edge_weight(const double c0[3], const double dc[3]) {
+  unsigned long long L = 0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const unsigned long long a = abs_max_bits(c0[x], __dadd_rn(c0[x], dc[x]));
+    L = a > L ? a : L;
+  }
+  return L;
+}
+
+// Per-query set-up; the reading of the error box and split weights matches the
+// oracle's setup_query.  ids: VF (P, T0, T1, T2), EE (A0, A1, B0, B1).
+__device__ void setup_query(QueryData &Q, bool vf, const int ids[4], const double *__restrict__ V0,
+                            const double *__restrict__ V1, int64_t nV, double min_sep, double delta) {
+  double x0[4][3], x1[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      x0[k][x] = __ldg(&V0[x * nV + ids[k]]);
+      x1[k][x] = __ldg(&V1[x * nV + ids[k]]);
+    }
+  // vector j = X - Y: VF (P - T0, T1 - T0, T2 - T0); EE (A0 - B0, A1 - A0, B1 - B0)
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const double X0[3] = {x0[0][x], vf ? x0[2][x] : x0[1][x], x0[3][x]};
+    const double Y0[3] = {vf ? x0[1][x] : x0[2][x], vf ? x0[1][x] : x0[0][x], vf ? x0[1][x] : x0[2][x]};
+    const double X1[3] = {x1[0][x], vf ? x1[2][x] : x1[1][x], x1[3][x]};
+    const double Y1[3] = {vf ? x1[1][x] : x1[2][x], vf ? x1[1][x] : x1[0][x], vf ? x1[1][x] : x1[2][x]};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double a = __dsub_rn(X0[j], Y0[j]);
+      double b = __dsub_rn(X1[j], Y1[j]);
+      Q.c0[j][x] = a;
+      Q.dc[j][x] = __dsub_rn(b, a);
+    }
+  }
+  double eps[3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    unsigned long long m = kM0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const unsigned long long a = abs_max_bits(x0[k][x], x1[k][x]);
+      m = a > m ? a : m;
+    }
+    eps[x] = eps_of(m);
+  }
+  setup_tail(Q, eps, edge_weight(Q.c0[1], Q.dc[1]), edge_weight(Q.c0[2], Q.dc[2]), min_sep, delta);
+}
+
+// Per-primitive set-up (the parts of a query's set-up that depend on one
+// primitive only, computed once per primitive instead of once per query):
+//   vertex v:  eps[3] of its coordinates, padded to 4 words;
+//   edge e:    c0[3], dc[3] of A1 - A0, eps[3] over its two vertices, the
+//              split weight of the vector (kEdgeWords words);
+//   face f:    c0[3], dc[3] of T1 - T0 and of T2 - T0, eps[3] over its three
+//              vertices, the two split weights, padded (kFaceWords words).
+// The same FP64 operations on the same operands as setup_query, so every
+// value is bit-identical; eps of a query is the largest of its primitives'
+// (rounding of m * 48 * 2^-53 is monotone in m).
+constexpr int kVertWords = 4, kEdgeWords = 10, kFaceWords = 18;
+
+__device__ __forceinline__ void load_pos(const double *__restrict__ V0, const double *__restrict__ V1, int64_t nV,
+                                         int id, double p0[3], double p1[3]) {
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    p0[x] = __ldg(&V0[x * nV + id]);
+    p1[x] = __ldg(&V1[x * nV + id]);
+  }
+}
+
+// vector Y -> X: c0 = X0 - Y0, dc = (X1 - Y1) - c0
+__device__ __forceinline__ void vec_of(const double X0[3], const double X1[3], const double Y0[3], const double Y1[3],
+                                       double c0[3], double dc[3]) {
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    c0[x] = __dsub_rn(X0[x], Y0[x]);
+    dc[x] = __dsub_rn(__dsub_rn(X1[x], Y1[x]), c0[x]);
+  }
+}
+
+__device__ __forceinline__ void store2(double *p, double a, double b) { *(double2 *)p = make_double2(a, b); }
+
+__device__ __forceinline__ double dmax_pos(double a, double b) {   // both > 0
+  return dbits(a) > dbits(b) ? a : b;
+}
+
+// Query set-up from the per-primitive records: only the vector w = P - T0
+// (vertex-face) or A0 - B0 (edge-edge) and the time weight L_t are computed
+// here; the edge vectors, eps and L_u, L_v come from the primitives.
+__device__ void setup_query_prims(QueryData &Q, bool &vf, int64_t q, const NarrowArgs &A, int &first_vertex) {
+  const double *__restrict__ P = A.prims;
+  double X0[3], X1[3], Y0[3], Y1[3], eps[3];
+  unsigned long long Lu, Lv;
+  if (q < A.n_vf) {
+    vf = true;
+    const int v = __ldg(&A.vf[2 * q]), f = __ldg(&A.vf[2 * q + 1]);
+    const int t0 = __ldg(&A.F[3 * (int64_t)f]);
+    first_vertex = v;
+    load_pos(A.V0, A.V1, A.nV, v, X0, X1);
+    load_pos(A.V0, A.V1, A.nV, t0, Y0, Y1);
+    const double *rv = P + kVertWords * (int64_t)v;
+    const double *rf = P + kVertWords * A.nV + kEdgeWords * A.nE + kFaceWords * (int64_t)f;
+    double w[kFaceWords];
+#pragma unroll
+    for (int k = 0; k < kFaceWords / 2; ++k) {
+      const double2 t = __ldg((const double2 *)rf + k);
+      w[2 * k] = t.x;
+      w[2 * k + 1] = t.y;
+    }
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Q.c0[1][x] = w[x];
+      Q.dc[1][x] = w[3 + x];
+      Q.c0[2][x] = w[6 + x];
+      Q.dc[2][x] = w[9 + x];
+      eps[x] = dmax_pos(__ldg(&rv[x]), w[12 + x]);
+    }
+    Lu = dbits(w[15]);
+    Lv = dbits(w[16]);
+  } else {
+    vf = false;
+    const int64_t r = q - A.n_vf;
+    const int a = __ldg(&A.ee[2 * r]), b = __ldg(&A.ee[2 * r + 1]);
+    const int a0 = __ldg(&A.E[2 * (int64_t)a]), b0 = __ldg(&A.E[2 * (int64_t)b]);
+    first_vertex = a0;
+    load_pos(A.V0, A.V1, A.nV, a0, X0, X1);
+    load_pos(A.V0, A.V1, A.nV, b0, Y0, Y1);
+    const double *ra = P + kVertWords * A.nV + kEdgeWords * (int64_t)a;
+    const double *rb = P + kVertWords * A.nV + kEdgeWords * (int64_t)b;
+    double wa[kEdgeWords], wb[kEdgeWords];
+#pragma unroll
+    for (int k = 0; k < kEdgeWords / 2; ++k) {
+      const double2 ta = __ldg((const double2 *)ra + k), tb = __ldg((const double2 *)rb + k);
+      wa[2 * k] = ta.x;
+      wa[2 * k + 1] = ta.y;
+      wb[2 * k] = tb.x;
+      wb[2 * k + 1] = tb.y;
+    }
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Q.c0[1][x] = wa[x];
+      Q.dc[1][x] = wa[3 + x];
+      Q.c0[2][x] = wb[x];
+      Q.dc[2][x] = wb[3 + x];
+      eps[x] = dmax_pos(wa[6 + x], wb[6 + x]);
+    }
+    Lu = dbits(wa[9]);
+    Lv = dbits(wb[9]);
+  }
+  double c0[3], dc[3];
+  vec_of(X0, X1, Y0, Y1, c0, dc);   // w = P - T0 or A0 - B0
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    Q.c0[0][x] = c0[x];
+    Q.dc[0][x] = dc[x];
+  }
+  setup_tail(Q, eps, Lu, Lv, A.min_sep, A.delta);
 }
 
 // Split rule (reading): axis with the largest L_k * 2^-l_k, ties t, u, v;
@@ -1566,9 +1706,83 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
 __global__ void __launch_bounds__(kNarrowThreads, 3) k_narrow(NarrowArgs A) { narrow_body<true>(A); }
 __global__ void __launch_bounds__(kNarrowThreads, 3) k_narrow_setup(NarrowArgs A) { narrow_body<false>(A); }
 
-// One thread per query: gather the 4 vertices at t = 0 and t = 1 and store the
-// query's set-up as a record, so that the narrow kernel's lanes set up a unit
-// from 24 coalesced loads with no FP64 work.
+// One thread per primitive: the per-primitive part of the query set-up
+// (records described at kVertWords).
+__global__ void k_prepare_prims(NarrowArgs A) {
+  if (A.only_if_rerun && A.ctl->rerun == 0) return;
+  const int64_t nP = A.nV + A.nE + A.nF;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nP; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < A.nV) {
+      double p0[3], p1[3];
+      load_pos(A.V0, A.V1, A.nV, (int)i, p0, p1);
+      double *r = A.prims + kVertWords * i;
+      double e[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const unsigned long long a = abs_max_bits(p0[x], p1[x]);
+        e[x] = eps_of(a > kM0 ? a : kM0);
+      }
+      store2(r, e[0], e[1]);
+      store2(r + 2, e[2], 0.0);
+    } else if (i < A.nV + A.nE) {
+      const int64_t k = i - A.nV;
+      const int a0 = __ldg(&A.E[2 * k]), a1 = __ldg(&A.E[2 * k + 1]);
+      double p0[3], p1[3], q0[3], q1[3], c0[3], dc[3], e[3];
+      load_pos(A.V0, A.V1, A.nV, a0, p0, p1);
+      load_pos(A.V0, A.V1, A.nV, a1, q0, q1);
+      vec_of(q0, q1, p0, p1, c0, dc);   // A1 - A0
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        unsigned long long m = kM0;
+        unsigned long long t = abs_max_bits(p0[x], p1[x]);
+        m = t > m ? t : m;
+        t = abs_max_bits(q0[x], q1[x]);
+        m = t > m ? t : m;
+        e[x] = eps_of(m);
+      }
+      double *r = A.prims + kVertWords * A.nV + kEdgeWords * k;
+      store2(r, c0[0], c0[1]);
+      store2(r + 2, c0[2], dc[0]);
+      store2(r + 4, dc[1], dc[2]);
+      store2(r + 6, e[0], e[1]);
+      store2(r + 8, e[2], __longlong_as_double((long long)edge_weight(c0, dc)));
+    } else {
+      const int64_t k = i - A.nV - A.nE;
+      const int t0 = __ldg(&A.F[3 * k]), t1 = __ldg(&A.F[3 * k + 1]), t2 = __ldg(&A.F[3 * k + 2]);
+      double p0[3], p1[3], q0[3], q1[3], s0[3], s1[3], c0a[3], dca[3], c0b[3], dcb[3], e[3];
+      load_pos(A.V0, A.V1, A.nV, t0, p0, p1);
+      load_pos(A.V0, A.V1, A.nV, t1, q0, q1);
+      load_pos(A.V0, A.V1, A.nV, t2, s0, s1);
+      vec_of(q0, q1, p0, p1, c0a, dca);   // T1 - T0
+      vec_of(s0, s1, p0, p1, c0b, dcb);   // T2 - T0
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        unsigned long long m = kM0;
+        unsigned long long t = abs_max_bits(p0[x], p1[x]);
+        m = t > m ? t : m;
+        t = abs_max_bits(q0[x], q1[x]);
+        m = t > m ? t : m;
+        t = abs_max_bits(s0[x], s1[x]);
+        m = t > m ? t : m;
+        e[x] = eps_of(m);
+      }
+      double *r = A.prims + kVertWords * A.nV + kEdgeWords * A.nE + kFaceWords * k;
+      store2(r, c0a[0], c0a[1]);
+      store2(r + 2, c0a[2], dca[0]);
+      store2(r + 4, dca[1], dca[2]);
+      store2(r + 6, c0b[0], c0b[1]);
+      store2(r + 8, c0b[2], dcb[0]);
+      store2(r + 10, dcb[1], dcb[2]);
+      store2(r + 12, e[0], e[1]);
+      store2(r + 14, e[2], __longlong_as_double((long long)edge_weight(c0a, dca)));
+      store2(r + 16, __longlong_as_double((long long)edge_weight(c0b, dcb)), 0.0);
+    }
+  }
+}
+
+// One thread per query: the query's set-up from its primitives' records
+// (k_prepare_prims) and two vertices, stored as a record, so that the narrow
+// kernel's lanes set up a unit from coalesced loads with no FP64 work.
 __global__ void k_prepare_queries(NarrowArgs A) {
   if (A.only_if_rerun && A.ctl->rerun == 0) return;
   if (A.counts_from_ctl) {
@@ -1578,13 +1792,12 @@ __global__ void k_prepare_queries(NarrowArgs A) {
   }
   const int64_t nq = A.n_vf + A.n_ee;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
-    int ids[4];
     bool vf;
-    query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
     QueryData Q;
-    setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep, A.delta);
+    int v0;
+    setup_query_prims(Q, vf, q, A, v0);
     store_record(Q, vf, A.qrec, A.rec_stride, q);
-    if (A.n_scenes > 0) A.qsid[q] = scene_of(A.voff, A.n_scenes, ids[0]);
+    if (A.n_scenes > 0) A.qsid[q] = scene_of(A.voff, A.n_scenes, v0);
   }
 }
 
