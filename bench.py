@@ -502,6 +502,26 @@ def form_scene(name, s, min_sep, steps, flush, fp64_gflops, hbm_gbs, per_pair=Fa
         c.close()
     res["step_speedup_vs_plain_fp64"] = res["plain_fp64"]["ms_per_step"] / res["fp32_broad"]["ms_per_step"]
     assert res["plain_fp64"]["toi"] == res["fp32_broad"]["toi"]
+    if per_pair:
+        # a small scene is launch-bound: the same step replayed as a captured CUDA graph
+        import torch
+        c = ccd.CCD(0, use_graph=1)
+        out = torch.empty(1, dtype=torch.float64, device=d[0].device)
+        c.step(*d, min_sep=min_sep)
+        for _ in range(3):
+            ccd.ccd_step(c.ctx, *d, 1e-6, min_sep, 10 ** 6, out)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = _events()
+            a.record()
+            ccd.ccd_step(c.ctx, *d, 1e-6, min_sep, 10 ** 6, out)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        assert c.status()[0] == 0 and float(out.item()) == res["fp32_broad"]["toi"]
+        c.close()
+        res["fp32_broad"]["graph_ms_per_step"] = float(np.median(ms))
     return res
 
 
@@ -675,12 +695,14 @@ def form_batch(envs, steps, warmup):
             "batch512_ms": rep}
 
 
-def form_serve(envs, rate, n_slots=2, verify=32):
+def form_serve(envs, rate, n_slots=2, verify=32, clients=4):
     """Serving form: the environments arrive as a Poisson stream; at its
-    arrival time a client writes the scene into the server's arena and
-    submits it.  Latency runs from the arrival (before the write) to the
-    completion; a sample of results is compared with the scene stepped
-    alone."""
+    arrival time a client writes the scene into the server's arena (four
+    copies of arrays it holds in the arena's layout: V0, V1 as [3][nV], E, F)
+    and submits it (`clients` client threads take the arrivals in turn).
+    Latency runs from the arrival (before the write) to the completion; a
+    sample of results is compared with the scene stepped alone."""
+    import threading
     from paper_2112_06300_gb300 import ccd
     srv = ccd.Server(0, n_slots=n_slots, max_scenes=256, memory_cap=BUDGET, arena_bytes=4 << 30,
                      pairs_per_box=PAIRS_PER_BOX, autotune=1)
@@ -688,21 +710,50 @@ def form_serve(envs, rate, n_slots=2, verify=32):
         srv.wait(srv.submit_scene(e.V0, e.V1, e.E, e.F))
     rng = np.random.default_rng(3)
     arrive = np.cumsum(rng.exponential(1.0 / rate, len(envs)))
-    tickets, write_ms = [], np.empty(len(envs))
-    t0 = time.perf_counter()
-    for k, e in enumerate(envs):
-        while time.perf_counter() - t0 < arrive[k]:
-            pass
-        tw = time.perf_counter()
-        tickets.append(srv.submit_scene(e.V0, e.V1, e.E, e.F))
-        write_ms[k] = (time.perf_counter() - tw) * 1e3
+    # the clients' scenes in the arena's layout (structure of arrays)
+    soa = [(np.ascontiguousarray(e.V0.T), np.ascontiguousarray(e.V1.T), np.ascontiguousarray(e.E, np.int32),
+            np.ascontiguousarray(e.F, np.int32)) for e in envs]
+    tickets = [None] * len(envs)
+    late_ms = np.zeros(len(envs))                  # arrival -> the client starts writing
+    write_ms = np.zeros(len(envs))                 # writing and queueing the scene
+    t0 = time.perf_counter() + 0.05
+
+    def client(ks):
+        for k in ks:
+            e = envs[k]
+            while True:
+                dt = t0 + arrive[k] - time.perf_counter()
+                if dt <= 0:
+                    break
+                if dt > 2e-4:
+                    time.sleep(dt - 1e-4)
+            tw = time.perf_counter()
+            t, a, b, ee, ff = srv.request(len(e.V0), len(e.E), len(e.F))
+            sa, sb, se, sf = soa[k]
+            if len(e.V0):
+                np.copyto(a, sa)
+                np.copyto(b, sb)
+            if len(e.E):
+                np.copyto(ee, se)
+            if len(e.F):
+                np.copyto(ff, sf)
+            srv.submit(t)
+            tickets[k] = t
+            write_ms[k] = (time.perf_counter() - tw) * 1e3
+            late_ms[k] = (tw - (t0 + arrive[k])) * 1e3
+
+    th = [threading.Thread(target=client, args=(range(i, len(envs), clients),)) for i in range(clients)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
     t_sub = time.perf_counter() - t0
     res = [srv.wait(t) for t in tickets]
     t_all = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
     lat_srv = np.array([r[1] for r in res])       # submission -> completion
-    lat = lat_srv + write_ms                       # arrival -> completion
+    lat = lat_srv + write_ms + late_ms             # arrival -> completion
     toi = np.array([r[0] for r in res])
     c = ccd.CCD(0)
     pick = np.random.default_rng(4).choice(len(envs), size=min(verify, len(envs)), replace=False)
@@ -710,12 +761,14 @@ def form_serve(envs, rate, n_slots=2, verify=32):
         e = envs[k]
         assert c.step(*ccd.mesh_to_device(e.V0, e.V1, e.E, e.F, "cuda:0")) == toi[k], k
     c.close()
-    return {"workload": f"{len(envs)} rigid environments arriving as a Poisson stream at {rate:g}/s, {n_slots} slots "
-                        f"autotuned on their first batch, <= 256 scenes per batch, 64 GiB cap",
+    return {"workload": f"{len(envs)} rigid environments arriving as a Poisson stream at {rate:g}/s, {clients} client "
+                        f"threads writing and submitting each scene at its arrival, {n_slots} slots autotuned on "
+                        f"their first batch, <= 256 scenes per batch, 64 GiB cap",
             "steps_per_s": len(envs) / t_all, "offered_rate": len(envs) / t_sub, "target_rate": rate,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean()), "max": float(lat.max()),
                            "client_write_p50": float(np.percentile(write_ms, 50)),
+                           "client_start_delay_p99": float(np.percentile(late_ms, 99)),
                            "server_p50": float(np.percentile(lat_srv, 50)),
                            "server_p99": float(np.percentile(lat_srv, 99))},
             "batches": st["n_batches"], "max_batch_scenes": st["max_batch_scenes"],

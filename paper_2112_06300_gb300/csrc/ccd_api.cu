@@ -200,7 +200,8 @@ int ensure_narrow(ccd_ctx *c, int64_t nq, cudaStream_t s) {
     // ring positions start at 0: cell i expects sequence number i
     k_ring_init<<<(unsigned)std::min<unsigned long long>(cdiv(cap, 256), 4096), 256, 0, s>>>(c->ring, cap, 0);
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(&c->ctl->q_head, 0, 2 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(&c->ctl->q_head, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(&c->ctl->q_tail, 0, sizeof(unsigned long long), s));
   }
   if (nq <= c->cap_q) return CCD_OK;
   if (c->qflags) CK(cudaFree(c->qflags));

@@ -20,8 +20,11 @@ struct DevCtl {
   // 128-byte lines, so that atomics on one do not queue behind traffic on
   // another
   alignas(128) unsigned long long q_next;   // next query to hand out
-  alignas(128) unsigned long long q_head;   // ring positions (monotonic, never reset;
-  unsigned long long q_tail;                // adjacent: cleared together)
+  // ring positions (monotonic; reset only with the ring itself): the head,
+  // moved by idle warps taking work, and the tail, moved by warps handing
+  // work out, on lines of their own
+  alignas(128) unsigned long long q_head;
+  alignas(128) unsigned long long q_tail;
   alignas(128) unsigned long long pending;  // units fetched or queued and not finished
   alignas(128) unsigned long long toi_bits; // earliest t* so far, bits of a non-negative double
   alignas(128) unsigned long long n_intervals;
