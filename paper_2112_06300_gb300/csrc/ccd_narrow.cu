@@ -940,6 +940,7 @@ constexpr int kIdleRounds = 1 << 14;   // idle warp rounds before a warp retires
 // slow the busy warps of the tail (measured: 0.25-2 us worse, 1-32 us best)
 constexpr unsigned kNapMin = 1000, kNapMax = 32000;
 constexpr int kRefresh = 8;            // iterations between reads of the shared values
+constexpr int kDonateMin = 4;          // idle lanes a warp gathers before a round of donation
 // A query whose work is split over several units (donation, hand-off) shares
 // one iteration budget: each unit counts its evaluations in windows of at
 // most kBudgetWindow and adds them to the query's counter at the end of each
@@ -1182,7 +1183,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       // own warp; the query data moves by shuffles, the donor keeps the rest
       // of its subtree (its root moves down to the donated sibling's depth).
       const unsigned idle = __ballot_sync(FULL, !have);
-      if (idle && exhausted) {
+      if (exhausted && __popc(idle) >= kDonateMin) {
         // candidate donors: the first busy lanes, one per idle lane; only they
         // walk their path to find the shallowest pending sibling
         const unsigned busy = __ballot_sync(FULL, have && !fresh);
