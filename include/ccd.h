@@ -164,6 +164,25 @@ int ccd_broad(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV,
               int32_t *ee_out, int64_t ee_cap, int64_t *n_ee, void *stream);
 
 /*
+ * One shard of the broad phase: the decomposition of the sweep over several
+ * GPUs (the paper's multi-GPU broad phase, Section "Conclusion and Future
+ * Work"), callable on one.  Every shard builds and sorts all boxes (the same
+ * small work on each), then sweeps from its own contiguous part
+ * [n s / n_shards, n (s + 1) / n_shards) of the n sorted cell copies,
+ * reading past the part's end; each pair is reported from exactly one copy,
+ * so the shards' pair sets are disjoint and their union is ccd_broad's set.
+ * The earliest time of the whole step is the minimum over the shards of the
+ * narrow phase (mode 1) on each shard's pairs: the only exchange a multi-GPU
+ * step needs is that one minimum.  Arguments and outputs as in ccd_broad,
+ * plus 0 <= shard < n_shards.  Cell sweep only (sweep_kernel 0); synchronous.
+ */
+int ccd_broad_shard(ccd_ctx *ctx, const double *V0, const double *V1, int64_t nV,
+                    const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
+                    int32_t shard, int32_t n_shards,
+                    int32_t *vf_out, int64_t vf_cap, int64_t *n_vf,
+                    int32_t *ee_out, int64_t ee_cap, int64_t *n_ee, void *stream);
+
+/*
  * Narrow phase (Section "Narrow-Phase", Algorithm 3): conservative interval
  * bisection over (t, u, v) with an FP64 inclusion function and error box, for
  * the given pairs.  mode 0: each pair gets its own time of impact (toi_vf,
@@ -415,6 +434,13 @@ int ccd_server_request(ccd_server *srv, int64_t nV, int64_t nE, int64_t nF, doub
 
 /* Queue a written scene (thread-safe). */
 int ccd_server_submit(ccd_server *srv, uint64_t ticket);
+
+/* ccd_server_request, a copy of the scene from the caller's host arrays
+ * (V0, V1 as [3][nV], E [nE][2], F [nF][3], local vertex ids) into the arena,
+ * and ccd_server_submit, in one call (thread-safe; blocks while the arena is
+ * full).  *ticket receives the scene's ticket for ccd_server_wait. */
+int ccd_server_submit_scene(ccd_server *srv, int64_t nV, int64_t nE, int64_t nF, const double *V0,
+                            const double *V1, const int32_t *E, const int32_t *F, uint64_t *ticket);
 
 /* Wait up to timeout_ms (< 0: forever) for a submitted scene; on completion
  * writes its earliest time and latency (ms from submission to completion),

@@ -106,6 +106,8 @@ def lib():
     L.ccd_destroy.argtypes = [P]
     L.ccd_broad.argtypes = [P, P, P, i64, P, i64, P, i64, P, i64, ctypes.POINTER(i64), P, i64,
                             ctypes.POINTER(i64), P]
+    L.ccd_broad_shard.argtypes = [P, P, P, i64, P, i64, P, i64, i32, i32, P, i64, ctypes.POINTER(i64), P, i64,
+                                  ctypes.POINTER(i64), P]
     L.ccd_narrow.argtypes = [P, P, i64, P, i64, P, P, i64, P, i64, P, i64, d, d, i64, i32,
                              P, P, P, P, P, P]
     L.ccd_step.argtypes = [P, P, P, i64, P, i64, P, i64, d, d, i64, P, P]
@@ -142,6 +144,9 @@ def lib():
     L.ccd_server_request.restype = ctypes.c_int
     L.ccd_server_submit.argtypes = [P, ctypes.c_uint64]
     L.ccd_server_submit.restype = ctypes.c_int
+    L.ccd_server_submit_scene.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P, P, P,
+                                          ctypes.POINTER(ctypes.c_uint64)]
+    L.ccd_server_submit_scene.restype = ctypes.c_int
     L.ccd_server_wait.argtypes = [P, ctypes.c_uint64, d, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]
     L.ccd_server_wait.restype = ctypes.c_int
@@ -207,6 +212,19 @@ def ccd_broad(ctx, V0, V1, E, F, vf_out, ee_out, stream=None, check=True) -> Tup
                          _ptr(ee_out), ee_out.shape[0], ctypes.byref(nee), _stream(stream))
     if check and rc not in (CCD_OK, CCD_ETRUNC):
         raise CCDError(rc, "ccd_broad")
+    return rc, nvf.value, nee.value
+
+
+def ccd_broad_shard(ctx, V0, V1, E, F, shard, n_shards, vf_out, ee_out, stream=None, check=True) -> Tuple[int, int, int]:
+    """One shard of the broad phase into caller buffers; returns (status,
+    n_vf, n_ee) totals of the shard."""
+    nV, nE, nF = _mesh(V0, V1, E, F)
+    nvf, nee = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().ccd_broad_shard(ctx, _ptr(V0), _ptr(V1), nV, _ptr(E), nE, _ptr(F), nF, int(shard), int(n_shards),
+                               _ptr(vf_out), vf_out.shape[0], ctypes.byref(nvf),
+                               _ptr(ee_out), ee_out.shape[0], ctypes.byref(nee), _stream(stream))
+    if check and rc not in (CCD_OK, CCD_ETRUNC):
+        raise CCDError(rc, "ccd_broad_shard")
     return rc, nvf.value, nee.value
 
 
@@ -364,6 +382,21 @@ class CCD:
             cap = max(nvf, nee) + 1
         raise CCDError(CCD_ETRUNC, "CCD.broad")
 
+    def broad_shard(self, V0, V1, E, F, shard, n_shards, stream=None):
+        """Pairs of one shard of the broad phase (ccd_broad_shard) as int32
+        CUDA tensors (vf, ee)."""
+        import torch
+        dev = V0.device
+        cap = max(1024, 4 * (V0.shape[1] + E.shape[0] + F.shape[0]))
+        for _ in range(2):
+            vf = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+            ee = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+            rc, nvf, nee = ccd_broad_shard(self.ctx, V0, V1, E, F, shard, n_shards, vf, ee, stream)
+            if rc == CCD_OK:
+                return vf[:nvf], ee[:nee]
+            cap = max(nvf, nee) + 1
+        raise CCDError(CCD_ETRUNC, "CCD.broad_shard")
+
     def narrow(self, vf, ee, V0, V1, E, F, delta=None, min_sep=None, max_iter=None, mode=0, stream=None):
         import torch
         dev = V0.device
@@ -471,6 +504,17 @@ class Server:
             f[...] = F
         _check(lib().ccd_server_submit(self.handle, t), "ccd_server_submit")
         return t
+
+    def submit_soa(self, V0T, V1T, E, F) -> int:
+        """Queue one scene given in the arena's layout (V0T, V1T float64 (3, nV)
+        C-contiguous, E int32 (nE, 2), F int32 (nF, 3)): the library copies it
+        into the arena and submits it in one call; returns the ticket."""
+        t = ctypes.c_uint64()
+        nV, nE, nF = V0T.shape[1], E.shape[0], F.shape[0]
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a.size else None
+        _check(lib().ccd_server_submit_scene(self.handle, nV, nE, nF, p(V0T), p(V1T), p(E), p(F), ctypes.byref(t)),
+               "ccd_server_submit_scene")
+        return t.value
 
     def submit(self, ticket: int) -> None:
         _check(lib().ccd_server_submit(self.handle, ticket), "ccd_server_submit")

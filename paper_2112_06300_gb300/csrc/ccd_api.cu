@@ -774,6 +774,50 @@ int ccd_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const 
   return ((int64_t)h[0] > vf_cap || (int64_t)h[1] > ee_cap) ? CCD_ETRUNC : CCD_OK;
 }
 
+int ccd_broad_shard(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+                    const int32_t *F, int64_t nF, int32_t shard, int32_t n_shards, int32_t *vf_out, int64_t vf_cap,
+                    int64_t *n_vf, int32_t *ee_out, int64_t ee_cap, int64_t *n_ee, void *stream) {
+  if (!c || !n_vf || !n_ee || vf_cap < 0 || ee_cap < 0 || n_shards < 1 || shard < 0 || shard >= n_shards)
+    return CCD_EINVAL;
+  if (c->opts.sweep_kernel != 0) return CCD_EINVAL;   // sweep ranges exist in the cell sweep only
+  if (!mesh_args_ok(V0, V1, nV, E, nE, F, nF)) return CCD_EINVAL;
+  if ((vf_cap > 0 && !vf_out) || (ee_cap > 0 && !ee_out)) return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  clear_marks(c);
+  k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+  c->n_launches += 1;
+  // boxes, cell copies and sort (every shard does the same, small work) ...
+  int rc = launch_broad(c, V0, V1, nV, E, nE, F, nF, vf_out, vf_cap, ee_out, ee_cap, s,
+                        SceneSpec{0, nullptr, nullptr, nullptr}, false, 1);
+  if (rc) return rc;
+  unsigned long long ncopy = 0;
+  CK(cudaMemcpyAsync(&ncopy, &c->ctl->n_copies, sizeof(ncopy), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // ... then the sweep from this shard's contiguous part of the sorted
+  // copies (it reads past the part's end; every pair is reported from one
+  // copy, so the shards' pair sets are disjoint and cover the whole set)
+  const int64_t b = (int64_t)(ncopy * (unsigned long long)shard / (unsigned long long)n_shards);
+  const int64_t e = (int64_t)(ncopy * (unsigned long long)(shard + 1) / (unsigned long long)n_shards);
+  rc = launch_broad(c, V0, V1, nV, E, nE, F, nF, vf_out, vf_cap, ee_out, ee_cap, s,
+                    SceneSpec{0, nullptr, nullptr, nullptr}, false, 2, b, e);
+  if (rc) return rc;
+  unsigned long long h[3];
+  int ovf = 0;
+  CK(cudaMemcpyAsync(h, &c->ctl->n_vf, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&ovf, &c->ctl->sup_overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *n_vf = (int64_t)h[0];
+  *n_ee = (int64_t)h[1];
+  if (ovf) {
+    *n_vf = std::max<int64_t>(*n_vf, (int64_t)h[2]);
+    *n_ee = std::max<int64_t>(*n_ee, (int64_t)h[2]);
+    return CCD_ETRUNC;
+  }
+  return ((int64_t)h[0] > vf_cap || (int64_t)h[1] > ee_cap) ? CCD_ETRUNC : CCD_OK;
+}
+
 int ccd_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee, const double *V0,
                const double *V1, int64_t nV, const int32_t *E, int64_t nE, const int32_t *F, int64_t nF,
                double delta, double min_sep, int64_t max_iter, int32_t mode, double *toi_vf, double *toi_ee,
