@@ -534,6 +534,27 @@ int ccd_server_submit(ccd_server *S, uint64_t ticket) {
   return CCD_OK;
 }
 
+int ccd_server_submit_scene(ccd_server *S, int64_t nV, int64_t nE, int64_t nF, const double *V0, const double *V1,
+                            const int32_t *E, const int32_t *F, uint64_t *ticket) {
+  if (!S || !ticket || (nV > 0 && (!V0 || !V1)) || (nE > 0 && !E) || (nF > 0 && !F)) return CCD_EINVAL;
+  double *a = nullptr, *b = nullptr;
+  int32_t *e = nullptr, *f = nullptr;
+  uint64_t t = 0;
+  int rc = ccd_server_request(S, nV, nE, nF, &a, &b, &e, &f, &t);
+  if (rc) return rc;
+  if (nV > 0) {
+    std::memcpy(a, V0, 3 * nV * sizeof(double));
+    std::memcpy(b, V1, 3 * nV * sizeof(double));
+  }
+  if (nE > 0) std::memcpy(e, E, 2 * nE * sizeof(int32_t));
+  if (nF > 0) std::memcpy(f, F, 3 * nF * sizeof(int32_t));
+  rc = ccd_server_submit(S, t);
+  if (rc) return rc;
+  *ticket = t;
+  return CCD_OK;
+}
+
+
 int ccd_server_wait(ccd_server *S, uint64_t ticket, double timeout_ms, double *toi, double *latency_ms) {
   if (!S || !toi) return CCD_EINVAL;
   std::unique_lock<std::mutex> lk(S->mu);

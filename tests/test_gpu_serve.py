@@ -157,3 +157,29 @@ def test_memory_cap_binds(ccd):
     assert st["n_batches"] >= 4, st
     assert st["max_batch_bytes"] <= share and st["max_inflight_bytes"] <= cap, st
     assert used <= 1.15 * cap + (64 << 20), (used, cap)
+
+
+def test_submit_scene_copies_from_caller_arrays(ccd):
+    """ccd_server_submit_scene (copy into the arena and queue in one call),
+    from two client threads: every result equals the oracle's."""
+    envs = [scenes.rigid_environment(s, 500, 3000, vmax=0.2) for s in range(60, 72)]
+    ref = {k: O.step(e.V0, e.V1, e.E, e.F) for k, e in enumerate(envs)}
+    soa = [(np.ascontiguousarray(e.V0.T), np.ascontiguousarray(e.V1.T), np.ascontiguousarray(e.E, np.int32),
+            np.ascontiguousarray(e.F, np.int32)) for e in envs]
+    srv = ccd.Server(0, n_slots=2, max_scenes=3, arena_bytes=32 << 20, memory_cap=8 << 30)
+    out = {}
+
+    def client(ks):
+        tick = [(k, srv.submit_soa(*soa[k])) for k in ks]
+        for k, t in tick:
+            out[k] = srv.wait(t)[0]
+
+    try:
+        th = [threading.Thread(target=client, args=(range(i, len(envs), 2),)) for i in range(2)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+    finally:
+        srv.close()
+    assert out == ref
