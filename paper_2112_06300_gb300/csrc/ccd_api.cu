@@ -40,6 +40,9 @@ struct ccd_ctx {
   int *qsid = nullptr;                         // scene of each query (batched scenes)
   double *prims = nullptr;                     // per-primitive set-up records of the narrow phase
   int64_t cap_prims = 0;                       // (words)
+  // side stream of ccd_step: the per-primitive set-up runs beside the broad phase
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // batched scenes
   int64_t cap_bsid = 0, cap_scenes = 0;
   int *bsid = nullptr, *saxis = nullptr;
@@ -522,13 +525,37 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   return CCD_OK;
 }
 
+// The per-primitive set-up alone (needs only the mesh), e.g. on a side stream
+// beside the broad phase.
+int launch_prims(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const int32_t *E, int64_t nE,
+                 const int32_t *F, int64_t nF, cudaStream_t s) {
+  const int64_t nP = nV + nE + nF;
+  if (nP == 0) return CCD_OK;
+  if (narrow_prim_words(nV, nE, nF) > c->cap_prims) return CCD_EINVAL;   // sized before
+  NarrowArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.ctl = c->ctl;
+  A.V0 = V0;
+  A.V1 = V1;
+  A.nV = nV;
+  A.nE = nE;
+  A.nF = nF;
+  A.E = E;
+  A.F = F;
+  A.prims = c->prims;
+  k_prepare_prims<<<(unsigned)std::min<int64_t>(cdiv(nP, 256), (int64_t)c->sm_count * 16), 256, 0, s>>>(A);
+  c->n_launches += 1;
+  CK(cudaGetLastError());
+  return CCD_OK;
+}
+
 int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee, int64_t n_ee,
                   int counts_from_ctl, const double *V0, const double *V1, int64_t nV, const int32_t *E,
                   int64_t nE, const int32_t *F, int64_t nF, double delta, double min_sep, int64_t max_iter, int mode,
                   unsigned long long *toi_vf_bits, unsigned long long *toi_ee_bits, cudaStream_t s,
                   bool zero_rule_pass = false, int n_scenes = 0, const int64_t *voff = nullptr,
                   unsigned long long *toi_scene = nullptr, int64_t ee_end = 0, bool keep_toi = false,
-                  unsigned long long phantom_units = 0) {
+                  unsigned long long phantom_units = 0, bool prims_done = false) {
   const int64_t nq = counts_from_ctl && ee_end > 0 ? ee_end : n_vf + n_ee;
   int rc = ensure_narrow(c, nq, s);
   if (rc) return rc;
@@ -582,7 +609,7 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
   // per-primitive set-up (independent of min_sep: the zero-TOI pass reuses
   // it), then the query records in one dense pass (the zero-TOI pass has
   // min_sep = 0: redo them)
-  const bool prims = !zero_rule_pass && nP > 0;
+  const bool prims = !zero_rule_pass && !prims_done && nP > 0;
   if (prims)
     k_prepare_prims<<<(unsigned)std::min<int64_t>(cdiv(nP, 256), (int64_t)c->sm_count * 16), 256, 0, s>>>(A);
   k_prepare_queries<<<(unsigned)std::min<int64_t>(cdiv(std::max<int64_t>(nq, 1), 256), (int64_t)c->sm_count * 16),
@@ -727,6 +754,9 @@ int ccd_destroy(ccd_ctx *c) {
   cudaFree(c->qrec);
   cudaFree(c->qsid);
   cudaFree(c->prims);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   cudaFree(c->bsid);
   cudaFree(c->ssum);
   cudaFree(c->saxis);
@@ -943,13 +973,22 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
   auto enqueue = [&](cudaStream_t st) -> int {
     clear_marks(c);
     k_reset_status<<<1, 1, 0, st>>>(c->ctl);
-    int r = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, st,
-                         SceneSpec{0, nullptr, nullptr, nullptr}, true);
+    // the per-primitive set-up of the narrow phase needs only the mesh: it
+    // runs on a side stream beside the broad phase and joins before the
+    // query records are built
+    CK(cudaEventRecord(c->ev_fork, st));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    int r = launch_prims(c, V0, V1, nV, E, nE, F, nF, c->side);
+    if (r) return r;
+    CK(cudaEventRecord(c->ev_join, c->side));
+    r = launch_broad(c, V0, V1, nV, E, nE, F, nF, c->vf, c->pair_cap, c->ee, c->pair_cap, st,
+                     SceneSpec{0, nullptr, nullptr, nullptr}, true);
     if (r) return r;
     k_counts_from_broad<<<1, 1, 0, st>>>(c->ctl, c->pair_cap);
     c->n_launches += 2;
+    CK(cudaStreamWaitEvent(st, c->ev_join, 0));
     r = launch_narrow(c, c->vf, c->pair_cap, c->ee, c->pair_cap, 1, V0, V1, nV, E, nE, F, nF, delta, min_sep, max_iter, 1,
-                      nullptr, nullptr, st, false, 0, nullptr, nullptr, c->pair_cap);
+                      nullptr, nullptr, st, false, 0, nullptr, nullptr, c->pair_cap, false, 0, true);
     if (r) return r;
     if (c->opts.no_zero_toi) {
       // second pass only when the first found t* = 0 (decided on the device)
@@ -969,6 +1008,11 @@ int ccd_step(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, const i
     if (rc) return rc;
     rc = ensure_prims(c, nV, nE, nF);
     if (rc) return rc;
+    if (!c->side) {
+      CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
     rc = ensure_broad(c, nV + nE + nF);
     if (rc) return rc;
     if (c->opts.broad_fp64 && c->opts.sweep_kernel == 0) {
