@@ -1022,6 +1022,10 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   // first, so that no iteration waits for an L2 round trip; stale values
   // only prune less or hand work out later.
   unsigned long long pf_toi = kInfBits, pf_qnext = 0;          // lane 0: values in use
+  unsigned long long g_toi = kInfBits;                          // all lanes: pf_toi at the last refresh
+  bool g_tail = false;                                          // all lanes: every query taken (last refresh)
+  unsigned long long cut_prev = ~0ull;                          // cut53 = ceil53(cut_prev)
+  uint64_t cut53 = 0;
   unsigned long long nx_toi = kInfBits, nx_qnext = 0;          // lane 0: loads in flight
   unsigned long long pf_occ = 0, nx_head = 0, nx_tail = 0;     // lane 0: ring occupancy
   unsigned long long nx_scene = kInfBits;                      // per lane
@@ -1075,7 +1079,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     // (intervals are exported only once every query has been handed out,
     // so a warp looks at the ring only after its own claim came back empty)
     if (__any_sync(FULL, !have)) {
-      const unsigned long long pf_toi_b = __shfl_sync(FULL, pf_toi, 0);
+      const unsigned long long pf_toi_b = g_toi;
       const unsigned m = __ballot_sync(FULL, !have);
       if (m && !exhausted && staged) {
         if (s_pos == s_n) {
@@ -1369,17 +1373,23 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         pf_scene = nx_scene;
         if (have) nx_scene = ld_relaxed_u64(&A.toi_scene[sid]);
       }
+      // broadcast once per refresh, not per iteration
+      g_toi = __shfl_sync(FULL, pf_toi, 0);
+      g_tail = __shfl_sync(FULL, pf_qnext, 0) >= (unsigned long long)nq;
     }
     unsigned long long cut = tq;
-    const unsigned long long g = __shfl_sync(FULL, pf_toi, 0);
+    const unsigned long long g = g_toi;
     // hand work out only once every query has been taken (idle lanes exist)
-    const bool tail_phase = __shfl_sync(FULL, pf_qnext, 0) >= (unsigned long long)nq;
+    const bool tail_phase = g_tail;
     if (A.mode == 1) cut = g < cut ? g : cut;
     if (A.mode == 2) cut = pf_scene < cut ? pf_scene : cut;
     bool node_done = true;     // false when the node was split (go to its left child)
     bool unit_end = false;
     bool evaluate = false;
-    const uint64_t cut53 = ceil53(cut);
+    if (cut != cut_prev) {     // (t* changes rarely)
+      cut_prev = cut;
+      cut53 = ceil53(cut);
+    }
     if (have) {
       if (s53(N.n0, N.l0) >= cut53) {
         // pruned: starts at or after the current t*
@@ -1613,7 +1623,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       const bool trig = wsince >= 32ll * A.budget;   // (tail phase only)
       if (trig) wsince = 0;
       const bool want_exp = trig && have && !unit_end;
-      if (__any_sync(FULL, want_exp)) {
+      if (trig && __any_sync(FULL, want_exp)) {   // (trig is the same in every lane)
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
         if (want_exp) {
