@@ -332,13 +332,15 @@ int ccd_status_async(ccd_ctx *ctx, int32_t *status, void *stream);
 int ccd_get_status(ccd_ctx *ctx, ccd_stats *stats);
 
 /* Stages timed when opts.profile_stages is set. */
-enum { CCD_STAGE_BOXES = 0, CCD_STAGE_SORT = 1, CCD_STAGE_SWEEP = 2, CCD_STAGE_NARROW = 3, CCD_NSTAGES = 4 };
+enum { CCD_STAGE_BOXES = 0, CCD_STAGE_SORT = 1, CCD_STAGE_SWEEP = 2, CCD_STAGE_NARROW = 3,
+       CCD_STAGE_NARROW_KERNEL = 4, CCD_NSTAGES = 5 };
 
 /* Milliseconds spent in each stage by the last ccd_broad / ccd_narrow /
  * ccd_step call (CUDA events on its stream; boxes = box build and axis
  * choice, sort = keys (cell sweep: copies per cell), radix sort and
- * gather, sweep = sweep with the exact
- * filter, narrow = narrow-phase kernel); stages the call did not run read 0.
+ * gather, sweep = sweep with the exact filter, narrow = query records and
+ * the narrow-phase kernel, narrow_kernel = the narrow-phase kernel alone,
+ * inside the narrow stage); stages the call did not run read 0.
  * Synchronizes the stream.  Returns CCD_EINVAL unless profile_stages was set. */
 int ccd_stage_times(ccd_ctx *ctx, double ms[CCD_NSTAGES]);
 

@@ -305,11 +305,11 @@ def ccd_selftest_unfinished_work(ctx, stream=None) -> int:
     return st.value
 
 
-STAGES = ("boxes", "sort", "sweep", "narrow")
+STAGES = ("boxes", "sort", "sweep", "narrow", "narrow_kernel")
 
 
 def ccd_stage_times(ctx) -> dict:
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * len(STAGES))()
     _check(lib().ccd_stage_times(ctx, ms), "ccd_stage_times")
     return dict(zip(STAGES, list(ms)))
 

@@ -614,7 +614,9 @@ int launch_narrow(ccd_ctx *c, const int32_t *vf, int64_t n_vf, const int32_t *ee
     k_prepare_prims<<<(unsigned)std::min<int64_t>(cdiv(nP, 256), (int64_t)c->sm_count * 16), 256, 0, s>>>(A);
   k_prepare_queries<<<(unsigned)std::min<int64_t>(cdiv(std::max<int64_t>(nq, 1), 256), (int64_t)c->sm_count * 16),
                       256, 0, s>>>(A);
+  if (!zero_rule_pass) mark(c, CCD_STAGE_NARROW_KERNEL, true, s);
   k_narrow<<<c->narrow_blocks, kNarrowThreads, kNarrowDynSmem, s>>>(A);
+  if (!zero_rule_pass) mark(c, CCD_STAGE_NARROW_KERNEL, false, s);
   if (zero_rule_pass) k_nozero_finish<<<1, 1, 0, s>>>(c->ctl);
   mark(c, CCD_STAGE_NARROW, false, s);
   // reset/prepare, primitives, records, narrow, finish
