@@ -55,18 +55,28 @@ METRIC = "CCD queries/s and ms/step (broad+narrow) vs plain FP64 GPU form; % HBM
 UNIT = "queries/s"
 HBM_FALLBACK_GBS = 6800.0
 
-# Per-launch DRAM traffic from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by kernel with the hash of the source file it
-# was taken on; ignored once the source changes.
 # Issue counters of k_narrow from one ncu capture on the 256 x 256 cloth
 # (smsp__inst_executed.sum / intervals evaluated, smsp__thread_inst_executed.sum
 # / smsp__inst_executed.sum, sm__warps_active), keyed by the source hash.
-NCU_ISSUE = {}
+NCU_ISSUE = {
+    # ncu --replay-mode application --clock-control none --metrics smsp__inst_executed.sum,
+    #     smsp__thread_inst_executed.sum,sm__warps_active... -k regex:"^k_narrow$|..." -s 24 -c 6
+    #     python bench.py --n 256 --steps 1 --warmup 3 --no-cpu-baseline --no-forms --no-autotune
+    #     (789.4M warp instructions over 18,578,774 intervals)
+    "k_narrow": {"warp_inst_per_interval": 42.49, "threads_per_inst": 18.67, "warps_active": 0.1859,
+                 "src": "09bafc2baa5205b7",
+                 "cmd": "ncu --replay-mode application, 256 x 256 cloth, bench.py --no-autotune"},
+}
 
+# Per-launch DRAM traffic from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by kernel with the hash of the source file it
+# was taken on; ignored once the source changes.
 NCU_TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_narrow -s 1 -c 1
-    #     python bench.py --steps 2 --warmup 3 --no-cpu-baseline   (1.61 GB read + 59.26 MB written)
-    "k_narrow": (1.610e9 + 59.26e6, "c2e68d772b701aea"),
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+    #     -k regex:"^k_narrow$|..." -s 28 -c 7
+    #     python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-forms --no-autotune
+    #     (1.605 GB read + 57.05 MB written)
+    "k_narrow": (1.605e9 + 57.05e6, "09bafc2baa5205b7"),
 }
 
 
@@ -79,6 +89,7 @@ def parse():
     p.add_argument("--n", type=int, default=512, help="cloth grid size")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the other configurations and forms")
+    p.add_argument("--no-autotune", action="store_true", help="time the cloth step with the default settings")
     p.add_argument("--workload", choices=["cloth", "batch", "serve", "precision"], default="cloth")
     p.add_argument("--envs", type=int, default=4096, help="batch/serve: environments")
     p.add_argument("--rate", type=float, default=2e4, help="serve: arrivals per second")
@@ -232,7 +243,7 @@ def run_ours(args):
     t_ref = c.step(V0, V1, E, F)                    # sizes the pair buffers (synchronous)
     # the library's own autotuner picks the cell width, hand-off budget and
     # interval-queue size for this mesh (outside the timed region, once)
-    tuning = c.autotune(V0, V1, E, F, reps=3)
+    tuning = c.autotune(V0, V1, E, F, reps=3) if not args.no_autotune else None
     for _ in range(args.warmup):
         ccd.ccd_step(c.ctx, V0, V1, E, F, 1e-6, 0.0, 10 ** 6, out)
     torch.cuda.synchronize()
@@ -375,8 +386,10 @@ def run_ours(args):
                    "superset_fp32": st["n_superset"], "intervals_per_step": stats[-1]["n_intervals"],
                    "toi": t_ref, "l2": "flushed (256 MiB write) before every timed step",
                    "precision": "broad FP32 outward-rounded + exact FP64 filter; narrow FP64",
-                   "autotuned": {k: tuning[k] for k in ("strip_width", "export_budget", "queue_capacity")},
-                   "autotune_ms": {"before": tuning["default_ms"], "after": tuning["broad_ms"] + tuning["narrow_ms"]},
+                   "autotuned": ({k: tuning[k] for k in ("strip_width", "export_budget", "queue_capacity")}
+                                 if tuning else "no (defaults)"),
+                   "autotune_ms": ({"before": tuning["default_ms"], "after": tuning["broad_ms"] + tuning["narrow_ms"]}
+                                   if tuning else None),
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": agg["e2e_value"], "unit": UNIT, "ms_per_step": e2e_mean,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
