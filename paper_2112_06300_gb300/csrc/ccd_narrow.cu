@@ -993,8 +993,11 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   float c0f[3][3], dcf[3][3], tn[3], tm[3], wn[3];
   unsigned long long K[3] = {0, 0, 0};
   bool vf = false;
-  int sid = 0;                               // scene of the lane's query (mode 2)
-  unsigned long long pf_scene = kInfBits;    // its t*, loaded one iteration ahead
+  __shared__ int SID[kNarrowThreads];        // mode 2: scene of the lane's query
+  // mode 2: the t* of the lane's scene in use (row 0) and loaded one refresh
+  // ahead (row 1)
+  __shared__ unsigned long long SCN[2][kNarrowThreads];
+  SCN[0][tid] = SCN[1][tid] = kInfBits;
   bool have = false, fresh = false, whole = false;
   bool exhausted = false;                    // warp-uniform
   int64_t q = 0;
@@ -1012,57 +1015,75 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
   long long cnt = 0, cap_left = 0;
   unsigned flags = 0;
-  unsigned n_eval = 0, n_exp = 0, n_cap = 0, n_don = 0, n_eval_tail = 0, n_eval64 = 0;   // per lane, per launch
-  int idle_rounds = 0;
-  long long wsince = 0;   // warp-uniform: evaluations of the warp in the tail since its last hand-off
+  unsigned n_eval = 0, n_eval64 = 0;          // per lane, per launch
+  int idle_rounds = 0;                       // warp-uniform: idle rounds in a row
   unsigned ended_acc = 0;                    // warp-uniform: ended units not yet subtracted from pending
-  unsigned nap = kNapMin;                    // warp-uniform: idle back-off (ns)
   // Shared values (global t*, next query, the scene's t*) are read from L2
-  // every kRefresh iterations into a second register and used from the
-  // first, so that no iteration waits for an L2 round trip; stale values
-  // only prune less or hand work out later.
-  unsigned long long pf_toi = kInfBits, pf_qnext = 0;          // lane 0: values in use
+  // every kRefresh iterations into a second slot and used from the first,
+  // so that no iteration waits for an L2 round trip; stale values only prune
+  // less or hand work out later.  Warp-uniform state that is touched only
+  // at claims, refreshes, hand-offs and the end (lane 0 writes it, behind
+  // __syncwarp) lives in shared memory, not in registers: the loop then
+  // needs fewer registers than 3 blocks of 128 threads allow, spill-free.
+  struct WarpCtl {
+    unsigned long long pf_toi, pf_qnext, nx_toi, nx_qnext, pf_occ, nx_head, nx_tail;
+    unsigned long long c_reg;                 // lane 0's claim after the next batch
+    uint32_t s_base, n_base;                  // staged batches (query indices < 2^32)
+    int sbuf, s_n, s_pos, n_n, claims_done;
+    unsigned n_exp, n_cap, n_don, n_eval_tail;
+    long long wsince;                         // evaluations in the tail since the last hand-off
+  };
+  __shared__ WarpCtl WC[kNarrowThreads / 32];
+  WarpCtl &wc = WC[threadIdx.x >> 5];
+  if (lane == 0) {
+    wc.pf_toi = kInfBits;
+    wc.pf_qnext = 0;
+    wc.pf_occ = 0;
+    wc.n_exp = wc.n_cap = wc.n_don = wc.n_eval_tail = 0;
+    wc.wsince = 0;
+  }
   unsigned long long g_toi = kInfBits;                          // all lanes: pf_toi at the last refresh
   bool g_tail = false;                                          // all lanes: every query taken (last refresh)
   unsigned long long cut_prev = ~0ull;                          // cut53 = ceil53(cut_prev)
   uint64_t cut53 = 0;
-  unsigned long long nx_toi = kInfBits, nx_qnext = 0;          // lane 0: loads in flight
-  unsigned long long pf_occ = 0, nx_head = 0, nx_tail = 0;     // lane 0: ring occupancy
-  unsigned long long nx_scene = kInfBits;                      // per lane
   int pf_age = 0;
   if (lane == 0) {
-    nx_toi = ld_relaxed_u64(&ctl->toi_bits);
-    nx_qnext = ld_relaxed_u64(&ctl->q_next);
-    nx_head = ld_relaxed_u64(&ctl->q_head);
-    nx_tail = ld_relaxed_u64(&ctl->q_tail);
+    wc.nx_toi = ld_relaxed_u64(&ctl->toi_bits);
+    wc.nx_qnext = ld_relaxed_u64(&ctl->q_next);
+    wc.nx_head = ld_relaxed_u64(&ctl->q_head);
+    wc.nx_tail = ld_relaxed_u64(&ctl->q_tail);
   }
+  __syncwarp(FULL);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->t_start, 0ull, globaltimer());
 
   // Staged claims (with query records only): the current batch [s_base,
   // s_base + s_n) of which s_pos are taken, the next batch (records in
-  // flight into the other buffer) and, in lane 0, the claim after it.
+  // flight into the other buffer) and the claim after it (WarpCtl).
   extern __shared__ __align__(16) unsigned char dyn_smem[];
 #define ST ((Stage *)dyn_smem + 2 * (threadIdx.x >> 5))
-  int sbuf = 0, s_n = 0, s_pos = 0, n_n = 0;
-  uint32_t s_base = 0, n_base = 0;           // query indices are below 2^32
-  unsigned long long c_reg = 0;
-  bool claims_done = false;                  // warp-uniform: a claim came back empty
   const bool staged = kRecords;
   if (staged) {
     unsigned long long b0 = 0, b1 = 0;
     if (lane == 0) {
       b0 = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
       b1 = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
-      c_reg = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
+      wc.c_reg = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
     }
     b0 = __shfl_sync(FULL, b0, 0);
     b1 = __shfl_sync(FULL, b1, 0);
     const unsigned long long un = (unsigned long long)nq;
-    s_base = (uint32_t)b0;
-    s_n = b0 < un ? (int)min((unsigned long long)kStageQ, un - b0) : 0;
-    n_base = (uint32_t)b1;
-    n_n = b1 < un ? (int)min((unsigned long long)kStageQ, un - b1) : 0;
-    claims_done = n_n < kStageQ;
+    const int s_n = b0 < un ? (int)min((unsigned long long)kStageQ, un - b0) : 0;
+    const int n_n = b1 < un ? (int)min((unsigned long long)kStageQ, un - b1) : 0;
+    const bool claims_done = n_n < kStageQ;
+    if (lane == 0) {
+      wc.s_base = (uint32_t)b0;
+      wc.s_n = s_n;
+      wc.n_base = (uint32_t)b1;
+      wc.n_n = n_n;
+      wc.claims_done = claims_done;
+      wc.sbuf = 0;
+      wc.s_pos = 0;
+    }
     if (lane == 0 && s_n + n_n > 0) atomicAdd(&ctl->pending, (unsigned long long)(s_n + n_n));
     if (s_n > 0) stage_copy(ST[0], A, b0, lane);
     if (n_n > 0) stage_copy(ST[1], A, b1, lane);
@@ -1082,6 +1103,10 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       const unsigned long long pf_toi_b = g_toi;
       const unsigned m = __ballot_sync(FULL, !have);
       if (m && !exhausted && staged) {
+        // the warp's staging state, kept in shared memory between claims
+        int sbuf = wc.sbuf, s_n = wc.s_n, s_pos = wc.s_pos, n_n = wc.n_n;
+        uint32_t s_base = wc.s_base, n_base = wc.n_base;
+        bool claims_done = wc.claims_done;
         if (s_pos == s_n) {
           if (n_n == 0) {
             exhausted = true;
@@ -1096,7 +1121,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
             s_pos = 0;
             n_n = 0;
             if (!claims_done) {
-              const unsigned long long nb = __shfl_sync(FULL, c_reg, 0);
+              const unsigned long long nb = wc.c_reg;
               const int nn = nb < (unsigned long long)nq ? (int)min((unsigned long long)kStageQ,
                                                                     (unsigned long long)nq - nb) : 0;
               claims_done = nn < kStageQ;
@@ -1106,7 +1131,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
                 stage_copy(ST[sbuf ^ 1], A, nb, lane);
                 if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)nn);
               }
-              if (!claims_done && lane == 0) c_reg = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
+              __syncwarp(FULL);   // every lane has read c_reg
+              if (!claims_done && lane == 0) wc.c_reg = atomicAdd(&ctl->q_next, (unsigned long long)kStageQ);
               if (claims_done && lane == 0 && ld_relaxed_u64(&ctl->t_exhausted) == 0)
                 atomicCAS(&ctl->t_exhausted, 0ull, globaltimer());
             }
@@ -1123,6 +1149,17 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           }
           s_pos += k;
         }
+        __syncwarp(FULL);   // every lane has read the staging state
+        if (lane == 0) {
+          wc.sbuf = sbuf;
+          wc.s_n = s_n;
+          wc.s_pos = s_pos;
+          wc.n_n = n_n;
+          wc.s_base = s_base;
+          wc.n_base = n_base;
+          wc.claims_done = claims_done;
+        }
+        __syncwarp(FULL);
       } else if (m && !exhausted) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&ctl->q_next, (unsigned long long)__popc(m));
@@ -1149,7 +1186,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       // lanes fills its idle ones by donation below (shuffles and shared
       // memory), which costs none of the ring's L2 round trips that would
       // otherwise sit on the path of the tail's long queries.
-      if (exhausted && __ballot_sync(FULL, have) == 0 && __shfl_sync(FULL, pf_occ, 0) > 0) {
+      if (exhausted && __ballot_sync(FULL, have) == 0 && wc.pf_occ > 0) {
         // pop up to one cell per idle lane: lanes test the cells' sequence
         // numbers in parallel, lane 0 claims the ready prefix with one CAS
         const unsigned m = __ballot_sync(FULL, !have);
@@ -1197,7 +1234,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         if (cand) {
           unsigned long long c = tq;
           if (A.mode == 1) c = min(c, pf_toi_b);
-          if (A.mode == 2) c = min(c, pf_scene);
+          if (A.mode == 2) c = min(c, SCN[0][tid]);
           dS = deep ? shallowest_pending(K, N, depth, root_depth, c, S)
                     : shallowest_owed(N, depth, root_depth, pend, axlo, axhi, c, S);
         }
@@ -1240,14 +1277,14 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           const int l0 = __shfl_sync(FULL, S.l0, src), l1 = __shfl_sync(FULL, S.l1, src),
                     l2 = __shfl_sync(FULL, S.l2, src);
           const long long qv = __shfl_sync(FULL, (long long)q, src);
-          const int sidv = __shfl_sync(FULL, sid, src);
+          const int sidv = A.mode == 2 ? SID[(tid & ~31) + src] : 0;   // (a busy lane's entry)
           const int vfv = __shfl_sync(FULL, (int)vf, src);
           const unsigned long long tqv = __shfl_sync(FULL, tq, src);
 
           if (recv) {
             q = qv;
-            sid = sidv;
-            pf_scene = nx_scene = kInfBits;
+            if (A.mode == 2) SID[tid] = sidv;
+            SCN[0][tid] = SCN[1][tid] = kInfBits;
             vf = vfv != 0;
             N = Node{s0, s1, s2, l0, l1, l2};
             depth = root_depth = N.depth();
@@ -1262,7 +1299,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           }
           if (give) {
             root_depth = dS;   // the donated sibling is no longer ours
-            ++n_don;
+            atomicAdd(&wc.n_don, 1u);
             if (whole) {
               // the query's budget becomes shared: publish the evaluations so
               // far (the counter was 0 while this lane owned the query)
@@ -1287,36 +1324,36 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       if (lane == 0) {
         const unsigned long long h = ld_relaxed_u64(&ctl->q_head), t = ld_relaxed_u64(&ctl->q_tail);
         const unsigned long long pend = ld_relaxed_u64(&ctl->pending);
-        pf_occ = t > h ? t - h : 0;   // an idle warp sees new exports at once
-        stop = (exhausted && pf_occ == 0 && pend == 0) || ++idle_rounds > kIdleRounds;
+        wc.pf_occ = t > h ? t - h : 0;   // an idle warp sees new exports at once
+        stop = (exhausted && wc.pf_occ == 0 && pend == 0) || idle_rounds >= kIdleRounds;
       }
       if (__shfl_sync(FULL, stop, 0)) break;
-      __nanosleep(nap);          // back off while nothing turns up
-      nap = min(2 * nap, kNapMax);
+      // back off while nothing turns up: kNapMin doubling up to kNapMax
+      __nanosleep(min(kNapMin << min(idle_rounds, 5), kNapMax));
+      ++idle_rounds;
       continue;
     }
     idle_rounds = 0;
-    nap = kNapMin;
 
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
       QueryData Q;
       if constexpr (kRecords) {
         if (slot >= 0) {
-          load_record_stage(Q, vf, ST[sbuf], slot);
-          sid = A.mode == 2 ? ST[sbuf].sid[slot] : 0;
+          load_record_stage(Q, vf, ST[wc.sbuf], slot);
+          if (A.mode == 2) SID[tid] = ST[wc.sbuf].sid[slot];
         } else {
           load_record(Q, vf, A.qrec, A.rec_stride, q);
-          sid = A.mode == 2 ? A.qsid[q] : 0;
+          if (A.mode == 2) SID[tid] = A.qsid[q];
         }
       } else {
         int ids[4];
         query_ids(q, A.n_vf, A.vf, A.ee, A.E, A.F, ids, vf);
         setup_query(Q, vf, ids, A.V0, A.V1, A.nV, A.min_sep, A.delta);
-        sid = A.mode == 2 ? A.qsid[q] : 0;
+        if (A.mode == 2) SID[tid] = A.qsid[q];
       }
       put_shared(SQ, tid, Q);
-      pf_scene = nx_scene = kInfBits;   // the loaded values belonged to the previous query
+      SCN[0][tid] = SCN[1][tid] = kInfBits;   // the loaded values belonged to the previous query
 #pragma unroll
       for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -1360,29 +1397,30 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     if (++pf_age == kRefresh) {
       pf_age = 0;
       if (lane == 0) {
-        pf_toi = nx_toi;
-        pf_qnext = nx_qnext;
-        pf_occ = nx_tail > nx_head ? nx_tail - nx_head : 0;
-        if (pf_occ > 0) atomicMax(&ctl->queue_peak, pf_occ);
-        nx_toi = ld_relaxed_u64(&ctl->toi_bits);
-        nx_qnext = ld_relaxed_u64(&ctl->q_next);
-        nx_head = ld_relaxed_u64(&ctl->q_head);
-        nx_tail = ld_relaxed_u64(&ctl->q_tail);
+        wc.pf_toi = wc.nx_toi;
+        wc.pf_qnext = wc.nx_qnext;
+        wc.pf_occ = wc.nx_tail > wc.nx_head ? wc.nx_tail - wc.nx_head : 0;
+        if (wc.pf_occ > 0) atomicMax(&ctl->queue_peak, wc.pf_occ);
+        wc.nx_toi = ld_relaxed_u64(&ctl->toi_bits);
+        wc.nx_qnext = ld_relaxed_u64(&ctl->q_next);
+        wc.nx_head = ld_relaxed_u64(&ctl->q_head);
+        wc.nx_tail = ld_relaxed_u64(&ctl->q_tail);
       }
+      __syncwarp(FULL);
       if (A.mode == 2) {
-        pf_scene = nx_scene;
-        if (have) nx_scene = ld_relaxed_u64(&A.toi_scene[sid]);
+        SCN[0][tid] = SCN[1][tid];
+        if (have) SCN[1][tid] = ld_relaxed_u64(&A.toi_scene[SID[tid]]);
       }
       // broadcast once per refresh, not per iteration
-      g_toi = __shfl_sync(FULL, pf_toi, 0);
-      g_tail = __shfl_sync(FULL, pf_qnext, 0) >= (unsigned long long)nq;
+      g_toi = wc.pf_toi;
+      g_tail = wc.pf_qnext >= (unsigned long long)nq;
     }
     unsigned long long cut = tq;
     const unsigned long long g = g_toi;
     // hand work out only once every query has been taken (idle lanes exist)
     const bool tail_phase = g_tail;
     if (A.mode == 1) cut = g < cut ? g : cut;
-    if (A.mode == 2) cut = pf_scene < cut ? pf_scene : cut;
+    if (A.mode == 2) cut = min(SCN[0][tid], cut);
     bool node_done = true;     // false when the node was split (go to its left child)
     bool unit_end = false;
     bool evaluate = false;
@@ -1409,9 +1447,9 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         }
         tq = m < tq ? m : tq;
         if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);       // (modes 1, 2: as an accept)
-        if (A.mode == 2) atomicMin(&A.toi_scene[sid], tq);
+        if (A.mode == 2) atomicMin(&A.toi_scene[SID[tid]], tq);
         flags |= CCD_FLAG_ITER_CAP;
-        ++n_cap;
+        atomicAdd(&wc.n_cap, 1u);
         --cnt;
         unit_end = true;
       } else {
@@ -1420,7 +1458,6 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     }
     if (evaluate) {
       ++n_eval;
-      n_eval_tail += tail_phase;
       // Single-precision filter: when every level is <= 24 the interval's
       // ends are exact floats and the FP32 hull is within e32 of the FP64
       // hull, its certified ends L, H bound R's; a miss, or a split (no miss,
@@ -1529,7 +1566,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         if (accept) {
           tq = dbits(dyadic(N.n0, N.l0));
           if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);
-          if (A.mode == 2) atomicMin(&A.toi_scene[sid], tq);
+          if (A.mode == 2) atomicMin(&A.toi_scene[SID[tid]], tq);
           // Every owed sibling that starts at or after T = this node's t_lo is
           // now pruned; drop them from the path at once instead of visiting
           // them one by one.  A t-sibling starts after T (T lies in its left
@@ -1619,9 +1656,17 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     //         ring every 32 x `budget` evaluations of the warp, in one
     //         reservation ---------------------------------------------------
     {
-      if (tail_phase) wsince += __popc(__ballot_sync(FULL, evaluate));
-      const bool trig = wsince >= 32ll * A.budget;   // (tail phase only)
-      if (trig) wsince = 0;
+      bool trig = false;   // (the same in every lane)
+      if (tail_phase) {
+        const int ne = __popc(__ballot_sync(FULL, evaluate));
+        const long long ws = wc.wsince + ne;
+        trig = ws >= 32ll * A.budget;
+        __syncwarp(FULL);
+        if (lane == 0) {
+          wc.n_eval_tail += ne;
+          wc.wsince = trig ? 0 : ws;
+        }
+      }
       const bool want_exp = trig && have && !unit_end;
       if (trig && __any_sync(FULL, want_exp)) {   // (trig is the same in every lane)
         Node S{0, 0, 0, 0, 0, 0};
@@ -1649,7 +1694,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
               if (A.mode == 0)
                 atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
               else if (A.mode == 2)
-                atomicMin(&A.toi_scene[sid], tq);
+                atomicMin(&A.toi_scene[SID[tid]], tq);
               else
                 atomicMin(&ctl->toi_bits, tq);
             }
@@ -1659,7 +1704,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
             whole = false;
             ring_write(A.ring, A.ring_mask, pos0 + __popc(xm & lt_mask), (uint32_t)q, S, &ctl->status);
             root_depth = dS;
-            ++n_exp;
+            atomicAdd(&wc.n_exp, 1u);
           }
         }
       }
@@ -1701,10 +1746,13 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     }
   }
   if (n_eval) atomicAdd(&ctl->n_intervals, (unsigned long long)n_eval);
-  if (n_exp) atomicAdd(&ctl->n_exported, (unsigned long long)n_exp);
-  if (n_cap) atomicAdd(&ctl->n_capped, (unsigned long long)n_cap);
-  if (n_don) atomicAdd(&ctl->n_donated, (unsigned long long)n_don);
-  if (n_eval_tail) atomicAdd(&ctl->n_intervals_tail, (unsigned long long)n_eval_tail);
+  __syncwarp(FULL);
+  if (lane == 0) {
+    if (wc.n_exp) atomicAdd(&ctl->n_exported, (unsigned long long)wc.n_exp);
+    if (wc.n_cap) atomicAdd(&ctl->n_capped, (unsigned long long)wc.n_cap);
+    if (wc.n_don) atomicAdd(&ctl->n_donated, (unsigned long long)wc.n_don);
+    if (wc.n_eval_tail) atomicAdd(&ctl->n_intervals_tail, (unsigned long long)wc.n_eval_tail);
+  }
   if (n_eval64) atomicAdd(&ctl->n_intervals_fp64, (unsigned long long)n_eval64);
   if (lane == 0) atomicMax(&ctl->t_end, globaltimer());
 }
