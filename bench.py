@@ -209,10 +209,12 @@ def stage_algorithmic(st, nV, nE, nF):
         # out: float box (24 B), ordered FP64 extents (48 B), ids (16 B)
         "boxes": ("hbm", 48 * nV + 8 * nE + 12 * nF + 88 * nB),
         # cell counts (8 B per box in), keys and values of the copies (12 B
-        # out), 7 passes (8-bit digits of the 56-bit key) of key + value in
-        # and out (24 B per copy), gather to sorted order (12 B key/value +
-        # 36 B box data in, 36 B out)
-        "sort": ("hbm", 8 * nB + 12 * nc + 7 * 24 * nc + 84 * nc),
+        # out), one counting read of the keys (8 B per copy), 7 passes (8-bit
+        # digits of the 56-bit key) of key + value in and out (24 B per copy;
+        # passes of digits that every key shares are skipped, two at a time,
+        # but still counted), gather to sorted order (12 B key/value + 36 B
+        # box data in, 36 B out)
+        "sort": ("hbm", 8 * nB + 12 * nc + 8 * nc + 7 * 24 * nc + 84 * nc),
         # sorted copies once (44 B with the key), 8 B per candidate written,
         # then the exact filter: 8 B read + 96 B of FP64 extents per
         # candidate, 8 B per pair written
@@ -329,7 +331,7 @@ def run_ours(args):
     if dom == "narrow":
         dom = "narrow_kernel"                # the dominant kernel: k_narrow, timed alone
     kind, work = algo[dom]
-    kernel = {"boxes": "k_build_boxes", "sort": "k_radix_scatter", "sweep": "k_sweep_strips",
+    kernel = {"boxes": "k_build_boxes", "sort": "k_sort_pass", "sweep": "k_sweep_strips",
               "narrow_kernel": "k_narrow"}[dom]
     traffic = None
     tr = NCU_TRAFFIC.get(kernel)

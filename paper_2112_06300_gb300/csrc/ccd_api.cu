@@ -49,6 +49,7 @@ struct ccd_ctx {
   float *ssum = nullptr;
   uint32_t *smm = nullptr;
   const unsigned long long *s_key_last = nullptr;   // sorted copy keys of the last broad phase
+  SortWork sortw{};                                  // radix sort counters and look-back states
   int64_t last_ranges = 0;                          // ranges of the last memory-limited step
   // FP64 strip sweep buffers, sized for cap_boxes boxes (allocated on first use)
   int64_t cap_strips64 = 0;
@@ -149,7 +150,6 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   // 3 nB + 4096 copies, and past that the device falls back to one strip per
   // scene (the plain sweep)
   const int64_t capc = 3 * cap + 4096;
-  int64_t ntiles = cdiv(capc, kSortTile);
   int64_t nbuild = cdiv(cap, kBuildThreads);
   size_t bytes = 0;
   auto take = [&](size_t n) { size_t off = bytes; bytes += (n + 255) & ~size_t(255); return off; };
@@ -157,7 +157,7 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   size_t o_lo64 = take(3 * cap * sizeof(long long)), o_hi64 = take(3 * cap * sizeof(long long));
   size_t o_vid = take(cap * sizeof(int4));
   size_t o_k0 = take(capc * 8), o_k1 = take(capc * 8), o_v0 = take(capc * 4), o_v1 = take(capc * 4);
-  size_t o_hist = take((256 * ntiles + 256) * 4);
+  size_t o_sortw = take(sort_work_bytes(capc));
   size_t o_salo = take(cap * 4), o_sahi = take(capc * 4);
   size_t o_soth = take(capc * sizeof(float4)), o_svid = take(capc * sizeof(int4));
   size_t o_part = take(kStatWords * nbuild * sizeof(float));
@@ -178,7 +178,8 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   B.keys[1] = m + o_k1;
   B.vals[0] = (uint32_t *)(m + o_v0);
   B.vals[1] = (uint32_t *)(m + o_v1);
-  B.hist = (uint32_t *)(m + o_hist);
+  CK(cudaMemset(m + o_sortw, 0, sort_work_bytes(capc)));   // the sort's counters start at zero
+  c->sortw = sort_work_at(m + o_sortw);
   B.s_alo = (float *)(m + o_salo);
   B.s_ahi = (float *)(m + o_sahi);
   B.s_oth = (float4 *)(m + o_soth);
@@ -421,13 +422,13 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     k_count_copies<<<nblk, kCopyBlock, 0, s>>>(nB, B, c->ctl);
     k_scan_copies<<<1, 1024, 0, s>>>(nblk, nB, B, c->ctl);
     k_expand_copies64<<<grid, 256, 0, s>>>(nB, B, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
-    const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, B.hist, s, 64, &c->ctl->n_copies);
+    const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, c->sortw, s, &c->ctl->status, 64, &c->ctl->n_copies);
     const int cgrid = (int)std::min<int64_t>(cdiv(B.cap_copies, 256), (int64_t)c->sm_count * 8);
     uint32_t *ka = (uint32_t *)B.keys[cur ^ 1];
     void *k2[2] = {ka, ka + B.cap_copies};
     uint32_t *v2[2] = {B.vals[cur], B.vals[cur ^ 1]};
     k_gather_seg<<<cgrid, 256, 0, s>>>(B.cap_copies, c->ctl, B.vals[cur], B.c_seg, ka);
-    const int cur2 = radix_sort(k2, v2, 4, B.cap_copies, B.hist, s, 24, &c->ctl->n_copies);
+    const int cur2 = radix_sort(k2, v2, 4, B.cap_copies, c->sortw, s, &c->ctl->status, 24, &c->ctl->n_copies);
     k_gather_copies64<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, v2[cur2]);
     sort_passes = 8 + 3;
     extra = 3;
@@ -437,7 +438,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     k_scan_copies<<<1, 1024, 0, s>>>(nblk, nB, B, c->ctl);
     k_expand_copies<<<grid, 256, 0, s>>>(nB, B, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
     const int bits = sc.n > 0 ? 48 + sbits : 56;   // cell index: 16 bits batched, 24 bits alone
-    const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, B.hist, s, bits, &c->ctl->n_copies);
+    const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, c->sortw, s, &c->ctl->status, bits, &c->ctl->n_copies);
     const int cgrid = (int)std::min<int64_t>(cdiv(B.cap_copies, 256), (int64_t)c->sm_count * 8);
     k_gather_copies<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, (const unsigned long long *)B.keys[cur], B.vals[cur]);
     s_key = (const unsigned long long *)B.keys[cur];
@@ -447,16 +448,16 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     // scene in the high word of the key: one sorted run per scene
     const int bits = 32 + sbits;
     k_make_keys_scenes<<<grid, 256, 0, s>>>(nB, B, (unsigned long long *)B.keys[0], B.vals[0]);
-    const int cur = radix_sort(B.keys, B.vals, 8, nB, B.hist, s, bits);
+    const int cur = radix_sort(B.keys, B.vals, 8, nB, c->sortw, s, &c->ctl->status, bits);
     k_gather_sorted<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
     sort_passes = (bits + 7) / 8;
   } else if (!fp64) {
     k_make_keys<<<grid, 256, 0, s>>>(nB, B.lo32, c->ctl, (uint32_t *)B.keys[0], B.vals[0]);
-    const int cur = radix_sort(B.keys, B.vals, 4, nB, B.hist, s);
+    const int cur = radix_sort(B.keys, B.vals, 4, nB, c->sortw, s, &c->ctl->status);
     k_gather_sorted<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
   } else {
     k_make_keys64<<<grid, 256, 0, s>>>(nB, B.lo64, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
-    const int cur = radix_sort(B.keys, B.vals, 8, nB, B.hist, s);
+    const int cur = radix_sort(B.keys, B.vals, 8, nB, c->sortw, s, &c->ctl->status);
     k_gather_sorted64<<<grid, 256, 0, s>>>(nB, B.vals[cur], c->ctl, B);
   }
   mark(c, CCD_STAGE_SORT, false, s);
@@ -1321,15 +1322,57 @@ int ccd_selftest_unfinished_work(ccd_ctx *c, int32_t *status, void *stream) {
   return CCD_OK;
 }
 
+int ccd_selftest_radix_sort(ccd_ctx *c, int key_bytes, int key_bits, int64_t n, int64_t n_cap, void *keys,
+                            uint32_t *vals, int32_t *status, void *stream) {
+  if (!c || !status || (key_bytes != 4 && key_bytes != 8) || key_bits < 0 || key_bits > 8 * key_bytes || n < 0 ||
+      n_cap < n || n_cap >= (1ll << 32) || (n > 0 && (!keys || !vals)))
+    return CCD_EINVAL;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t cap = std::max<int64_t>(n_cap, 1);
+  const size_t wb = sort_work_bytes(cap);
+  char *m = nullptr;
+  if (cudaMalloc(&m, 2 * cap * (key_bytes + 4) + wb + 1024) != cudaSuccess) return CCD_ENOMEM;
+  void *kb[2] = {m, m + cap * key_bytes};
+  uint32_t *vb[2] = {(uint32_t *)(m + 2 * cap * key_bytes), (uint32_t *)(m + 2 * cap * key_bytes) + cap};
+  char *wm = m + 2 * cap * (key_bytes + 4);
+  wm = (char *)(((uintptr_t)wm + 255) & ~(uintptr_t)255);
+  unsigned long long *n_dev = (unsigned long long *)(wm + wb);
+  int rc = CCD_OK;
+  int32_t h = CCD_OK;
+  int cur = 0;
+  const unsigned long long un = (unsigned long long)n;
+  if (cudaMemsetAsync(wm, 0, wb, s) != cudaSuccess ||
+      cudaMemcpyAsync(n_dev, &un, sizeof(un), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      (n > 0 && (cudaMemcpyAsync(kb[0], keys, n * key_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                 cudaMemcpyAsync(vb[0], vals, n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess))) {
+    rc = CCD_ECUDA;
+  } else {
+    k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+    cur = radix_sort(kb, vb, key_bytes, n_cap, sort_work_at(wm), s, &c->ctl->status, key_bits,
+                     n_cap > n ? n_dev : nullptr);
+    if ((n > 0 && (cudaMemcpyAsync(keys, kb[cur], n * key_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                   cudaMemcpyAsync(vals, vb[cur], n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)) ||
+        cudaMemcpyAsync(&h, &c->ctl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = CCD_ECUDA;
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(m);
+  *status = h;
+  return rc;
+}
+
 int ccd_get_memory_model(const ccd_opts *o, ccd_memory_model *m) {
   if (!m) return CCD_EINVAL;
   ccd_opts opts;
   ccd_default_opts(&opts);
   if (o) opts = *o;
   // per box, as laid out by ensure_broad: FP32 and FP64 extents, vertex ids,
-  // sort keys and values and the sorted arrays for 3 copies per box (strip
-  // sweep), the one-list sorted arrays, copy offsets; plus the scene index
-  m->bytes_per_box = 24 + 48 + 16 + 3 * (16 + 8) + 2 + 4 + 3 * (4 + 16 + 16) + (8 + 8 + 32) + 4 + 4;
+  // sort keys and values, the sort's look-back states (8 passes x 2 KB per
+  // 4096 keys) and the sorted arrays for 3 copies per box (strip sweep), the
+  // one-list sorted arrays, copy offsets; plus the scene index
+  m->bytes_per_box = 24 + 48 + 16 + 3 * (16 + 8) + 3 * 4 + 4 + 3 * (4 + 16 + 16) + (8 + 8 + 32) + 4 + 4;
   // and the narrow phase's per-primitive set-up record (at most a face's)
   m->bytes_per_box += narrow_prim_words(0, 0, 1) * 8;
   // per pair slot: the pair (8), two candidate slots (16), and the narrow

@@ -12,7 +12,8 @@
 //                    on the two other axes (both affect speed only).
 //   k_*_copies       one copy of each box per cell it overlaps, keyed by
 //                    (cell, ordered bits of the minimum on the sweep axis).
-//   k_radix_*        stable LSD radix sort of the keys, 8 bits per pass.
+//   k_sort_*         stable LSD radix sort of the keys, 8 bits per pass, one
+//                    kernel per pass (decoupled look-back across tiles).
 //   k_sweep_strips   the cell sweep (default): one thread per sorted copy
 //                    walks its range in its cell; a pair is reported in one
 //                    cell only; candidates go to a list for the exact filter.
@@ -367,151 +368,260 @@ __global__ void k_make_keys64(int64_t nB, const long long *lo64, const DevCtl *c
   }
 }
 
-// ---- radix sort: histogram / scan / stable scatter, 8 bits per pass --------
+// ---- radix sort: one kernel per 8-bit digit, decoupled look-back ----------
+//
+// k_sort_hist reads the keys once and counts every digit of every pass (the
+// global digit totals do not depend on the order), clears the look-back
+// states and, in its last block, turns the totals into each pass's digit
+// bases.  A pass whose digit is the same for every key would leave the order
+// as it is; such passes are skipped two at a time, so that the result always
+// lands in the buffers that running every pass would give.  Each k_sort_pass
+// block takes the next tile (an atomic counter, so that every earlier tile
+// belongs to a block that is already running), ranks its keys stably (warps
+// in index order; within a warp, the lanes of equal digit from 8 ballots),
+// publishes its per-digit counts, adds up the counts of the tiles before it
+// by walking back (16 tiles per round trip) until a tile that has published
+// its inclusive prefix, publishes its own prefix and scatters.  The
+// walk-back waits are bounded: a wait that runs out raises CCD_ETIMEOUT and
+// the scatter stays within the output.
 
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads)
-k_radix_hist(const K *__restrict__ keys, int64_t n, int shift, uint32_t *hist, int ntiles,
-             const unsigned long long *n_dev) {
-  __shared__ uint32_t h[256];
-  if (n_dev) n = min(n, (int64_t)*n_dev);
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    int64_t i = base + r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 0xFFu], 1u);
-  }
-  __syncthreads();
-  hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];   // digit-major
+constexpr unsigned long long kAggFlag = 1ull << 62, kPrefixFlag = 2ull << 62;
+constexpr unsigned long long kStateValue = (1ull << 62) - 1;
+constexpr unsigned kLookbackSpins = 1u << 21;
+constexpr int kLookbackWindow = 16;
+constexpr int kOsWarps = kOsThreads / 32;
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Row scan of the digit-major histogram: block d turns row d (the counts of
-// digit d in every tile) into its exclusive prefix and stores the row total;
-// the scatter adds the exclusive prefix of the totals (the digit's base).
-__global__ void __launch_bounds__(256) k_radix_scan_rows(uint32_t *hist, int ntiles, uint32_t *totals) {
-  __shared__ uint32_t wsum[8];
-  __shared__ uint32_t carry;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t *row = hist + (int64_t)blockIdx.x * ntiles;
-  if (tid == 0) carry = 0;
+// Lanes of the warp whose 8-bit digit equals this lane's (lanes outside
+// `valid` excluded): eight ballots, one per bit.
+__device__ __forceinline__ unsigned same_digit_lanes(uint32_t d, unsigned valid) {
+  unsigned peers = valid;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const unsigned bb = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+    peers &= ((d >> b) & 1u) ? bb : ~bb;
+  }
+  return peers;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kOsThreads)
+k_sort_hist(const K *__restrict__ keys, int64_t n, const unsigned long long *n_dev, int passes, SortWork W) {
+  __shared__ uint32_t h[kMaxSortPasses][256];
+  __shared__ uint32_t wsum[kOsWarps];
+  __shared__ int last;
+  __shared__ int constant[kMaxSortPasses];
+  if (n_dev) n = min(n, (int64_t)*n_dev);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int p = 0; p < passes; ++p) {
+    W.states[((int64_t)p * gridDim.x + blockIdx.x) * 256 + tid] = 0;   // this tile's look-back states
+    h[p][tid] = 0;
+  }
   __syncthreads();
-  for (int base = 0; base < ntiles; base += 256) {
-    const int i = base + tid;
-    const uint32_t v = i < ntiles ? row[i] : 0u;
+  const int64_t base = (int64_t)blockIdx.x * kOsTile;
+  if (base < n) {
+#pragma unroll 4
+    for (int r = 0; r < kOsItems; ++r) {
+      const int64_t i = base + r * kOsThreads + tid;
+      const bool ok = i < n;
+      const K k = ok ? keys[i] : K(0);
+      const unsigned valid = __ballot_sync(0xFFFFFFFFu, ok);
+      for (int p = 0; p < passes; ++p) {
+        // a digit that every valid lane of the warp shares (the common case
+        // for the high digits) takes one shared-memory atomic, others one each
+        const uint32_t d = (uint32_t)(k >> (8 * p)) & 0xFFu;
+        const uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, ok ? d : 0xFFu);
+        const uint32_t hi = __reduce_max_sync(0xFFFFFFFFu, ok ? d : 0u);
+        if (lo == hi) {
+          if (lane == 0 && valid) atomicAdd(&h[p][lo], (uint32_t)__popc(valid));
+        } else if (ok) {
+          atomicAdd(&h[p][d], 1u);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < passes; ++p)
+    if (h[p][tid]) atomicAdd(&W.ghist[p * 256 + tid], h[p][tid]);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(&W.plan->blocks_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  // the last block: digit bases per pass (exclusive prefix of the totals)
+  __threadfence();
+  SortPlan *P = W.plan;
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t v = atomicExch(&W.ghist[p * 256 + tid], 0u);   // read, and clear for the next sort
     uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    uint32_t before = carry;
-    for (int w = 0; w < warp; ++w) before += wsum[w];
-    const uint32_t excl = before + x - v;
-    if (i < ntiles) row[i] = excl;
-    __syncthreads();
-    if (tid == 255) carry = excl + v;
-    __syncthreads();
-  }
-  if (tid == 0) totals[blockIdx.x] = carry;
-}
-
-// Stable scatter of one tile: rounds of 256 consecutive keys; within a round
-// each key's rank among equal digits comes from __match_any_sync (warp) plus
-// the counts of earlier warps and earlier rounds.
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads)
-k_radix_scatter(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in, K *__restrict__ keys_out,
-                uint32_t *__restrict__ vals_out, int64_t n, int shift, const uint32_t *__restrict__ offsets,
-                int ntiles, const uint32_t *__restrict__ totals, const unsigned long long *n_dev) {
-  constexpr int kWarps = kSortThreads / 32;
-  if (n_dev) n = min(n, (int64_t)*n_dev);
-  if ((int64_t)blockIdx.x * kSortTile >= n) return;   // whole tile beyond the count (uniform)
-  __shared__ uint32_t run[256];              // running position per digit
-  __shared__ uint32_t wcnt[kWarps][256];     // per-warp digit counts of the round
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  {
-    // digit base: exclusive scan of the 256 digit totals
-    const uint32_t tot = totals[threadIdx.x];
-    uint32_t x = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wcnt[0][w] = x;
+    if (lane == 31) wsum[w] = x;
+    if (tid == 0) constant[p] = 0;
     __syncthreads();
     uint32_t before = 0;
-    for (int j = 0; j < w; ++j) before += wcnt[0][j];
-    run[threadIdx.x] = before + x - tot + offsets[threadIdx.x * ntiles + blockIdx.x];
+    for (int j = 0; j < w; ++j) before += wsum[j];
+    P->base[p][tid] = before + x - v;
+    if ((int64_t)v == n) constant[p] = 1;
     __syncthreads();
   }
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  for (int r = 0; r < kSortItems; ++r) {
-    for (int j = 0; j < kWarps; ++j) wcnt[j][threadIdx.x] = 0;
-    __syncthreads();
-    int64_t i = base + r * kSortThreads + threadIdx.x;
-    bool valid = i < n;
-    K key = valid ? keys_in[i] : K(0);
-    uint32_t val = valid ? vals_in[i] : 0;
-    uint32_t d = valid ? (uint32_t)(key >> shift) & 0xFFu : 256u + lane;   // invalid lanes never match
-    unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-    uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
-    __syncthreads();
-    // exclusive prefix over warps for this thread's digit column
-    uint32_t before = 0, tot = 0;
-    {
-      uint32_t col = threadIdx.x;
-      uint32_t acc = 0;
-      for (int j = 0; j < kWarps; ++j) {
-        uint32_t c = wcnt[j][col];
-        wcnt[j][col] = acc;
-        acc += c;
+  if (tid == 0) {
+    int nskip = 0, skip_last = -1;
+    for (int p = 0; p < passes; ++p) {
+      P->run[p] = !constant[p];
+      if (constant[p]) {
+        ++nskip;
+        skip_last = p;
       }
-      tot = acc;
     }
-    __syncthreads();
-    if (valid) {
-      before = wcnt[w][d];
-      uint32_t pos = run[d] + before + rank;
-      keys_out[pos] = key;
-      vals_out[pos] = val;
+    if (nskip & 1) P->run[skip_last] = 1;   // skip in pairs: the result's buffers stay those of every pass run
+    P->in[0] = 0;
+    for (int p = 0; p < passes; ++p) {
+      P->in[p + 1] = P->in[p] ^ P->run[p];
+      P->tiles_next[p] = 0;
     }
-    __syncthreads();
-    run[threadIdx.x] += tot;
-    __syncthreads();
+    P->n = (unsigned long long)n;
+    P->blocks_done = 0;
   }
 }
 
 template <typename K>
-int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, uint32_t *hist, cudaStream_t s, int key_bits,
-                 const unsigned long long *n_dev) {
-  const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
-  uint32_t *totals = hist + 256 * (int64_t)ntiles;
-  int cur = 0;
-  const int bits = key_bits > 0 ? key_bits : (int)(8 * sizeof(K));
-  for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], n, shift, hist, ntiles, n_dev);
-    k_radix_scan_rows<<<256, 256, 0, s>>>(hist, ntiles, totals);
-    k_radix_scatter<K><<<ntiles, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
-                                                       hist, ntiles, totals, n_dev);
-    cur ^= 1;
+__global__ void __launch_bounds__(kOsThreads)
+k_sort_pass(K *__restrict__ k0, K *__restrict__ k1, uint32_t *__restrict__ v0, uint32_t *__restrict__ v1, int pass,
+            SortWork W, int *status) {
+  const SortPlan *P = W.plan;
+  if (!P->run[pass]) return;
+  __shared__ uint32_t wh[kOsWarps][256];   // per warp and digit: count, then the warp's offset in the tile
+  __shared__ uint32_t s_pos[256];          // output position of the tile's first key of each digit
+  __shared__ uint32_t s_tile;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    s_tile = atomicAdd(&W.plan->tiles_next[pass], 1u);
+    s_bad = 0;
   }
-  return cur;
+#pragma unroll
+  for (int j = 0; j < kOsWarps; ++j) wh[j][tid] = 0;
+  __syncthreads();
+  const int64_t n = (int64_t)P->n;
+  const int64_t tile = s_tile;
+  if (tile * kOsTile >= n) return;   // (uniform) beyond the keys
+  const int in = P->in[pass];
+  const K *kin = in ? k1 : k0;
+  K *kout = in ? k0 : k1;
+  const uint32_t *vin = in ? v1 : v0;
+  uint32_t *vout = in ? v0 : v1;
+  const int shift = 8 * pass;
+  const int64_t wb = tile * kOsTile + (int64_t)w * (kOsItems * 32);   // the warp's keys, in index order
+  K key[kOsItems];
+  uint32_t val[kOsItems], off[kOsItems];
+#pragma unroll
+  for (int r = 0; r < kOsItems; ++r) {
+    const int64_t i = wb + r * 32 + lane;
+    key[r] = i < n ? kin[i] : K(0);
+    val[r] = i < n ? vin[i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kOsItems; ++r) {
+    const bool ok = wb + r * 32 + lane < n;
+    const uint32_t d = (uint32_t)(key[r] >> shift) & 0xFFu;
+    const unsigned peers = same_digit_lanes(d, __ballot_sync(0xFFFFFFFFu, ok));
+    const uint32_t before = ok ? wh[w][d] : 0u;
+    __syncwarp();
+    if (ok && lane == __ffs(peers) - 1) wh[w][d] = before + __popc(peers);
+    __syncwarp();
+    off[r] = before + __popc(peers & ((1u << lane) - 1u));
+  }
+  __syncthreads();
+  // thread tid handles digit tid: offsets of the warps within the tile
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int j = 0; j < kOsWarps; ++j) {
+    const uint32_t c = wh[j][tid];
+    wh[j][tid] = cnt;
+    cnt += c;
+  }
+  unsigned long long *st = W.states + (int64_t)pass * gridDim.x * 256;
+  unsigned long long excl = 0;
+  if (tile == 0) {
+    st_relaxed_u64(&st[tid], kPrefixFlag | cnt);
+  } else {
+    st_relaxed_u64(&st[tile * 256 + tid], kAggFlag | cnt);
+    // walk back kLookbackWindow tiles per round trip: add their counts up to
+    // the nearest tile with an inclusive prefix; a tile that has published
+    // nothing yet is read again (from there) on the next round
+    int64_t t = tile - 1;
+    unsigned spins = 0;
+    while (true) {
+      unsigned long long v[kLookbackWindow];
+#pragma unroll
+      for (int j = 0; j < kLookbackWindow; ++j) v[j] = t - j >= 0 ? ld_relaxed_u64(&st[(t - j) * 256 + tid]) : 0ull;
+      int used = 0;
+      bool done = false, wait = false;
+#pragma unroll
+      for (int j = 0; j < kLookbackWindow; ++j) {
+        if (done || wait) continue;
+        if ((v[j] >> 62) == 0 || t - j < 0) {   // (tile 0 always publishes a prefix: t - j >= 0 here)
+          wait = true;
+          continue;
+        }
+        excl += v[j] & kStateValue;
+        done = (v[j] & kPrefixFlag) != 0;
+        used = j + 1;
+      }
+      if (done) break;
+      t -= used;
+      if (wait && used == 0 && ++spins > kLookbackSpins) {   // (a tile before this one never published)
+        s_bad = 1;
+        break;
+      }
+    }
+    st_relaxed_u64(&st[tile * 256 + tid], kPrefixFlag | (excl + cnt));
+  }
+  s_pos[tid] = P->base[pass][tid] + (uint32_t)excl;
+  __syncthreads();
+  if (tid == 0 && s_bad) atomicCAS(status, CCD_OK, CCD_ETIMEOUT);
+#pragma unroll
+  for (int r = 0; r < kOsItems; ++r) {
+    if (wb + r * 32 + lane < n) {
+      const uint32_t d = (uint32_t)(key[r] >> shift) & 0xFFu;
+      const int64_t pos = (int64_t)s_pos[d] + wh[w][d] + off[r];
+      if (pos < n) {   // (always, unless a walk-back gave up)
+        kout[pos] = key[r];
+        vout[pos] = val[r];
+      }
+    }
+  }
 }
 
-int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s,
-               int key_bits, const unsigned long long *n_dev) {
+int64_t sort_tiles(int64_t n) { return std::max<int64_t>(1, (n + kOsTile - 1) / kOsTile); }
+
+template <typename K>
+int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, const SortWork &W, cudaStream_t s, int *status,
+                 int key_bits, const unsigned long long *n_dev) {
+  const int64_t ntiles = sort_tiles(n);
+  const int bits = key_bits > 0 ? key_bits : (int)(8 * sizeof(K));
+  const int passes = (bits + 7) / 8;
+  k_sort_hist<K><<<(unsigned)ntiles, kOsThreads, 0, s>>>(keys[0], n, n_dev, passes, W);
+  for (int p = 0; p < passes; ++p)
+    k_sort_pass<K><<<(unsigned)ntiles, kOsThreads, 0, s>>>(keys[0], keys[1], vals[0], vals[1], p, W, status);
+  return passes & 1;
+}
+
+int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, const SortWork &W, cudaStream_t s,
+               int *status, int key_bits, const unsigned long long *n_dev) {
   if (key_bytes == 4) {
     uint32_t *k[2] = {(uint32_t *)keys[0], (uint32_t *)keys[1]};
-    return radix_sort_t<uint32_t>(k, vals, n, hist, s, key_bits, n_dev);
+    return radix_sort_t<uint32_t>(k, vals, n, W, s, status, key_bits, n_dev);
   }
   unsigned long long *k[2] = {(unsigned long long *)keys[0], (unsigned long long *)keys[1]};
-  return radix_sort_t<unsigned long long>(k, vals, n, hist, s, key_bits, n_dev);
+  return radix_sort_t<unsigned long long>(k, vals, n, W, s, status, key_bits, n_dev);
 }
 
 __global__ void k_gather_sorted64(int64_t nB, const uint32_t *__restrict__ perm, const DevCtl *ctl, BroadBufs B) {

@@ -110,9 +110,10 @@ __global__ void k_flags_out(const uint32_t *qflags, int64_t n_vf, int64_t n_ee, 
 
 // ---- broad phase ----
 constexpr int kBuildThreads = 256;
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;                  // keys per thread per tile
-constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kOsThreads = 256;                // radix sort: threads per tile
+constexpr int kOsItems = 16;                   // keys per thread per tile
+constexpr int kOsTile = kOsThreads * kOsItems;
+constexpr int kMaxSortPasses = 8;              // 8-bit digits of a 64-bit key
 
 // Cell sweep.  Per scene, the boxes are binned into a grid of cells on the
 // two axes other than the sweep axis (a box goes into every cell it
@@ -158,7 +159,6 @@ struct BroadBufs {
   // sort (keys are 4 or 8 bytes: single-precision or FP64 form)
   void *keys[2];                 // [nB]
   uint32_t *vals[2];             // [nB]
-  uint32_t *hist;                // [256 * nTiles + 256]: digit-major counts, then digit totals
   // sorted by the minimum on the sweep axis
   float *s_alo, *s_ahi;          // [nB]
   float4 *s_oth;                 // [nB] (lo1, hi1, lo2, hi2)
@@ -219,11 +219,40 @@ __global__ void k_make_keys64(int64_t nB, const long long *lo64, const DevCtl *c
                               uint32_t *vals);
 // Stable LSD radix sort of (key, value) pairs, 8 bits per pass, on stream s;
 // keys[0]/vals[0] hold the input; returns the index (0 or 1) of the buffers
-// holding the sorted output.  key_bytes = 4 or 8.  Launches 3 kernels per pass.
+// holding the sorted output.  key_bytes = 4 or 8; only the low key_bits (0:
+// all) are sorted on.  Launches one counting kernel and one kernel per pass.
 // n_dev (optional): device count, read by the kernels, of the keys to sort
-// (at most n; grids are sized for n).
-int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, uint32_t *hist, cudaStream_t s,
-               int key_bits = 0, const unsigned long long *n_dev = nullptr);
+// (at most n; grids are sized for n).  W holds at least sort_work_bytes(n)
+// bytes, zeroed once when allocated.  A look-back wait that runs out raises
+// CCD_ETIMEOUT in *status.
+struct SortPlan {
+  unsigned long long n;                         // keys sorted
+  uint32_t blocks_done;                         // counting blocks finished
+  uint32_t tiles_next[kMaxSortPasses];          // next tile of each pass
+  int run[kMaxSortPasses];                      // the pass moves data
+  int in[kMaxSortPasses + 1];                   // buffer pass p reads; in[passes]: the result
+  uint32_t base[kMaxSortPasses][256];           // first output position of each digit
+};
+struct SortWork {
+  SortPlan *plan;
+  uint32_t *ghist;                              // [kMaxSortPasses][256], zero between sorts
+  unsigned long long *states;                   // [passes][tiles][256] look-back states
+};
+int64_t sort_tiles(int64_t n);
+inline size_t sort_work_bytes(int64_t n) {
+  return sizeof(SortPlan) + kMaxSortPasses * 256 * sizeof(uint32_t) +
+         (size_t)kMaxSortPasses * (size_t)sort_tiles(n) * 256 * sizeof(unsigned long long) + 512;
+}
+inline SortWork sort_work_at(void *base) {
+  char *m = (char *)base;
+  SortWork W;
+  W.plan = (SortPlan *)m;
+  W.ghist = (uint32_t *)(m + ((sizeof(SortPlan) + 255) & ~size_t(255)));
+  W.states = (unsigned long long *)((char *)W.ghist + kMaxSortPasses * 256 * sizeof(uint32_t));
+  return W;
+}
+int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, const SortWork &W, cudaStream_t s,
+               int *status, int key_bits = 0, const unsigned long long *n_dev = nullptr);
 __global__ void k_gather_sorted(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 __global__ void k_gather_sorted64(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 

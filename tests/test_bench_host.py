@@ -22,15 +22,16 @@ def test_stage_work_per_unit():
     nB = nV + nE + nF
     assert nB == 1_568_771
     assert w["boxes"] == ("hbm", 48 * nV + 8 * nE + 12 * nF + 88 * nB)
-    # 7 radix passes over the copies (24 B each: 8 B key and 4 B value, read and written)
-    assert w["sort"] == ("hbm", 8 * nB + (12 + 7 * 24 + 84) * 2_000_000)
+    # a counting read of the keys (8 B) and 7 radix passes over the copies (24 B each:
+    # 8 B key and 4 B value, read and written)
+    assert w["sort"] == ("hbm", 8 * nB + (12 + 8 + 7 * 24 + 84) * 2_000_000)
     assert w["sweep"] == ("hbm", 44 * 2_000_000 + 112 * 6000 + 8 * 4000)
     # per interval 42 DFMA (2 flops) + 3 DADD; per unit 45 FP64 operations
     assert bench.FLOPS_PER_INTERVAL == 87 and bench.FLOPS_PER_UNIT == 45
     assert w["narrow"] == ("alu", 87 * 50_000 + 45 * (4000 + 200))
     # copies default to one per box when the sweep did not report them
     st.pop("n_box_copies")
-    assert bench.stage_algorithmic(st, nV, nE, nF)["sort"][1] == 8 * nB + (12 + 168 + 84) * nB
+    assert bench.stage_algorithmic(st, nV, nE, nF)["sort"][1] == 8 * nB + (12 + 8 + 168 + 84) * nB
 
 
 def test_source_hash_is_short_hex():
