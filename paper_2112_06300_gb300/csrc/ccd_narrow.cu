@@ -122,70 +122,98 @@ __device__ __forceinline__ double eps_of(unsigned long long m) {
   return __dmul_rn(__longlong_as_double((long long)m), 0x1.8p-48);
 }
 
-// Second half of the per-query set-up, from c0, dc (already in Q), the error
-// term eps = 48 * 2^-53 m per axis and the split weights L_u, L_v (bits):
-// the error box e = eps + min_sep moved one ulp up, the time weight L_t, the
-// split keys and the single-precision filter data.  Rounding of eps + min_sep
-// is monotone, so the box of a query is the largest box of its primitives
-// when eps comes as the largest of theirs.
+// One axis of the second half of the per-query set-up, from the three
+// vectors' c0, dc on that axis and the error term eps = 48 * 2^-53 m: the
+// error box e = eps + min_sep moved one ulp up, the axis's part of the time
+// weight L_t (bits of sum_j |dc_j|) and the single-precision filter data.
+// Rounding of eps + min_sep is monotone, so the box of a query is the
+// largest box of its primitives when eps comes as the largest of theirs.
+struct AxisSetup {
+  double e;                      // error box half-width on the axis
+  float c0f[3], dcf[3];          // c0, dc rounded to float
+  float tn, tm, wn, cc0, cdc;    // filter thresholds and rounding bounds
+  unsigned long long st;         // bits of |dc_0| + |dc_1| + |dc_2|
+};
+
+__device__ __forceinline__ void setup_axis(AxisSetup &o, const double c0[3], const double dc[3], double eps,
+                                           double min_sep, double delta) {
+  double e = min_sep == 0.0 ? eps : __dadd_rn(eps, min_sep);   // eps + 0 is eps (eps > 0)
+  e = __longlong_as_double(__double_as_longlong(e) + 1);       // one ulp up
+  o.e = e;
+  // FP32 filter bounds (derivations at inclusion32).  With S the sum over
+  // the three vectors of |c0| + |dc| on this axis, the FP32 and FP64 hulls
+  // are less than e32 = 8 * 2^-24 * max(S, 2^-100) apart, and the FP64 hull
+  // is within e64 = 4 * 2^-53 S (+ 2^-1060 for subnormals) of R, the hull
+  // evaluated exactly from c0 and dc.  A decision taken on the FP32 hull must
+  // hold for the FP64 hull:
+  //   tm = e + eps + e32  (beyond it, the FP64 hull misses or sticks out of C;
+  //                        eps is spare margin)
+  //   wn = (delta (1 + 2^-50) + 2 eps + 2 e32)(1 + 2^-23)  (an FP32 width at or
+  //        above it means an FP64 width at or above delta)
+  //   tn = e - e64, rounded down  (an upper bound of R's low end at or below
+  //        it means the FP64 low end is at most e: no miss on that side)
+  // (all in single precision, every operation rounded toward the safe side,
+  // so each threshold is at least (tn: at most) its exact value; S from
+  // |c0| <= |float(c0)| + cc0-term; delta (1 + 2^-50) is bounded by
+  // delta (1 + 2^-23); 2^-149 stands in for 2^-1060)
+  float s32 = 0.f, cc0 = 0.f, cdc = 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float cf = d2f_near(c0[j]), df = d2f_near(dc[j]);
+    const float ec = to_float_error(c0[j]), ed = to_float_error(dc[j]);
+    o.c0f[j] = cf;
+    o.dcf[j] = df;
+    cc0 = __fadd_ru(cc0, ec);
+    cdc = __fadd_ru(cdc, ed);
+    s32 = __fadd_ru(s32, __fadd_ru(fabsf(cf), ec));
+    s32 = __fadd_ru(s32, __fadd_ru(fabsf(df), ed));
+  }
+  o.cc0 = cc0;
+  o.cdc = cdc;
+  s32 = fmaxf(s32, 0x1p-100f);
+  const float e32 = __fmul_ru(s32, 8.0f * 0x1p-24f);
+  const float eps32 = d2f_up(eps), e_32 = d2f_up(e);
+  const float e64 = __fmaf_ru(s32, 0x1p-51f, 0x1p-149f);
+  o.tn = __fsub_rd(d2f_down(e), e64);
+  o.tm = __fadd_ru(__fadd_ru(e_32, eps32), e32);
+  const float d32 = __fmul_ru(d2f_up(delta), 1.0f + 0x1p-23f);
+  const float wn = __fadd_ru(__fadd_ru(d32, __fmul_ru(2.0f, eps32)), __fmul_ru(2.0f, e32));
+  o.wn = __fmul_ru(wn, 1.0f + 0x1p-23f);
+  double st = __dadd_rn(dabs_int(dc[0]), dabs_int(dc[1]));
+  st = __dadd_rn(st, dabs_int(dc[2]));
+  o.st = dbits(st);
+}
+
+constexpr unsigned long long kKeyFloor = 0x0DF0000000000000ull;   // 2^-800: smaller split weights never split
+
+// Second half of the per-query set-up, from c0, dc (already in Q), eps per
+// axis and the split weights L_u, L_v (bits): setup_axis on each axis, the
+// time weight L_t and the split keys.
 __device__ void setup_tail(QueryData &Q, const double eps_x[3], unsigned long long Lu, unsigned long long Lv,
                            double min_sep, double delta) {
   unsigned long long Lt = 0;
 #pragma unroll
   for (int x = 0; x < 3; ++x) {
-    const double eps = eps_x[x];
-    double e = min_sep == 0.0 ? eps : __dadd_rn(eps, min_sep);   // eps + 0 is eps (eps > 0)
-    e = __longlong_as_double(__double_as_longlong(e) + 1);       // one ulp up
-    Q.ebox_p[x] = f64_ord(e);
-    Q.ebox_n[x] = f64_ord(-e);
-    // FP32 filter bounds (derivations at inclusion32).  With S the sum over
-    // the three vectors of |c0| + |dc| on this axis, the FP32 and FP64 hulls
-    // are less than e32 = 8 * 2^-24 * max(S, 2^-100) apart, and the FP64 hull
-    // is within e64 = 4 * 2^-53 S (+ 2^-1060 for subnormals) of R, the hull
-    // evaluated exactly from c0 and dc.  A decision taken on the FP32 hull must
-    // hold for the FP64 hull:
-    //   tm = e + eps + e32  (beyond it, the FP64 hull misses or sticks out of C;
-    //                        eps is spare margin)
-    //   wn = (delta (1 + 2^-50) + 2 eps + 2 e32)(1 + 2^-23)  (an FP32 width at or
-    //        above it means an FP64 width at or above delta)
-    //   tn = e - e64, rounded down  (an upper bound of R's low end at or below
-    //        it means the FP64 low end is at most e: no miss on that side)
-    // (all in single precision, every operation rounded toward the safe side,
-    // so each threshold is at least (tn: at most) its exact value; S from
-    // |c0| <= |float(c0)| + cc0-term; delta (1 + 2^-50) is bounded by
-    // delta (1 + 2^-23); 2^-149 stands in for 2^-1060)
-    float s32 = 0.f, cc0 = 0.f, cdc = 0.f;
+    const double c0[3] = {Q.c0[0][x], Q.c0[1][x], Q.c0[2][x]}, dc[3] = {Q.dc[0][x], Q.dc[1][x], Q.dc[2][x]};
+    AxisSetup o;
+    setup_axis(o, c0, dc, eps_x[x], min_sep, delta);
+    Q.ebox_p[x] = f64_ord(o.e);
+    Q.ebox_n[x] = f64_ord(-o.e);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const float cf = d2f_near(Q.c0[j][x]), df = d2f_near(Q.dc[j][x]);
-      const float ec = to_float_error(Q.c0[j][x]), ed = to_float_error(Q.dc[j][x]);
-      Q.c0f[j][x] = cf;
-      Q.dcf[j][x] = df;
-      cc0 = __fadd_ru(cc0, ec);
-      cdc = __fadd_ru(cdc, ed);
-      s32 = __fadd_ru(s32, __fadd_ru(fabsf(cf), ec));
-      s32 = __fadd_ru(s32, __fadd_ru(fabsf(df), ed));
+      Q.c0f[j][x] = o.c0f[j];
+      Q.dcf[j][x] = o.dcf[j];
     }
-    Q.cc0[x] = cc0;
-    Q.cdc[x] = cdc;
-    s32 = fmaxf(s32, 0x1p-100f);
-    const float e32 = __fmul_ru(s32, 8.0f * 0x1p-24f);
-    const float eps32 = d2f_up(eps), e_32 = d2f_up(e);
-    const float e64 = __fmaf_ru(s32, 0x1p-51f, 0x1p-149f);
-    Q.tn[x] = __fsub_rd(d2f_down(e), e64);
-    Q.tm[x] = __fadd_ru(__fadd_ru(e_32, eps32), e32);
-    const float d32 = __fmul_ru(d2f_up(delta), 1.0f + 0x1p-23f);
-    const float wn = __fadd_ru(__fadd_ru(d32, __fmul_ru(2.0f, eps32)), __fmul_ru(2.0f, e32));
-    Q.wn[x] = __fmul_ru(wn, 1.0f + 0x1p-23f);
-    double st = __dadd_rn(dabs_int(Q.dc[0][x]), dabs_int(Q.dc[1][x]));
-    st = __dadd_rn(st, dabs_int(Q.dc[2][x]));
-    const unsigned long long sb = dbits(st);
-    Lt = sb > Lt ? sb : Lt;
+    Q.cc0[x] = o.cc0;
+    Q.cdc[x] = o.cdc;
+    Q.tn[x] = o.tn;
+    Q.tm[x] = o.tm;
+    Q.wn[x] = o.wn;
+    Lt = o.st > Lt ? o.st : Lt;
   }
-  const unsigned long long kFloor = 0x0DF0000000000000ull;  // 2^-800
-  Q.K[0] = Lt < kFloor ? 0 : Lt;
-  Q.K[1] = Lu < kFloor ? 0 : Lu;
-  Q.K[2] = Lv < kFloor ? 0 : Lv;
+  Q.K[0] = Lt < kKeyFloor ? 0 : Lt;
+  Q.K[1] = Lu < kKeyFloor ? 0 : Lu;
+  Q.K[2] = Lv < kKeyFloor ? 0 : Lv;
 }
 
 // Bits of max over axes and t in {0, 1} of |c0 + t dc| for one vector (the
@@ -276,79 +304,6 @@ __device__ __forceinline__ void store2(double *p, double a, double b) { *(double
 
 __device__ __forceinline__ double dmax_pos(double a, double b) {   // both > 0
   return dbits(a) > dbits(b) ? a : b;
-}
-
-// Query set-up from the per-primitive records: only the vector w = P - T0
-// (vertex-face) or A0 - B0 (edge-edge) and the time weight L_t are computed
-// here; the edge vectors, eps and L_u, L_v come from the primitives.
-__device__ void setup_query_prims(QueryData &Q, bool &vf, int64_t q, const NarrowArgs &A, int &first_vertex) {
-  const double *__restrict__ P = A.prims;
-  double X0[3], X1[3], Y0[3], Y1[3], eps[3];
-  unsigned long long Lu, Lv;
-  if (q < A.n_vf) {
-    vf = true;
-    const int v = __ldg(&A.vf[2 * q]), f = __ldg(&A.vf[2 * q + 1]);
-    const int t0 = __ldg(&A.F[3 * (int64_t)f]);
-    first_vertex = v;
-    load_pos(A.V0, A.V1, A.nV, v, X0, X1);
-    load_pos(A.V0, A.V1, A.nV, t0, Y0, Y1);
-    const double *rv = P + kVertWords * (int64_t)v;
-    const double *rf = P + kVertWords * A.nV + kEdgeWords * A.nE + kFaceWords * (int64_t)f;
-    double w[kFaceWords];
-#pragma unroll
-    for (int k = 0; k < kFaceWords / 2; ++k) {
-      const double2 t = __ldg((const double2 *)rf + k);
-      w[2 * k] = t.x;
-      w[2 * k + 1] = t.y;
-    }
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      Q.c0[1][x] = w[x];
-      Q.dc[1][x] = w[3 + x];
-      Q.c0[2][x] = w[6 + x];
-      Q.dc[2][x] = w[9 + x];
-      eps[x] = dmax_pos(__ldg(&rv[x]), w[12 + x]);
-    }
-    Lu = dbits(w[15]);
-    Lv = dbits(w[16]);
-  } else {
-    vf = false;
-    const int64_t r = q - A.n_vf;
-    const int a = __ldg(&A.ee[2 * r]), b = __ldg(&A.ee[2 * r + 1]);
-    const int a0 = __ldg(&A.E[2 * (int64_t)a]), b0 = __ldg(&A.E[2 * (int64_t)b]);
-    first_vertex = a0;
-    load_pos(A.V0, A.V1, A.nV, a0, X0, X1);
-    load_pos(A.V0, A.V1, A.nV, b0, Y0, Y1);
-    const double *ra = P + kVertWords * A.nV + kEdgeWords * (int64_t)a;
-    const double *rb = P + kVertWords * A.nV + kEdgeWords * (int64_t)b;
-    double wa[kEdgeWords], wb[kEdgeWords];
-#pragma unroll
-    for (int k = 0; k < kEdgeWords / 2; ++k) {
-      const double2 ta = __ldg((const double2 *)ra + k), tb = __ldg((const double2 *)rb + k);
-      wa[2 * k] = ta.x;
-      wa[2 * k + 1] = ta.y;
-      wb[2 * k] = tb.x;
-      wb[2 * k + 1] = tb.y;
-    }
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      Q.c0[1][x] = wa[x];
-      Q.dc[1][x] = wa[3 + x];
-      Q.c0[2][x] = wb[x];
-      Q.dc[2][x] = wb[3 + x];
-      eps[x] = dmax_pos(wa[6 + x], wb[6 + x]);
-    }
-    Lu = dbits(wa[9]);
-    Lv = dbits(wb[9]);
-  }
-  double c0[3], dc[3];
-  vec_of(X0, X1, Y0, Y1, c0, dc);   // w = P - T0 or A0 - B0
-#pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    Q.c0[0][x] = c0[x];
-    Q.dc[0][x] = dc[x];
-  }
-  setup_tail(Q, eps, Lu, Lv, A.min_sep, A.delta);
 }
 
 // Split rule (reading): axis with the largest L_k * 2^-l_k, ties t, u, v;
@@ -766,47 +721,14 @@ __device__ __forceinline__ void query_ids(int64_t q, int64_t n_vf, const int32_t
 }
 
 // Query records (the paper's CD step, Section "Broad-Phase", computed once per
-// query in a dense pass): the set-up of setup_query stored as structure of
-// arrays, 24 words per query -- c0[3][3], dc[3][3], the error box e[3] (as a
-// double) and the split keys K[3]; bit 63 of K[0] marks a vertex-face query.
+// query in a dense pass, prepare_record): the set-up of setup_query stored as
+// structure of arrays with stride rec_stride -- 24 words per query, c0[3][3],
+// dc[3][3] (word 3j + x and 9 + 3j + x), the error box e[3] (as a double, word
+// 18 + x) and the split keys K[3] (words 21-23; bit 63 of K[0] marks a
+// vertex-face query) -- then 33 floats: c0f, dcf of vector j on axis x at
+// 2 (3j + x) and 2 (3j + x) + 1, and per axis tn, tm, wn, cc0, cdc at
+// 18 + 5x ... 22 + 5x.
 constexpr int kRecWords = 24;
-
-__device__ __forceinline__ void store_record(const QueryData &Q, bool vf, unsigned long long *rec, int64_t stride,
-                                             int64_t q) {
-  int w = 0;
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-#pragma unroll
-    for (int x = 0; x < 3; ++x) rec[(w++) * stride + q] = dbits(Q.c0[j][x]);
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-#pragma unroll
-    for (int x = 0; x < 3; ++x) rec[(w++) * stride + q] = dbits(Q.dc[j][x]);
-#pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    // ebox_p is the ordered key of a positive double: its bits
-    rec[(w++) * stride + q] = (unsigned long long)Q.ebox_p[x];
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) rec[(w++) * stride + q] = Q.K[k] | (k == 0 && vf ? (1ull << 63) : 0ull);
-  float *r32 = (float *)(rec + kRecWords * stride);
-  int f = 0;
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      r32[(f++) * stride + q] = Q.c0f[j][x];
-      r32[(f++) * stride + q] = Q.dcf[j][x];
-    }
-#pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    r32[(f++) * stride + q] = Q.tn[x];
-    r32[(f++) * stride + q] = Q.tm[x];
-    r32[(f++) * stride + q] = Q.wn[x];
-    r32[(f++) * stride + q] = Q.cc0[x];
-    r32[(f++) * stride + q] = Q.cdc[x];
-  }
-}
 
 __device__ __forceinline__ void load_record(QueryData &Q, bool &vf, const unsigned long long *__restrict__ rec,
                                             int64_t stride, int64_t q) {
@@ -1839,6 +1761,78 @@ __global__ void k_prepare_prims(NarrowArgs A) {
   }
 }
 
+// The record of query q from its primitives' records and the two vertices of
+// w (the vector P - T0 or A0 - B0; the edge vectors, eps and L_u, L_v come
+// from the primitives), written axis by axis so that only one axis's values
+// are live at a time: the same operations on the same operands as
+// setup_query + setup_tail, so every word is bit-identical.
+__device__ __forceinline__ void prepare_record(const NarrowArgs &A, int64_t q, int &first_vertex) {
+  const double *__restrict__ P = A.prims;
+  const int64_t S = A.rec_stride;
+  unsigned long long *__restrict__ rec = A.qrec;
+  float *__restrict__ r32 = (float *)(A.qrec + kRecWords * S);
+  const double *r1, *r2, *e1, *e2;   // vectors 1, 2 (c0 at [0, 3), dc at [3, 6)) and their eps words
+  int xi, yi;                        // w = X - Y
+  unsigned long long Lu, Lv;
+  const bool vf = q < A.n_vf;
+  if (vf) {
+    const int v = __ldg(&A.vf[2 * q]), f = __ldg(&A.vf[2 * q + 1]);
+    xi = v;
+    yi = __ldg(&A.F[3 * (int64_t)f]);
+    const double *rf = P + kVertWords * A.nV + kEdgeWords * A.nE + kFaceWords * (int64_t)f;
+    r1 = rf;
+    r2 = rf + 6;
+    e1 = P + kVertWords * (int64_t)v;
+    e2 = rf + 12;
+    Lu = dbits(__ldg(&rf[15]));
+    Lv = dbits(__ldg(&rf[16]));
+  } else {
+    const int64_t r = q - A.n_vf;
+    const int a = __ldg(&A.ee[2 * r]), b = __ldg(&A.ee[2 * r + 1]);
+    xi = __ldg(&A.E[2 * (int64_t)a]);
+    yi = __ldg(&A.E[2 * (int64_t)b]);
+    r1 = P + kVertWords * A.nV + kEdgeWords * (int64_t)a;
+    r2 = P + kVertWords * A.nV + kEdgeWords * (int64_t)b;
+    e1 = r1 + 6;
+    e2 = r2 + 6;
+    Lu = dbits(__ldg(&r1[9]));
+    Lv = dbits(__ldg(&r2[9]));
+  }
+  first_vertex = xi;
+  unsigned long long Lt = 0;
+#pragma unroll 1
+  for (int x = 0; x < 3; ++x) {
+    const double X0 = __ldg(&A.V0[x * A.nV + xi]), X1 = __ldg(&A.V1[x * A.nV + xi]);
+    const double Y0 = __ldg(&A.V0[x * A.nV + yi]), Y1 = __ldg(&A.V1[x * A.nV + yi]);
+    double c0[3], dc[3];
+    c0[0] = __dsub_rn(X0, Y0);
+    dc[0] = __dsub_rn(__dsub_rn(X1, Y1), c0[0]);
+    c0[1] = __ldg(&r1[x]);
+    dc[1] = __ldg(&r1[3 + x]);
+    c0[2] = __ldg(&r2[x]);
+    dc[2] = __ldg(&r2[3 + x]);
+    AxisSetup o;
+    setup_axis(o, c0, dc, dmax_pos(__ldg(&e1[x]), __ldg(&e2[x])), A.min_sep, A.delta);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      rec[(3 * j + x) * S + q] = dbits(c0[j]);
+      rec[(9 + 3 * j + x) * S + q] = dbits(dc[j]);
+      r32[(2 * (3 * j + x)) * S + q] = o.c0f[j];
+      r32[(2 * (3 * j + x) + 1) * S + q] = o.dcf[j];
+    }
+    rec[(18 + x) * S + q] = dbits(o.e);   // (e > 0: its ordered key is its bits)
+    r32[(18 + 5 * x) * S + q] = o.tn;
+    r32[(19 + 5 * x) * S + q] = o.tm;
+    r32[(20 + 5 * x) * S + q] = o.wn;
+    r32[(21 + 5 * x) * S + q] = o.cc0;
+    r32[(22 + 5 * x) * S + q] = o.cdc;
+    Lt = o.st > Lt ? o.st : Lt;
+  }
+  rec[21 * S + q] = (Lt < kKeyFloor ? 0ull : Lt) | (vf ? (1ull << 63) : 0ull);
+  rec[22 * S + q] = Lu < kKeyFloor ? 0ull : Lu;
+  rec[23 * S + q] = Lv < kKeyFloor ? 0ull : Lv;
+}
+
 // One thread per query: the query's set-up from its primitives' records
 // (k_prepare_prims) and two vertices, stored as a record, so that the narrow
 // kernel's lanes set up a unit from coalesced loads with no FP64 work.
@@ -1851,11 +1845,8 @@ __global__ void k_prepare_queries(NarrowArgs A) {
   }
   const int64_t nq = A.n_vf + A.n_ee;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
-    bool vf;
-    QueryData Q;
     int v0;
-    setup_query_prims(Q, vf, q, A, v0);
-    store_record(Q, vf, A.qrec, A.rec_stride, q);
+    prepare_record(A, q, v0);
     if (A.n_scenes > 0) A.qsid[q] = scene_of(A.voff, A.n_scenes, v0);
   }
 }
