@@ -159,7 +159,7 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   size_t o_k0 = take(capc * 8), o_k1 = take(capc * 8), o_v0 = take(capc * 4), o_v1 = take(capc * 4);
   size_t o_sortw = take(sort_work_bytes(capc));
   size_t o_salo = take(cap * 4), o_sahi = take(capc * 4);
-  size_t o_soth = take(capc * sizeof(float4)), o_svid = take(capc * sizeof(int4));
+  size_t o_soth = take(capc * sizeof(float4)), o_svid = take(capc * sizeof(int4)), o_stag = take(capc);
   size_t o_part = take(kStatWords * nbuild * sizeof(float));
   size_t o_salo64 = take(cap * 8), o_sahi64 = take(cap * 8), o_soth64 = take(2 * cap * sizeof(longlong2));
   size_t o_clocal = take(cap * 4), o_cblk = take((cdiv(cap, kCopyBlock) + 1) * 8);
@@ -184,6 +184,7 @@ int ensure_broad(ccd_ctx *c, int64_t nB) {
   B.s_ahi = (float *)(m + o_sahi);
   B.s_oth = (float4 *)(m + o_soth);
   B.s_vid = (int4 *)(m + o_svid);
+  B.s_tag = (uint8_t *)(m + o_stag);
   B.partials = (float *)(m + o_part);
   B.s_alo64 = (long long *)(m + o_salo64);
   B.s_ahi64 = (long long *)(m + o_sahi64);
@@ -477,6 +478,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   A.s_ahi = B.s_ahi;
   A.s_oth = B.s_oth;
   A.s_vid = B.s_vid;
+  A.s_tag = B.s_tag;
   A.s_alo64 = B.s_alo64;
   A.s_ahi64 = B.s_ahi64;
   A.s_oth64 = B.s_oth64;
@@ -1370,9 +1372,10 @@ int ccd_get_memory_model(const ccd_opts *o, ccd_memory_model *m) {
   if (o) opts = *o;
   // per box, as laid out by ensure_broad: FP32 and FP64 extents, vertex ids,
   // sort keys and values, the sort's look-back states (8 passes x 2 KB per
-  // 4096 keys) and the sorted arrays for 3 copies per box (strip sweep), the
-  // one-list sorted arrays, copy offsets; plus the scene index
-  m->bytes_per_box = 24 + 48 + 16 + 3 * (16 + 8) + 3 * 4 + 4 + 3 * (4 + 16 + 16) + (8 + 8 + 32) + 4 + 4;
+  // 4096 keys) and the sorted arrays (with the 1-byte tag) for 3 copies per
+  // box (strip sweep), the one-list sorted arrays, copy offsets; plus the
+  // scene index
+  m->bytes_per_box = 24 + 48 + 16 + 3 * (16 + 8) + 3 * 4 + 4 + 3 * (4 + 16 + 16 + 1) + (8 + 8 + 32) + 4 + 4;
   // and the narrow phase's per-primitive set-up record (at most a face's)
   m->bytes_per_box += narrow_prim_words(0, 0, 1) * 8;
   // per pair slot: the pair (8), two candidate slots (16), and the narrow

@@ -795,6 +795,8 @@ __global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, cons
     const uint32_t f1 = fallback || (int)(cell % p.ncell[1]) == strip_of(lo2, p, 1);
     const int4 v = B.vid[b];
     B.s_vid[i] = make_int4(v.x, v.y, v.z, (int)((uint32_t)b | (f0 << 31) | (f1 << 30)));
+    // kind from the padding: a vertex box has one vertex, an edge two, a face three
+    B.s_tag[i] = (uint8_t)((v.y >= 0) + (v.z >= 0) + (f1 << 2) + (f0 << 3));
   }
 }
 
@@ -1180,14 +1182,22 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
     const int ki = box_kind(vi.w, A.nV, A.nE);
     // the copy's range (i, end), 4 copies a step: neighbouring lanes read
     // neighbouring copies, so the loads coalesce and mostly hit L1; ids are
-    // loaded for overlapping pairs only, one per lane per round
+    // loaded only for pairs that pass the tests on extents, kinds and cells
+    // (one per lane per round)
     for (int64_t j0 = i + 1; __any_sync(0xFFFFFFFFu, j0 < end); j0 += 4) {
       unsigned hits = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (j0 + u < end) {
+          // overlap on the two cell axes, a vertex-face or edge-edge pair
+          // (kinds 0 + 2 or 1 + 1) and the one-cell reporting rule, before
+          // the copy's ids are read
           const float4 oj = A.s_oth[j0 + u];
-          hits |= ((oj.x <= oi.y) & (oi.x <= oj.y) & (oj.z <= oi.w) & (oi.z <= oj.w)) ? 1u << u : 0u;
+          const unsigned tj = A.s_tag[j0 + u];
+          hits |= ((oj.x <= oi.y) & (oi.x <= oj.y) & (oj.z <= oi.w) & (oi.z <= oj.w) &
+                   ((unsigned)ki + (tj & 3u) == 2u) & ((fi | (tj >> 2)) == 3u))
+                      ? 1u << u
+                      : 0u;
         }
       }
       while (__any_sync(0xFFFFFFFFu, hits)) {

@@ -163,6 +163,7 @@ struct BroadBufs {
   float *s_alo, *s_ahi;          // [nB]
   float4 *s_oth;                 // [nB] (lo1, hi1, lo2, hi2)
   int4 *s_vid;                   // [nB]
+  uint8_t *s_tag;                // [copies] cell sweep: box kind | first-cell flags << 2
   float *partials;               // [kStatWords * nBuildBlocks]
   // FP64 form: sorted ordered-int64 extents
   long long *s_alo64, *s_ahi64;  // [nB]
@@ -266,6 +267,7 @@ struct SweepArgs {
   const long long *s_alo64, *s_ahi64;
   const longlong2 *s_oth64;
   const int4 *s_vid;
+  const uint8_t *s_tag;          // cell sweep: kind (0 vertex, 1 edge, 2 face) | first-cell flags << 2
   const long long *lo64, *hi64;  // [3][nB] by box id
   int32_t *vf_out, *ee_out;
   int64_t vf_cap, ee_cap;
