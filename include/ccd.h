@@ -359,15 +359,18 @@ int ccd_selftest_unfinished_work(ccd_ctx *ctx, int32_t *status, void *stream);
  * sorted by their minimum; here the cell-and-minimum keys of the cell sweep):
  * sorts n (key, value) pairs in place, stably, by the low key_bits bits of
  * the key (0: all; key_bytes 4 or 8), with the library's kernels -- one
- * counting pass and one pass per 8-bit digit.  keys (n x key_bytes) and vals
- * (n x uint32) are device arrays.  n_cap >= n sizes the launch; with
- * n_cap > n the count is read from device memory, as the broad phase does.
+ * counting pass and one pass per 8-bit digit.  Passes of a digit that every
+ * key shares are skipped two at a time, or (skip_all != 0, as the cell sort
+ * does) all of them, with the result's buffers named on the device.  keys
+ * (n x key_bytes) and vals (n x uint32) are device arrays.  n_cap >= n sizes
+ * the launch; with n_cap > n the count is read from device memory, as the
+ * broad phase does.
  * Allocates and frees its own buffers.  *status (host) receives the device
  * status (CCD_OK, or CCD_ETIMEOUT if a cross-tile wait ran out).  Synchronous
  * on `stream`.  Returns CCD_OK, CCD_EINVAL (bad sizes, n_cap >= 2^32),
  * CCD_ENOMEM or CCD_ECUDA. */
-int ccd_selftest_radix_sort(ccd_ctx *ctx, int key_bytes, int key_bits, int64_t n, int64_t n_cap, void *keys,
-                            uint32_t *vals, int32_t *status, void *stream);
+int ccd_selftest_radix_sort(ccd_ctx *ctx, int key_bytes, int key_bits, int64_t n, int64_t n_cap, int skip_all,
+                            void *keys, uint32_t *vals, int32_t *status, void *stream);
 
 /* Human-readable text of a CCD_* status (static storage). */
 const char *ccd_status_str(int status);

@@ -129,8 +129,8 @@ def lib():
     L.ccd_status_async.restype = ctypes.c_int
     L.ccd_selftest_unfinished_work.argtypes = [P, ctypes.POINTER(ctypes.c_int32), P]
     L.ccd_selftest_unfinished_work.restype = ctypes.c_int
-    L.ccd_selftest_radix_sort.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, P, P,
-                                          ctypes.POINTER(ctypes.c_int32), P]
+    L.ccd_selftest_radix_sort.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_int32), P]
     L.ccd_selftest_radix_sort.restype = ctypes.c_int
     L.ccd_get_memory_model.argtypes = [ctypes.POINTER(ccd_opts), ctypes.POINTER(ccd_memory_model)]
     L.ccd_get_memory_model.restype = ctypes.c_int
@@ -308,16 +308,18 @@ def ccd_selftest_unfinished_work(ctx, stream=None) -> int:
     return st.value
 
 
-def ccd_selftest_radix_sort(ctx, keys, vals, key_bits=0, n_cap=None, stream=None) -> int:
+def ccd_selftest_radix_sort(ctx, keys, vals, key_bits=0, n_cap=None, skip_all=False, stream=None) -> int:
     """Sort device tensors keys (int32/uint32 or int64/uint64, n) and vals
     (int32/uint32, n) in place with the broad phase's radix sort, stably by
     the low key_bits bits (0: all); n_cap > n passes the count through
-    device memory.  Returns the device status; synchronous."""
+    device memory; skip_all skips every pass of a digit all keys share (the
+    cell sort's mode).  Returns the device status; synchronous."""
     n = keys.numel()
     assert vals.numel() == n and keys.is_contiguous() and vals.is_contiguous() and vals.element_size() == 4
     st = ctypes.c_int32()
     _check(lib().ccd_selftest_radix_sort(ctx, keys.element_size(), key_bits, n, n if n_cap is None else n_cap,
-                                         _ptr(keys), _ptr(vals), ctypes.byref(st), _stream(stream)),
+                                         1 if skip_all else 0, _ptr(keys), _ptr(vals), ctypes.byref(st),
+                                         _stream(stream)),
            "ccd_selftest_radix_sort")
     return st.value
 

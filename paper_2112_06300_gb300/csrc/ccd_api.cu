@@ -439,10 +439,14 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     k_scan_copies<<<1, 1024, 0, s>>>(nblk, nB, B, c->ctl);
     k_expand_copies<<<grid, 256, 0, s>>>(nB, B, c->ctl, (unsigned long long *)B.keys[0], B.vals[0]);
     const int bits = sc.n > 0 ? 48 + sbits : 56;   // cell index: 16 bits batched, 24 bits alone
-    const int cur = radix_sort(B.keys, B.vals, 8, B.cap_copies, c->sortw, s, &c->ctl->status, bits, &c->ctl->n_copies);
+    // every pass of a digit the keys share is skipped; the gather finds the
+    // result's buffers on the device and leaves the sorted keys in keys[0]
+    const int *sel = nullptr;
+    radix_sort(B.keys, B.vals, 8, B.cap_copies, c->sortw, s, &c->ctl->status, bits, &c->ctl->n_copies, &sel);
     const int cgrid = (int)std::min<int64_t>(cdiv(B.cap_copies, 256), (int64_t)c->sm_count * 8);
-    k_gather_copies<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, (const unsigned long long *)B.keys[cur], B.vals[cur]);
-    s_key = (const unsigned long long *)B.keys[cur];
+    k_gather_copies<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, (unsigned long long *)B.keys[0],
+                                          (const unsigned long long *)B.keys[1], B.vals[0], B.vals[1], sel);
+    s_key = (const unsigned long long *)B.keys[0];
     sort_passes = (bits + 7) / 8;
     extra = 2;
   } else if (sc.n > 0) {
@@ -1324,8 +1328,8 @@ int ccd_selftest_unfinished_work(ccd_ctx *c, int32_t *status, void *stream) {
   return CCD_OK;
 }
 
-int ccd_selftest_radix_sort(ccd_ctx *c, int key_bytes, int key_bits, int64_t n, int64_t n_cap, void *keys,
-                            uint32_t *vals, int32_t *status, void *stream) {
+int ccd_selftest_radix_sort(ccd_ctx *c, int key_bytes, int key_bits, int64_t n, int64_t n_cap, int skip_all,
+                            void *keys, uint32_t *vals, int32_t *status, void *stream) {
   if (!c || !status || (key_bytes != 4 && key_bytes != 8) || key_bits < 0 || key_bits > 8 * key_bytes || n < 0 ||
       n_cap < n || n_cap >= (1ll << 32) || (n > 0 && (!keys || !vals)))
     return CCD_EINVAL;
@@ -1351,9 +1355,13 @@ int ccd_selftest_radix_sort(ccd_ctx *c, int key_bytes, int key_bits, int64_t n, 
     rc = CCD_ECUDA;
   } else {
     k_reset_status<<<1, 1, 0, s>>>(c->ctl);
+    const int *sel = nullptr;
     cur = radix_sort(kb, vb, key_bytes, n_cap, sort_work_at(wm), s, &c->ctl->status, key_bits,
-                     n_cap > n ? n_dev : nullptr);
-    if ((n > 0 && (cudaMemcpyAsync(keys, kb[cur], n * key_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                     n_cap > n ? n_dev : nullptr, skip_all ? &sel : nullptr);
+    if (sel && (cudaMemcpyAsync(&cur, sel, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess))
+      rc = CCD_ECUDA;
+    else if ((n > 0 && (cudaMemcpyAsync(keys, kb[cur], n * key_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
                    cudaMemcpyAsync(vals, vb[cur], n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)) ||
         cudaMemcpyAsync(&h, &c->ctl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -409,7 +409,8 @@ __device__ __forceinline__ unsigned same_digit_lanes(uint32_t d, unsigned valid)
 
 template <typename K>
 __global__ void __launch_bounds__(kOsThreads)
-k_sort_hist(const K *__restrict__ keys, int64_t n, const unsigned long long *n_dev, int passes, SortWork W) {
+k_sort_hist(const K *__restrict__ keys, int64_t n, const unsigned long long *n_dev, int passes, int pair_skip,
+            SortWork W) {
   __shared__ uint32_t h[kMaxSortPasses][256];
   __shared__ uint32_t wsum[kOsWarps];
   __shared__ int last;
@@ -480,7 +481,7 @@ k_sort_hist(const K *__restrict__ keys, int64_t n, const unsigned long long *n_d
         skip_last = p;
       }
     }
-    if (nskip & 1) P->run[skip_last] = 1;   // skip in pairs: the result's buffers stay those of every pass run
+    if (pair_skip && (nskip & 1)) P->run[skip_last] = 1;   // in pairs: the result stays where every pass puts it
     P->in[0] = 0;
     for (int p = 0; p < passes; ++p) {
       P->in[p + 1] = P->in[p] ^ P->run[p];
@@ -604,24 +605,25 @@ int64_t sort_tiles(int64_t n) { return std::max<int64_t>(1, (n + kOsTile - 1) / 
 
 template <typename K>
 int radix_sort_t(K *keys[2], uint32_t *vals[2], int64_t n, const SortWork &W, cudaStream_t s, int *status,
-                 int key_bits, const unsigned long long *n_dev) {
+                 int key_bits, const unsigned long long *n_dev, const int **result_sel) {
   const int64_t ntiles = sort_tiles(n);
   const int bits = key_bits > 0 ? key_bits : (int)(8 * sizeof(K));
   const int passes = (bits + 7) / 8;
-  k_sort_hist<K><<<(unsigned)ntiles, kOsThreads, 0, s>>>(keys[0], n, n_dev, passes, W);
+  if (result_sel) *result_sel = &W.plan->in[passes];
+  k_sort_hist<K><<<(unsigned)ntiles, kOsThreads, 0, s>>>(keys[0], n, n_dev, passes, result_sel ? 0 : 1, W);
   for (int p = 0; p < passes; ++p)
     k_sort_pass<K><<<(unsigned)ntiles, kOsThreads, 0, s>>>(keys[0], keys[1], vals[0], vals[1], p, W, status);
   return passes & 1;
 }
 
 int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, const SortWork &W, cudaStream_t s,
-               int *status, int key_bits, const unsigned long long *n_dev) {
+               int *status, int key_bits, const unsigned long long *n_dev, const int **result_sel) {
   if (key_bytes == 4) {
     uint32_t *k[2] = {(uint32_t *)keys[0], (uint32_t *)keys[1]};
-    return radix_sort_t<uint32_t>(k, vals, n, W, s, status, key_bits, n_dev);
+    return radix_sort_t<uint32_t>(k, vals, n, W, s, status, key_bits, n_dev, result_sel);
   }
   unsigned long long *k[2] = {(unsigned long long *)keys[0], (unsigned long long *)keys[1]};
-  return radix_sort_t<unsigned long long>(k, vals, n, W, s, status, key_bits, n_dev);
+  return radix_sort_t<unsigned long long>(k, vals, n, W, s, status, key_bits, n_dev, result_sel);
 }
 
 __global__ void k_gather_sorted64(int64_t nB, const uint32_t *__restrict__ perm, const DevCtl *ctl, BroadBufs B) {
@@ -776,14 +778,20 @@ __global__ void k_expand_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, unsi
 
 // Copies in sorted order: maximum on the sweep axis, extents on the strip
 // axis and the third axis, vertex ids and box id; bit 31 of the box id marks
-// the copy in the box's first strip (the reporting rule of the sweep).
-__global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, const unsigned long long *keys,
-                                const uint32_t *perm) {
+// the copy in the box's first strip (the reporting rule of the sweep).  The
+// sort leaves its result in buffers *sel (read on the device: it skips the
+// passes of digits that every key shares); the sorted keys end in keys0.
+__global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, unsigned long long *keys0,
+                                const unsigned long long *keys1, const uint32_t *perm0, const uint32_t *perm1,
+                                const int *sel) {
   const int64_t n = (int64_t)ctl->n_copies;
   const bool fallback = ctl->strip_fallback != 0;
+  const bool in1 = *sel != 0;
+  const uint32_t *perm = in1 ? perm1 : perm0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = perm[i];
-    const unsigned long long key = keys[i];
+    const unsigned long long key = in1 ? keys1[i] : keys0[i];
+    if (in1) keys0[i] = key;
     const int sid = B.n_scenes > 0 ? (int)(key >> 48) : 0;
     const uint32_t cell = B.n_scenes > 0 ? (uint32_t)((key >> 32) & 0xFFFFu) : (uint32_t)(key >> 32);
     const StripParam p = B.sparam[sid];

@@ -211,8 +211,9 @@ __global__ void k_count_copies(int64_t nB, BroadBufs B, DevCtl *ctl);
 __global__ void k_scan_copies(int nblk, int64_t nB, BroadBufs B, DevCtl *ctl);
 __global__ void k_expand_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, unsigned long long *keys,
                                 uint32_t *vals);
-__global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, const unsigned long long *keys,
-                                const uint32_t *perm);
+__global__ void k_gather_copies(int64_t nB, BroadBufs B, const DevCtl *ctl, unsigned long long *keys0,
+                                const unsigned long long *keys1, const uint32_t *perm0, const uint32_t *perm1,
+                                const int *sel);
 __global__ void k_make_keys(int64_t nB, const float *lo32, const DevCtl *ctl, uint32_t *keys, uint32_t *vals);
 __global__ void k_axis_select_scenes(BroadBufs B);
 __global__ void k_make_keys_scenes(int64_t nB, BroadBufs B, unsigned long long *keys, uint32_t *vals);
@@ -225,7 +226,11 @@ __global__ void k_make_keys64(int64_t nB, const long long *lo64, const DevCtl *c
 // n_dev (optional): device count, read by the kernels, of the keys to sort
 // (at most n; grids are sized for n).  W holds at least sort_work_bytes(n)
 // bytes, zeroed once when allocated.  A look-back wait that runs out raises
-// CCD_ETIMEOUT in *status.
+// CCD_ETIMEOUT in *status.  Passes of a digit that every key shares are
+// skipped two at a time, so that the result lands where running every pass
+// puts it -- or, with result_sel, all of them: *result_sel is then set to
+// a device int naming the result's buffers (0 or 1) and the return value
+// means nothing.
 struct SortPlan {
   unsigned long long n;                         // keys sorted
   uint32_t blocks_done;                         // counting blocks finished
@@ -253,7 +258,8 @@ inline SortWork sort_work_at(void *base) {
   return W;
 }
 int radix_sort(void *keys[2], uint32_t *vals[2], int key_bytes, int64_t n, const SortWork &W, cudaStream_t s,
-               int *status, int key_bits = 0, const unsigned long long *n_dev = nullptr);
+               int *status, int key_bits = 0, const unsigned long long *n_dev = nullptr,
+               const int **result_sel = nullptr);
 __global__ void k_gather_sorted(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 __global__ void k_gather_sorted64(int64_t nB, const uint32_t *perm, const DevCtl *ctl, BroadBufs B);
 

@@ -136,8 +136,8 @@ struct AxisSetup {
 };
 
 __device__ __forceinline__ void setup_axis(AxisSetup &o, const double c0[3], const double dc[3], double eps,
-                                           double min_sep, double delta) {
-  double e = min_sep == 0.0 ? eps : __dadd_rn(eps, min_sep);   // eps + 0 is eps (eps > 0)
+                                           double min_sep, bool no_sep, double delta) {
+  double e = no_sep ? eps : __dadd_rn(eps, min_sep);   // (no_sep: min_sep == 0, and eps + 0 is eps)
   e = __longlong_as_double(__double_as_longlong(e) + 1);       // one ulp up
   o.e = e;
   // FP32 filter bounds (derivations at inclusion32).  With S the sum over
@@ -196,7 +196,7 @@ __device__ void setup_tail(QueryData &Q, const double eps_x[3], unsigned long lo
   for (int x = 0; x < 3; ++x) {
     const double c0[3] = {Q.c0[0][x], Q.c0[1][x], Q.c0[2][x]}, dc[3] = {Q.dc[0][x], Q.dc[1][x], Q.dc[2][x]};
     AxisSetup o;
-    setup_axis(o, c0, dc, eps_x[x], min_sep, delta);
+    setup_axis(o, c0, dc, eps_x[x], min_sep, min_sep == 0.0, delta);
     Q.ebox_p[x] = f64_ord(o.e);
     Q.ebox_n[x] = f64_ord(-o.e);
 #pragma unroll
@@ -1799,6 +1799,7 @@ __device__ __forceinline__ void prepare_record(const NarrowArgs &A, int64_t q, i
     Lv = dbits(__ldg(&r2[9]));
   }
   first_vertex = xi;
+  const bool no_sep = A.min_sep == 0.0;   // (one FP64 comparison per query, not per axis)
   unsigned long long Lt = 0;
 #pragma unroll 1
   for (int x = 0; x < 3; ++x) {
@@ -1812,7 +1813,7 @@ __device__ __forceinline__ void prepare_record(const NarrowArgs &A, int64_t q, i
     c0[2] = __ldg(&r2[x]);
     dc[2] = __ldg(&r2[3 + x]);
     AxisSetup o;
-    setup_axis(o, c0, dc, dmax_pos(__ldg(&e1[x]), __ldg(&e2[x])), A.min_sep, A.delta);
+    setup_axis(o, c0, dc, dmax_pos(__ldg(&e1[x]), __ldg(&e2[x])), A.min_sep, no_sep, A.delta);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       rec[(3 * j + x) * S + q] = dbits(c0[j]);

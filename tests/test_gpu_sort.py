@@ -25,12 +25,12 @@ def ctx():
     c.close()
 
 
-def run_sort(c, keys, key_bits, n_cap=None):
+def run_sort(c, keys, key_bits, n_cap=None, skip_all=False):
     n = len(keys)
     vals = np.arange(n, dtype=np.uint32)[::-1].copy()          # values: a permutation, reversed
     kd = torch.from_numpy(keys.view(np.int64 if keys.dtype.itemsize == 8 else np.int32).copy()).cuda()
     vd = torch.from_numpy(vals.view(np.int32)).cuda()
-    st = ccd.ccd_selftest_radix_sort(c.ctx, kd, vd, key_bits=key_bits, n_cap=n_cap)
+    st = ccd.ccd_selftest_radix_sort(c.ctx, kd, vd, key_bits=key_bits, n_cap=n_cap, skip_all=skip_all)
     assert st == 0
     ko = kd.cpu().numpy().view(keys.dtype)
     vo = vd.cpu().numpy().view(np.uint32)
@@ -48,16 +48,19 @@ def test_sizes(ctx, n):
     run_sort(ctx, keys, 56)
 
 
+@pytest.mark.parametrize("skip_all", [False, True])
 @pytest.mark.parametrize("high", [20, 40, 48, 56, 64])
-def test_constant_digits(ctx, high):
+def test_constant_digits(ctx, high, skip_all):
     """Keys below 2^high: digits at and above high/8 are the same for every
-    key (4, 2, 1, 0 and 0 of the 7 passes of a 56-bit sort, or of 8)."""
+    key (4, 2, 1, 0 and 0 of the 7 passes of a 56-bit sort, or of 8); those
+    passes are skipped in pairs, or all of them (the cell sort's mode, the
+    result's buffers then named on the device)."""
     rng = np.random.default_rng(high)
     n = 5 * TILE + 123
     keys = rng.integers(0, 1 << min(high, 63), n, dtype=np.uint64)
     if high == 64:
         keys = keys * np.uint64(2) + rng.integers(0, 2, n, dtype=np.uint64)
-    run_sort(ctx, keys, 0 if high == 64 else 56)
+    run_sort(ctx, keys, 0 if high == 64 else 56, skip_all=skip_all)
 
 
 def test_many_duplicates_cell_keys(ctx):
@@ -69,10 +72,12 @@ def test_many_duplicates_cell_keys(ctx):
     cell = rng.integers(0, 300, n, dtype=np.uint64)
     mn = rng.integers(0x3F000000, 0x3F000040, n, dtype=np.uint64)
     run_sort(ctx, (cell << np.uint64(32)) | mn, 56)
+    run_sort(ctx, (cell << np.uint64(32)) | mn, 56, n_cap=n + 3 * TILE, skip_all=True)
 
 
-def test_all_equal(ctx):
-    run_sort(ctx, np.full(2 * TILE + 5, 0x123456789A, dtype=np.uint64), 56)
+@pytest.mark.parametrize("skip_all", [False, True])
+def test_all_equal(ctx, skip_all):
+    run_sort(ctx, np.full(2 * TILE + 5, 0x123456789A, dtype=np.uint64), 56, skip_all=skip_all)
 
 
 @pytest.mark.parametrize("key_bits", [0, 24])
