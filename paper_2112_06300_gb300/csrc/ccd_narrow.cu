@@ -922,7 +922,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   SCN[0][tid] = SCN[1][tid] = kInfBits;
   bool have = false, fresh = false, whole = false;
   bool exhausted = false;                    // warp-uniform
-  int64_t q = 0;
+  int64_t q = -1;   // the query whose data the lane's registers and shared column hold (-1: none yet)
   Node N{0, 0, 0, 0, 0, 0};
   int depth = 0, root_depth = 0;
   // the path as bit masks over depths 1..31: pend bit d is set while the path
@@ -1168,46 +1168,56 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           const bool recv = !have && __popc(idle & lt_mask) < pairs;
           const bool give = dS > 0 && __popc(donors & lt_mask) < pairs;
           const int src = recv ? (int)__fns(donors, 0, __popc(idle & lt_mask) + 1) : lane;
+          const long long qv = __shfl_sync(FULL, (long long)q, src);
+          // A receiver whose last unit was a piece of the same query still
+          // holds that query's data in its registers and shared column (the
+          // data depend on the query only).  In the tail the lanes of a warp
+          // mostly share one long query, so the data move only when some
+          // receiver holds another query.
+          const bool move = recv && qv != q;
           __syncwarp(FULL);
-          if (recv) copy_shared(SQ, tid, (tid & ~31) | src);   // the donor's FP64 data
+          if (__any_sync(FULL, move)) {
+            if (move) copy_shared(SQ, tid, (tid & ~31) | src);   // the donor's FP64 data
 #pragma unroll
-          for (int j = 0; j < 3; ++j)
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+              for (int x = 0; x < 3; ++x) {
+                const float a = __shfl_sync(FULL, c0f[j][x], src);
+                const float b = __shfl_sync(FULL, dcf[j][x], src);
+                if (move) {
+                  c0f[j][x] = a;
+                  dcf[j][x] = b;
+                }
+              }
 #pragma unroll
             for (int x = 0; x < 3; ++x) {
-              const float a = __shfl_sync(FULL, c0f[j][x], src);
-              const float b = __shfl_sync(FULL, dcf[j][x], src);
-              if (recv) {
-                c0f[j][x] = a;
-                dcf[j][x] = b;
+              const float a = __shfl_sync(FULL, tn[x], src);
+              const float b = __shfl_sync(FULL, tm[x], src);
+              const float c = __shfl_sync(FULL, wn[x], src);
+              const unsigned long long kk = __shfl_sync(FULL, K[x], src);
+              if (move) {
+                tn[x] = a;
+                tm[x] = b;
+                wn[x] = c;
+                K[x] = kk;
               }
             }
-#pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            const float a = __shfl_sync(FULL, tn[x], src);
-            const float b = __shfl_sync(FULL, tm[x], src);
-            const float c = __shfl_sync(FULL, wn[x], src);
-            const unsigned long long kk = __shfl_sync(FULL, K[x], src);
-            if (recv) {
-              tn[x] = a;
-              tm[x] = b;
-              wn[x] = c;
-              K[x] = kk;
+            const int sidv = A.mode == 2 ? SID[(tid & ~31) + src] : 0;   // (a busy lane's entry)
+            const int vfv = __shfl_sync(FULL, (int)vf, src);
+            if (move) {
+              if (A.mode == 2) SID[tid] = sidv;
+              vf = vfv != 0;
             }
           }
           const uint64_t s0 = __shfl_sync(FULL, S.n0, src), s1 = __shfl_sync(FULL, S.n1, src),
                          s2 = __shfl_sync(FULL, S.n2, src);
           const int l0 = __shfl_sync(FULL, S.l0, src), l1 = __shfl_sync(FULL, S.l1, src),
                     l2 = __shfl_sync(FULL, S.l2, src);
-          const long long qv = __shfl_sync(FULL, (long long)q, src);
-          const int sidv = A.mode == 2 ? SID[(tid & ~31) + src] : 0;   // (a busy lane's entry)
-          const int vfv = __shfl_sync(FULL, (int)vf, src);
           const unsigned long long tqv = __shfl_sync(FULL, tq, src);
 
           if (recv) {
             q = qv;
-            if (A.mode == 2) SID[tid] = sidv;
             SCN[0][tid] = SCN[1][tid] = kInfBits;
-            vf = vfv != 0;
             N = Node{s0, s1, s2, l0, l1, l2};
             depth = root_depth = N.depth();
             pend = tright = 0;
