@@ -7,7 +7,8 @@
 //     split axis depends only on the interval's levels (see split_axis), so
 //     every node at a given depth has the same levels and the DFS needs no
 //     stack: the path is the binary expansion of the three numerators, kept
-//     as bit masks of owed siblings and split axes for depths up to 31.
+//     as bit masks of owed siblings and split axes for the 31 levels below
+//     the depth at which the lane took its unit.
 //   * Load balance at interval granularity: once every query has been
 //     claimed, idle lanes take the shallowest owed sibling of a busy lane of
 //     their warp, and every 32 x `budget` evaluations a warp hands its lanes'
@@ -403,10 +404,12 @@ __device__ __forceinline__ int shallowest_pending(const unsigned long long K[3],
   return found;
 }
 
-// shallowest_pending on the path masks of the narrow kernel (units no deeper
-// than 31): pend bit d marks an owed right sibling at depth d, (axhi, axlo)
-// bit d the axis split to reach depth d.  The owed siblings are visited from
-// the shallowest; the first that starts before `cut` is returned.
+// shallowest_pending on the path masks of the narrow kernel (units no more
+// than 31 levels below the masks' base depth; depth, root_depth and the
+// returned depth count from that base): pend bit d marks an owed right
+// sibling at depth d, (axhi, axlo) bit d the axis split to reach depth d.
+// The owed siblings are visited from the shallowest; the first that starts
+// before `cut` is returned.
 __device__ __forceinline__ int shallowest_owed(const Node &N, int depth, int root_depth, unsigned pend,
                                                unsigned axlo, unsigned axhi, unsigned long long cut, Node &S) {
   const uint64_t cut53 = ceil53(cut);
@@ -925,13 +928,19 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   int64_t q = -1;   // the query whose data the lane's registers and shared column hold (-1: none yet)
   Node N{0, 0, 0, 0, 0, 0};
   int depth = 0, root_depth = 0;
-  // the path as bit masks over depths 1..31: pend bit d is set while the path
-  // node at depth d is a left child whose right sibling is still owed, and
-  // bit d of (axhi, axlo) is the axis that was split to reach depth d; a unit
-  // that goes deeper (`deep`) backtracks by walking the path instead
+  // the path as bit masks over the 31 depths below rb, the depth at which
+  // the lane took its unit (0 for a whole query): pend bit d is set while the
+  // path node at depth rb + d is a left child whose right sibling is still
+  // owed, and bit d of (axhi, axlo) is the axis that was split to reach depth
+  // rb + d; a unit that goes deeper (`deep`) backtracks by walking the path
+  // instead.  (The long queries of a scene do most of their work 32-37
+  // levels down; the pieces other lanes take from them start well below
+  // the root, so with masks counted from their own start they stay on the
+  // mask path.)
   unsigned pend = 0, axlo = 0, axhi = 0;
-  // bit d of tright: the path node at depth d is the right child of a split
-  // along t (the path's t_lo grows exactly at those depths)
+  int rb = 0;
+  // bit d of tright: the path node at depth rb + d is the right child of a
+  // split along t (the path's t_lo grows exactly at those depths)
   unsigned tright = 0;
   bool deep = false;
   unsigned long long tq = kInfBits;          // bits of this unit's best t*
@@ -1157,8 +1166,12 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           unsigned long long c = tq;
           if (A.mode == 1) c = min(c, pf_toi_b);
           if (A.mode == 2) c = min(c, SCN[0][tid]);
-          dS = deep ? shallowest_pending(K, N, depth, root_depth, c, S)
-                    : shallowest_owed(N, depth, root_depth, pend, axlo, axhi, c, S);
+          if (deep) {
+            dS = shallowest_pending(K, N, depth, root_depth, c, S);
+          } else {
+            const int d = shallowest_owed(N, depth - rb, root_depth - rb, pend, axlo, axhi, c, S);
+            dS = d > 0 ? rb + d : 0;
+          }
         }
         const unsigned donors = __ballot_sync(FULL, dS > 0);
         const int pairs = min(__popc(donors), __popc(idle));
@@ -1219,9 +1232,9 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
             q = qv;
             SCN[0][tid] = SCN[1][tid] = kInfBits;
             N = Node{s0, s1, s2, l0, l1, l2};
-            depth = root_depth = N.depth();
+            depth = root_depth = rb = N.depth();
             pend = tright = 0;
-            deep = depth > 31;
+            deep = false;
             tq = tqv;
             cap_left = min(kBudgetWindow, A.max_iter);   // the query's shared budget, in windows
             cnt = 0;
@@ -1300,9 +1313,9 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         wn[x] = Q.wn[x];
         K[x] = Q.K[x];
       }
-      depth = root_depth = N.depth();
+      depth = root_depth = rb = N.depth();
       pend = tright = 0;
-      deep = depth > 31;
+      deep = false;
       cnt = 0;
       flags = 0;
       tq = kInfBits;
@@ -1511,8 +1524,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           N.down_left(a);
           depth += 1;
           node_done = false;
-          if (depth < 32) {
-            const unsigned bit = 1u << depth;
+          if (depth - rb < 32) {
+            const unsigned bit = 1u << (depth - rb);
             // the right child is owed unless it is already pruned (t* only
             // falls) or lies outside the vertex-face simplex
             bool owe = true;
@@ -1538,7 +1551,10 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       // jump to the deepest owed sibling: undo the splits below it per axis
       // (popcounts of the axis masks), take the right sibling, and go on
       // while the sibling is pruned or outside the simplex
-      const unsigned above_root = root_depth >= 31 ? 0u : ~0u << (root_depth + 1);
+      // (depths relative to rb)
+      const int rr = root_depth - rb;
+      const unsigned above_root = rr >= 31 ? 0u : ~0u << (rr + 1);
+      int dr = depth - rb;
       while (true) {
         const unsigned m = pend & above_root;
         if (m == 0) {
@@ -1546,9 +1562,9 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           break;
         }
         const int ds = 31 - __clz((int)m);
-        const unsigned r = (depth >= 31 ? ~0u : (2u << depth) - 1u) & (ds >= 31 ? 0u : ~0u << (ds + 1));
+        const unsigned r = (dr >= 31 ? ~0u : (2u << dr) - 1u) & (ds >= 31 ? 0u : ~0u << (ds + 1));
         const int c1 = __popc(r & axlo & ~axhi), c2 = __popc(r & axhi);
-        const int c0 = depth - ds - c1 - c2;
+        const int c0 = dr - ds - c1 - c2;
         N.n0 >>= c0;
         N.l0 -= c0;
         N.n1 >>= c1;
@@ -1557,7 +1573,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         N.l2 -= c2;
         const int a = (int)((axlo >> ds) & 1u) | ((int)((axhi >> ds) & 1u) << 1);
         N.add(a, 1);
-        depth = ds;
+        dr = ds;
+        depth = rb + ds;
         pend &= ~(~0u << ds);
         tright = (tright & ~(~0u << ds)) | (a == 0 ? 1u << ds : 0u);
         const bool pruned = s53(N.n0, N.l0) >= cut53;
@@ -1604,8 +1621,12 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
         if (want_exp) {
-          dS = deep ? shallowest_pending(K, N, depth, root_depth, cut, S)
-                    : shallowest_owed(N, depth, root_depth, pend, axlo, axhi, cut, S);
+          if (deep) {
+            dS = shallowest_pending(K, N, depth, root_depth, cut, S);
+          } else {
+            const int d = shallowest_owed(N, depth - rb, root_depth - rb, pend, axlo, axhi, cut, S);
+            dS = d > 0 ? rb + d : 0;
+          }
         }
         const unsigned xm = __ballot_sync(FULL, dS > 0);
         if (xm) {
