@@ -396,13 +396,15 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   B.s_oth64c = c->s_oth64c;
   const int nbuild = (int)cdiv(nB, kBuildThreads);
   const int grid = (int)std::min<int64_t>(cdiv(nB, 256), (int64_t)c->sm_count * 8);
-  int sort_passes = 0;
+  int sort_passes = 0;             // radix passes (one kernel each) ...
+  int n_sorts = 0;                 // ... of this many sorts (one counting kernel each)
   int extra = 0;
   int sbits = 0;   // bits of the scene index in the keys of batched scenes
   while ((1ll << sbits) < sc.n) ++sbits;
   const unsigned long long *s_key = c->s_key_last;
   if (phase & 1) {
   sort_passes = fp64 ? 8 : 4;
+  n_sorts = 1;
   mark(c, CCD_STAGE_BOXES, true, s);
   if (sc.n > 0) {
     CK(cudaMemsetAsync(c->ssum, 0, 9 * sc.n * sizeof(float), s));
@@ -432,6 +434,7 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
     const int cur2 = radix_sort(k2, v2, 4, B.cap_copies, c->sortw, s, &c->ctl->status, 24, &c->ctl->n_copies);
     k_gather_copies64<<<cgrid, 256, 0, s>>>(nB, B, c->ctl, v2[cur2]);
     sort_passes = 8 + 3;
+    n_sorts = 2;
     extra = 3;
   } else if (sweep == 0) {
     const int nblk = (int)cdiv(nB, kCopyBlock);
@@ -525,9 +528,10 @@ int launch_broad(ccd_ctx *c, const double *V0, const double *V1, int64_t nV, con
   }
   mark(c, CCD_STAGE_SWEEP, false, s);
   }
-  // reset, build, axis, keys (or count, scan, expand), passes x (hist, scan,
-  // scatter), gather, sweep (and exact filter)
-  c->n_launches += (phase & 1 ? 5 : 1) + (phase & 2 ? 1 : 0) + extra + 3 * sort_passes;
+  // reset, build, axis, keys (or count, scan, expand), per sort a counting
+  // kernel and one kernel per pass (skipped passes included: they return at
+  // once), gather, sweep (and exact filter)
+  c->n_launches += (phase & 1 ? 5 : 1) + (phase & 2 ? 1 : 0) + extra + n_sorts + sort_passes;
   CK(cudaGetLastError());
   return CCD_OK;
 }
