@@ -864,8 +864,7 @@ constexpr int kIdleRounds = 1 << 14;   // idle warp rounds before a warp retires
 // idle back-off bounds (ns): warps polling the ring more often than this
 // slow the busy warps of the tail (measured: 0.25-2 us worse, 1-32 us best)
 constexpr unsigned kNapMin = 1000, kNapMax = 32000;
-constexpr int kSteps = 3;              // depth-first steps per iteration
-constexpr int kRefresh = 3;            // iterations between reads of the shared values
+constexpr int kRefresh = 8;            // iterations between reads of the shared values
 constexpr int kDonateMin = 4;          // idle lanes a warp gathers before a round of donation
 // A query whose work is split over several units (donation, hand-off) shares
 // one iteration budget: each unit counts its evaluations in windows of at
@@ -895,9 +894,8 @@ __device__ __forceinline__ bool next_budget_window(const NarrowArgs &A, int64_t 
 
 // Control flow is warp-uniform at the loop level: refill, idling and exit are
 // decided for the whole warp (ballots and broadcasts), and the per-lane work
-// (kSteps depth-first steps) sits in structured branches, so the lanes of a
-// warp reconverge every step and the FP64 instructions of an interval issue
-// once per warp.
+// sits in structured branches, so the lanes of a warp reconverge every
+// iteration and the FP64 instructions of an interval issue once per warp.
 template <bool kRecords>
 __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   DevCtl *ctl = A.ctl;
@@ -1362,282 +1360,254 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       g_toi = wc.pf_toi;
       g_tail = wc.pf_qnext >= (unsigned long long)nq;
     }
+    unsigned long long cut = tq;
     const unsigned long long g = g_toi;
     // hand work out only once every query has been taken (idle lanes exist)
     const bool tail_phase = g_tail;
-    // kSteps depth-first steps per iteration: the warp-level work above
-    // (refill, set-up, refresh) and the hand-off below are shared by them.
-    // A step has no warp-wide operation, so lanes run their steps apart; a
-    // lane whose unit ends waits for the next iteration's refill.
-    unsigned nev = 0;          // intervals this lane evaluated in this iteration
-    bool ended = false;        // this lane's unit ended in this iteration
-#pragma unroll 1
-    for (int step = 0; step < kSteps && have; ++step) {
-      unsigned long long cut = tq;
-      if (A.mode == 1) cut = g < cut ? g : cut;
-      if (A.mode == 2) cut = min(SCN[0][tid], cut);
-      bool node_done = true;     // false when the node was split (go to its left child)
-      bool unit_end = false;
-      bool evaluate = false;
-      if (cut != cut_prev) {     // (t* changes rarely)
-        cut_prev = cut;
-        cut53 = ceil53(cut);
-      }
-      if (have) {
-        if (s53(N.n0, N.l0) >= cut53) {
-          // pruned: starts at or after the current t*
-        } else if (vf && outside_simplex(N)) {
-          // vertex-face: u_lo > 1 - v_lo, the interval lies outside the simplex
-        } else if (!(A.no_zero && N.n0 == 0) && ++cnt > cap_left && !next_budget_window(A, q, whole, cnt, cap_left)) {
-          // iteration cap: t* = min(t*, earliest left end among the live intervals)
-          unsigned long long m = dbits(dyadic(N.n0, N.l0));
-          Node W = N;
-          for (int d = depth; d > root_depth; --d) {
-            int a = last_axis(K, W);
-            if ((W.n(a) & 1) == 0) {
-              unsigned long long sb = dbits(a == 0 ? dyadic(W.n0 + 1, W.l0) : dyadic(W.n0, W.l0));
-              m = sb < m ? sb : m;
-            }
-            W.up(a);
+    if (A.mode == 1) cut = g < cut ? g : cut;
+    if (A.mode == 2) cut = min(SCN[0][tid], cut);
+    bool node_done = true;     // false when the node was split (go to its left child)
+    bool unit_end = false;
+    bool evaluate = false;
+    if (cut != cut_prev) {     // (t* changes rarely)
+      cut_prev = cut;
+      cut53 = ceil53(cut);
+    }
+    if (have) {
+      if (s53(N.n0, N.l0) >= cut53) {
+        // pruned: starts at or after the current t*
+      } else if (vf && outside_simplex(N)) {
+        // vertex-face: u_lo > 1 - v_lo, the interval lies outside the simplex
+      } else if (!(A.no_zero && N.n0 == 0) && ++cnt > cap_left && !next_budget_window(A, q, whole, cnt, cap_left)) {
+        // iteration cap: t* = min(t*, earliest left end among the live intervals)
+        unsigned long long m = dbits(dyadic(N.n0, N.l0));
+        Node W = N;
+        for (int d = depth; d > root_depth; --d) {
+          int a = last_axis(K, W);
+          if ((W.n(a) & 1) == 0) {
+            unsigned long long sb = dbits(a == 0 ? dyadic(W.n0 + 1, W.l0) : dyadic(W.n0, W.l0));
+            m = sb < m ? sb : m;
           }
-          tq = m < tq ? m : tq;
-          if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);       // (modes 1, 2: as an accept)
-          if (A.mode == 2) atomicMin(&A.toi_scene[SID[tid]], tq);
-          flags |= CCD_FLAG_ITER_CAP;
-          atomicAdd(&wc.n_cap, 1u);
-          --cnt;
-          unit_end = true;
-        } else {
-          evaluate = true;
+          W.up(a);
         }
+        tq = m < tq ? m : tq;
+        if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);       // (modes 1, 2: as an accept)
+        if (A.mode == 2) atomicMin(&A.toi_scene[SID[tid]], tq);
+        flags |= CCD_FLAG_ITER_CAP;
+        atomicAdd(&wc.n_cap, 1u);
+        --cnt;
+        unit_end = true;
+      } else {
+        evaluate = true;
       }
-      if (evaluate) {
-        ++n_eval;
-        // Single-precision filter: when every level is <= 24 the interval's
-        // ends are exact floats and the FP32 hull is within e32 of the FP64
-        // hull, its certified ends L, H bound R's; a miss, or a split (no miss,
-        // not narrow, not inside), proven on it is certainly the FP64 decision,
-        // so FP64 runs only on the rest.
-        bool decided = false, miss = false, accept = false;
-        bool full = true;            // the full FP64 evaluation decides
-        unsigned need = 0, tb = 0;   // ends FP32 left open: bit x low, bit 3 + x high
-        if (max(max(N.l0, N.l1), N.l2) <= 24) {
-          Box3f Bf;
-          float cc0[3], cdc[3];
-  #pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            cc0[x] = SQ.cc0[x][tid];
-            cdc[x] = SQ.cdc[x][tid];
-          }
-          inclusion32(c0f, dcf, cc0, cdc, vf, dyadic32(N.n0, N.l0), dyadic32(N.n0 + 1, N.l0), dyadic32(N.n1, N.l1),
-                      dyadic32(N.n1 + 1, N.l1), dyadic32(N.n2, N.l2), dyadic32(N.n2 + 1, N.l2), Bf);
-          // (levels <= 24 here: the corner checks below take their ends as
-          // exact doubles from these floats)
-          bool cmiss = false, cni = false, cnn = false;
-  #pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            cmiss |= (Bf.lo[x] > tm[x]) | (Bf.hi[x] < -tm[x]);
-            need |= (Bf.L[x] <= tn[x] ? 0u : 1u << x) | (Bf.H[x] >= -tn[x] ? 0u : 8u << x);
-            cni |= (Bf.lo[x] < -tm[x]) | (Bf.hi[x] > tm[x]);
-            cnn |= __fsub_rn(Bf.hi[x], Bf.lo[x]) >= wn[x];
-          }
-          tb = Bf.tb;
-          if (cmiss) {
-            decided = miss = true;
-          } else if (cni & cnn) {
-            full = false;
-            decided = need == 0;   // split
-          }
+    }
+    if (evaluate) {
+      ++n_eval;
+      // Single-precision filter: when every level is <= 24 the interval's
+      // ends are exact floats and the FP32 hull is within e32 of the FP64
+      // hull, its certified ends L, H bound R's; a miss, or a split (no miss,
+      // not narrow, not inside), proven on it is certainly the FP64 decision,
+      // so FP64 runs only on the rest.
+      bool decided = false, miss = false, accept = false;
+      bool full = true;            // the full FP64 evaluation decides
+      unsigned need = 0, tb = 0;   // ends FP32 left open: bit x low, bit 3 + x high
+      if (max(max(N.l0, N.l1), N.l2) <= 24) {
+        Box3f Bf;
+        float cc0[3], cdc[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          cc0[x] = SQ.cc0[x][tid];
+          cdc[x] = SQ.cdc[x][tid];
         }
-        // Not narrow and not inside, and "no miss" settled on every end but a
-        // few: each remaining end is checked on one FP64 corner, the one the FP64
-        // hull selects at the t end tb names, computed with the FP64 hull's own
-        // operations.  The FP64 low end is the smaller of its two
-        // t ends, so a low corner at or below e means no miss on that side, as
-        // the full evaluation would find; likewise a high corner at or above -e.
-        // An end the corner leaves open goes to the full FP64 evaluation.
-        if (!decided && !full) {
-          const double ul = f2d_exact(dyadic32(N.n1, N.l1)), ur = f2d_exact(dyadic32(N.n1 + 1, N.l1));
-          const double vl = f2d_exact(dyadic32(N.n2, N.l2)), vr = f2d_exact(dyadic32(N.n2 + 1, N.l2));
-  #pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            if (need & (9u << x)) {
-              const bool nlo = (need >> x) & 1u, nhi = (need >> (3 + x)) & 1u;
-              double w = SQ.c0[x][tid], a = SQ.c0[3 + x][tid], b = SQ.c0[6 + x][tid];
-              const double dw = SQ.dc[x][tid], da = SQ.dc[3 + x][tid], db = SQ.dc[6 + x][tid];
-              // an axis with no motion: fma(t, 0, c) is c (up to the sign of a
-              // zero, which neither the selection nor the ordered keys see)
-              if (((__double_as_longlong(dw) | __double_as_longlong(da) | __double_as_longlong(db)) << 1) != 0) {
-                const bool at_r = nlo ? ((tb >> x) & 1u) : ((tb >> (3 + x)) & 1u);
-                const double tt = f2d_exact(dyadic32(N.n0 + (at_r ? 1 : 0), N.l0));
-                w = fma(tt, dw, w);
-                a = fma(tt, da, a);
-                b = fma(tt, db, b);
-              }
-              const bool ap = __double_as_longlong(a) > 0;
-              const bool bp = __double_as_longlong(b) > 0;
-              if (nlo) {
-                const double fmin = vf ? fma(-(ap ? ur : ul), a, fma(-(bp ? vr : vl), b, w))
-                                       : fma(-(bp ? vr : vl), b, fma(ap ? ul : ur, a, w));
-                if (f64_ord(fmin) <= SQ.ep[x][tid]) need &= ~(1u << x);
-              }
-              if (nhi) {
-                const double fmax = vf ? fma(-(ap ? ul : ur), a, fma(-(bp ? vl : vr), b, w))
-                                       : fma(-(bp ? vl : vr), b, fma(ap ? ur : ul, a, w));
-                if (f64_ord(fmax) >= SQ.en[x][tid]) need &= ~(8u << x);
-              }
-            }
-          }
+        inclusion32(c0f, dcf, cc0, cdc, vf, dyadic32(N.n0, N.l0), dyadic32(N.n0 + 1, N.l0), dyadic32(N.n1, N.l1),
+                    dyadic32(N.n1 + 1, N.l1), dyadic32(N.n2, N.l2), dyadic32(N.n2 + 1, N.l2), Bf);
+        // (levels <= 24 here: the corner checks below take their ends as
+        // exact doubles from these floats)
+        bool cmiss = false, cni = false, cnn = false;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          cmiss |= (Bf.lo[x] > tm[x]) | (Bf.hi[x] < -tm[x]);
+          need |= (Bf.L[x] <= tn[x] ? 0u : 1u << x) | (Bf.H[x] >= -tn[x] ? 0u : 8u << x);
+          cni |= (Bf.lo[x] < -tm[x]) | (Bf.hi[x] > tm[x]);
+          cnn |= __fsub_rn(Bf.hi[x], Bf.lo[x]) >= wn[x];
+        }
+        tb = Bf.tb;
+        if (cmiss) {
+          decided = miss = true;
+        } else if (cni & cnn) {
+          full = false;
           decided = need == 0;   // split
         }
-        if (!decided) {
-          ++n_eval64;
-          const double tr = dyadic(N.n0 + 1, N.l0);
-          const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
-          const double vl = dyadic(N.n2, N.l2), vr = dyadic(N.n2 + 1, N.l2);
-          Box3 B;
-          inclusion_shared(SQ, tid, vf, dyadic(N.n0, N.l0), tr, ul, ur, vl, vr, B);
-          bool inside = true, narrow = true;
-  #pragma unroll
-          for (int x = 0; x < 3; ++x) {
-            const long long lo = f64_ord(B.lo[x]), hi = f64_ord(B.hi[x]);
-            const long long ep = SQ.ep[x][tid], en = SQ.en[x][tid];
-            miss |= (lo > ep) | (hi < en);
-            inside &= (lo >= en) & (hi <= ep);
-            narrow &= dbits(__dsub_rn(B.hi[x], B.lo[x])) < delta_bits;
+      }
+      // Not narrow and not inside, and "no miss" settled on every end but a
+      // few: each remaining end is checked on one FP64 corner, the one the FP64
+      // hull selects at the t end tb names, computed with the FP64 hull's own
+      // operations.  The FP64 low end is the smaller of its two
+      // t ends, so a low corner at or below e means no miss on that side, as
+      // the full evaluation would find; likewise a high corner at or above -e.
+      // An end the corner leaves open goes to the full FP64 evaluation.
+      if (!decided && !full) {
+        const double ul = f2d_exact(dyadic32(N.n1, N.l1)), ur = f2d_exact(dyadic32(N.n1 + 1, N.l1));
+        const double vl = f2d_exact(dyadic32(N.n2, N.l2)), vr = f2d_exact(dyadic32(N.n2 + 1, N.l2));
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          if (need & (9u << x)) {
+            const bool nlo = (need >> x) & 1u, nhi = (need >> (3 + x)) & 1u;
+            double w = SQ.c0[x][tid], a = SQ.c0[3 + x][tid], b = SQ.c0[6 + x][tid];
+            const double dw = SQ.dc[x][tid], da = SQ.dc[3 + x][tid], db = SQ.dc[6 + x][tid];
+            // an axis with no motion: fma(t, 0, c) is c (up to the sign of a
+            // zero, which neither the selection nor the ordered keys see)
+            if (((__double_as_longlong(dw) | __double_as_longlong(da) | __double_as_longlong(db)) << 1) != 0) {
+              const bool at_r = nlo ? ((tb >> x) & 1u) : ((tb >> (3 + x)) & 1u);
+              const double tt = f2d_exact(dyadic32(N.n0 + (at_r ? 1 : 0), N.l0));
+              w = fma(tt, dw, w);
+              a = fma(tt, da, a);
+              b = fma(tt, db, b);
+            }
+            const bool ap = __double_as_longlong(a) > 0;
+            const bool bp = __double_as_longlong(b) > 0;
+            if (nlo) {
+              const double fmin = vf ? fma(-(ap ? ur : ul), a, fma(-(bp ? vr : vl), b, w))
+                                     : fma(-(bp ? vr : vl), b, fma(ap ? ul : ur, a, w));
+              if (f64_ord(fmin) <= SQ.ep[x][tid]) need &= ~(1u << x);
+            }
+            if (nhi) {
+              const double fmax = vf ? fma(-(ap ? ul : ur), a, fma(-(bp ? vl : vr), b, w))
+                                     : fma(-(bp ? vl : vr), b, fma(ap ? ur : ul, a, w));
+              if (f64_ord(fmax) >= SQ.en[x][tid]) need &= ~(8u << x);
+            }
           }
-          // zero-TOI rule: an interval starting at t = 0 is always split
-          accept = (narrow || inside) && !(A.no_zero && N.n0 == 0);
         }
-        if (!miss) {
-          int a = -1;
-          if (!accept) {
-            a = split_axis(K, N);
-            if (a < 0) {
-              accept = true;
-              flags |= CCD_FLAG_LEVEL_CAP;
-            }
+        decided = need == 0;   // split
+      }
+      if (!decided) {
+        ++n_eval64;
+        const double tr = dyadic(N.n0 + 1, N.l0);
+        const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
+        const double vl = dyadic(N.n2, N.l2), vr = dyadic(N.n2 + 1, N.l2);
+        Box3 B;
+        inclusion_shared(SQ, tid, vf, dyadic(N.n0, N.l0), tr, ul, ur, vl, vr, B);
+        bool inside = true, narrow = true;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const long long lo = f64_ord(B.lo[x]), hi = f64_ord(B.hi[x]);
+          const long long ep = SQ.ep[x][tid], en = SQ.en[x][tid];
+          miss |= (lo > ep) | (hi < en);
+          inside &= (lo >= en) & (hi <= ep);
+          narrow &= dbits(__dsub_rn(B.hi[x], B.lo[x])) < delta_bits;
+        }
+        // zero-TOI rule: an interval starting at t = 0 is always split
+        accept = (narrow || inside) && !(A.no_zero && N.n0 == 0);
+      }
+      if (!miss) {
+        int a = -1;
+        if (!accept) {
+          a = split_axis(K, N);
+          if (a < 0) {
+            accept = true;
+            flags |= CCD_FLAG_LEVEL_CAP;
           }
-          if (accept) {
-            tq = dbits(dyadic(N.n0, N.l0));
-            if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);
-            if (A.mode == 2) atomicMin(&A.toi_scene[SID[tid]], tq);
-            // Every owed sibling that starts at or after T = this node's t_lo is
-            // now pruned; drop them from the path at once instead of visiting
-            // them one by one.  A t-sibling starts after T (T lies in its left
-            // neighbour); a u- or v-sibling at depth d starts at the t_lo of
-            // the path node at depth d - 1, which is below T only if the path
-            // went right along t somewhere at depth >= d.
-            const int D = tright ? 31 - __clz((int)tright) : 0;
-            pend &= (axlo | axhi) & (D >= 31 ? ~0u : (2u << D) - 1u);
-          } else {
-            N.down_left(a);
-            depth += 1;
-            node_done = false;
-            if (depth - rb < 32) {
-              const unsigned bit = 1u << (depth - rb);
-              // the right child is owed unless it is already pruned (t* only
-              // falls) or lies outside the vertex-face simplex
-              bool owe = true;
-              if (a == 0) {
-                owe = s53(N.n0 + 1, N.l0) < cut53;
-              } else if (vf) {
-                owe = !(a == 1 ? s53(N.n1 + 1, N.l1) + s53(N.n2, N.l2) > (1ull << 53)
-                               : s53(N.n1, N.l1) + s53(N.n2 + 1, N.l2) > (1ull << 53));
-              }
-              pend = owe ? (pend | bit) : (pend & ~bit);
-              tright &= ~bit;
-              axlo = (a & 1) ? (axlo | bit) : (axlo & ~bit);
-              axhi = (a & 2) ? (axhi | bit) : (axhi & ~bit);
-            } else {
-              deep = true;
+        }
+        if (accept) {
+          tq = dbits(dyadic(N.n0, N.l0));
+          if (A.mode == 1) atomicMin(&ctl->toi_bits, tq);
+          if (A.mode == 2) atomicMin(&A.toi_scene[SID[tid]], tq);
+          // Every owed sibling that starts at or after T = this node's t_lo is
+          // now pruned; drop them from the path at once instead of visiting
+          // them one by one.  A t-sibling starts after T (T lies in its left
+          // neighbour); a u- or v-sibling at depth d starts at the t_lo of
+          // the path node at depth d - 1, which is below T only if the path
+          // went right along t somewhere at depth >= d.
+          const int D = tright ? 31 - __clz((int)tright) : 0;
+          pend &= (axlo | axhi) & (D >= 31 ? ~0u : (2u << D) - 1u);
+        } else {
+          N.down_left(a);
+          depth += 1;
+          node_done = false;
+          if (depth - rb < 32) {
+            const unsigned bit = 1u << (depth - rb);
+            // the right child is owed unless it is already pruned (t* only
+            // falls) or lies outside the vertex-face simplex
+            bool owe = true;
+            if (a == 0) {
+              owe = s53(N.n0 + 1, N.l0) < cut53;
+            } else if (vf) {
+              owe = !(a == 1 ? s53(N.n1 + 1, N.l1) + s53(N.n2, N.l2) > (1ull << 53)
+                             : s53(N.n1, N.l1) + s53(N.n2 + 1, N.l2) > (1ull << 53));
             }
+            pend = owe ? (pend | bit) : (pend & ~bit);
+            tright &= ~bit;
+            axlo = (a & 1) ? (axlo | bit) : (axlo & ~bit);
+            axhi = (a & 2) ? (axhi | bit) : (axhi & ~bit);
+          } else {
+            deep = true;
           }
         }
       }
+    }
 
-      // ---- 5. next node: backtrack to the deepest pending right sibling ------
-      if (have && node_done && !unit_end && !deep) {
-        // jump to the deepest owed sibling: undo the splits below it per axis
-        // (popcounts of the axis masks), take the right sibling, and go on
-        // while the sibling is pruned or outside the simplex
-        // (depths relative to rb)
-        const int rr = root_depth - rb;
-        const unsigned above_root = rr >= 31 ? 0u : ~0u << (rr + 1);
-        int dr = depth - rb;
-        while (true) {
-          const unsigned m = pend & above_root;
-          if (m == 0) {
-            unit_end = true;
-            break;
-          }
-          const int ds = 31 - __clz((int)m);
-          const unsigned r = (dr >= 31 ? ~0u : (2u << dr) - 1u) & (ds >= 31 ? 0u : ~0u << (ds + 1));
-          const int c1 = __popc(r & axlo & ~axhi), c2 = __popc(r & axhi);
-          const int c0 = dr - ds - c1 - c2;
-          N.n0 >>= c0;
-          N.l0 -= c0;
-          N.n1 >>= c1;
-          N.l1 -= c1;
-          N.n2 >>= c2;
-          N.l2 -= c2;
-          const int a = (int)((axlo >> ds) & 1u) | ((int)((axhi >> ds) & 1u) << 1);
+    // ---- 5. next node: backtrack to the deepest pending right sibling ------
+    if (have && node_done && !unit_end && !deep) {
+      // jump to the deepest owed sibling: undo the splits below it per axis
+      // (popcounts of the axis masks), take the right sibling, and go on
+      // while the sibling is pruned or outside the simplex
+      // (depths relative to rb)
+      const int rr = root_depth - rb;
+      const unsigned above_root = rr >= 31 ? 0u : ~0u << (rr + 1);
+      int dr = depth - rb;
+      while (true) {
+        const unsigned m = pend & above_root;
+        if (m == 0) {
+          unit_end = true;
+          break;
+        }
+        const int ds = 31 - __clz((int)m);
+        const unsigned r = (dr >= 31 ? ~0u : (2u << dr) - 1u) & (ds >= 31 ? 0u : ~0u << (ds + 1));
+        const int c1 = __popc(r & axlo & ~axhi), c2 = __popc(r & axhi);
+        const int c0 = dr - ds - c1 - c2;
+        N.n0 >>= c0;
+        N.l0 -= c0;
+        N.n1 >>= c1;
+        N.l1 -= c1;
+        N.n2 >>= c2;
+        N.l2 -= c2;
+        const int a = (int)((axlo >> ds) & 1u) | ((int)((axhi >> ds) & 1u) << 1);
+        N.add(a, 1);
+        dr = ds;
+        depth = rb + ds;
+        pend &= ~(~0u << ds);
+        tright = (tright & ~(~0u << ds)) | (a == 0 ? 1u << ds : 0u);
+        const bool pruned = s53(N.n0, N.l0) >= cut53;
+        const bool outside = vf && outside_simplex(N);
+        if (!pruned && !outside) break;
+      }
+    } else if (have && node_done && !unit_end) {
+      while (true) {
+        if (depth == root_depth) {
+          unit_end = true;
+          break;
+        }
+        int a = last_axis(K, N);
+        if ((N.n(a) & 1) == 0) {
           N.add(a, 1);
-          dr = ds;
-          depth = rb + ds;
-          pend &= ~(~0u << ds);
-          tright = (tright & ~(~0u << ds)) | (a == 0 ? 1u << ds : 0u);
+          // a right sibling that would be pruned, or that lies outside the
+          // vertex-face simplex, is done at once (no iteration spent on it)
           const bool pruned = s53(N.n0, N.l0) >= cut53;
           const bool outside = vf && outside_simplex(N);
           if (!pruned && !outside) break;
         }
-      } else if (have && node_done && !unit_end) {
-        while (true) {
-          if (depth == root_depth) {
-            unit_end = true;
-            break;
-          }
-          int a = last_axis(K, N);
-          if ((N.n(a) & 1) == 0) {
-            N.add(a, 1);
-            // a right sibling that would be pruned, or that lies outside the
-            // vertex-face simplex, is done at once (no iteration spent on it)
-            const bool pruned = s53(N.n0, N.l0) >= cut53;
-            const bool outside = vf && outside_simplex(N);
-            if (!pruned && !outside) break;
-          }
-          N.up(a);
-          depth -= 1;
-        }
+        N.up(a);
+        depth -= 1;
       }
+    }
 
-      // ---- 6. finish the unit ------------------------------------------------
-      nev += evaluate ? 1u : 0u;
-      if (have && unit_end) {
-        // (modes 1 and 2 published every accept already: t* and the scene's
-        // t*; the global t* of mode 2 and the per-pair result of mode 0 here)
-        if (tq != kInfBits && A.mode != 1) {
-          if (A.mode == 0)
-            atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
-          atomicMin(&ctl->toi_bits, tq);
-        }
-        if (flags) atomicOr(&A.qflags[q], flags);
-        if (!whole && cnt) atomicAdd(&A.qiters[q], (unsigned long long)cnt);
-        have = false;
-        ended = true;
-      }
-    }   // steps
-
-    // ---- 7. in the tail phase, hand the shallowest pending sibling to the
+    // ---- 6. in the tail phase, hand the shallowest pending sibling to the
     //         ring every 32 x `budget` evaluations of the warp, in one
     //         reservation ---------------------------------------------------
     {
-      unsigned long long cut = tq;
-      if (A.mode == 1) cut = g < cut ? g : cut;
-      if (A.mode == 2) cut = min(SCN[0][tid], cut);
       bool trig = false;   // (the same in every lane)
       if (tail_phase) {
-        const int ne = (int)__reduce_add_sync(FULL, nev);
+        const int ne = __popc(__ballot_sync(FULL, evaluate));
         const long long ws = wc.wsince + ne;
         trig = ws >= 32ll * A.budget;
         __syncwarp(FULL);
@@ -1646,7 +1616,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           wc.wsince = trig ? 0 : ws;
         }
       }
-      const bool want_exp = trig && have;
+      const bool want_exp = trig && have && !unit_end;
       if (trig && __any_sync(FULL, want_exp)) {   // (trig is the same in every lane)
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
@@ -1693,10 +1663,23 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       }
     }
 
+    // ---- 7. finish the unit ------------------------------------------------
+    if (have && unit_end) {
+      // (modes 1 and 2 published every accept already: t* and the scene's
+      // t*; the global t* of mode 2 and the per-pair result of mode 0 here)
+      if (tq != kInfBits && A.mode != 1) {
+        if (A.mode == 0)
+          atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
+        atomicMin(&ctl->toi_bits, tq);
+      }
+      if (flags) atomicOr(&A.qflags[q], flags);
+      if (!whole && cnt) atomicAdd(&A.qiters[q], (unsigned long long)cnt);
+      have = false;
+    }
     // units that ended: one pending decrement per warp for 64 of them (the
     // count stays an over-estimate until the warp flushes, at the latest
     // before it idles)
-    ended_acc += __popc(__ballot_sync(FULL, ended));
+    ended_acc += __popc(__ballot_sync(FULL, unit_end));
     if (ended_acc >= 64) {
       if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)ended_acc));
       ended_acc = 0;
