@@ -1105,7 +1105,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_tiled(SweepArgs A) {
 // first cell.  One thread per copy walks its own range (a few dozen copies):
 // neighbouring lanes read neighbouring copies, so the loads coalesce and are
 // served from L1, and a warp runs as many steps as its longest range.
-// Candidates (vertex-face or edge-edge, no shared vertex) collect in a
+// Pairs that pass the tests on the copies' extents, kinds and cells (hits,
+// a few per lane and step, unevenly spread) queue in a per-warp shared list
+// and are checked 32 at a time, one per lane, against the vertex-face /
+// edge-edge rule and the shared-vertex filter.  Candidates collect in a
 // per-warp shared buffer that is flushed with one atomic per 256 pairs; the
 // exact FP64 test runs afterwards over the whole list (k_exact_filter).  The
 // grid is persistent: the number of copies is known only on the device.
@@ -1163,12 +1166,47 @@ __device__ __forceinline__ void sup_flush(const SweepArgs &A, uint2 *buf, int &c
   cnt = 0;
 }
 
+// Candidates of a warp's pending hits, 32 at a time: lane k takes hit
+// hb[k] (copy indices i, j) and runs the vertex-face / edge-edge rule and the
+// shared-vertex filter on the two copies' boxes; survivors go to the warp's
+// candidate buffer.
+__device__ __forceinline__ void sweep_hits(const SweepArgs &A, const uint2 *hb, int nh, uint2 *buf, int &nbuf) {
+  const int lane = threadIdx.x & 31;
+  bool keep = false;
+  uint2 pr = make_uint2(0u, 0u);
+  if (lane < nh) {
+    const uint2 h = hb[lane];
+    int4 vi = A.s_vid[h.x], vj = A.s_vid[h.y];
+    const unsigned fi = ((uint32_t)vi.w >> 30) & 3u, fj = ((uint32_t)vj.w >> 30) & 3u;
+    vi.w &= 0x3FFFFFFF;
+    vj.w &= 0x3FFFFFFF;
+    bool vf;
+    int p0, p1;
+    if ((fi | fj) == 3u && candidate(vi, box_kind(vi.w, A.nV, A.nE), vj, A.nV, A.nE, vf, p0, p1)) {
+      keep = true;
+      pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)p1);
+    }
+  }
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+  if (m) {
+    if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
+    if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
+    nbuf += __popc(m);
+    __syncwarp();
+  }
+}
+
+constexpr int kHitBuf = 160;   // a warp's pending hits: fewer than 32 + one step's at most 4 x 32
+
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
   __shared__ uint2 sh_sup[kSweepThreads / 32][kSupBuf];
+  __shared__ uint2 sh_hit[kSweepThreads / 32][kHitBuf];
   const int64_t n = (int64_t)*A.n_dev;
   const int lane = threadIdx.x & 31;
   uint2 *buf = sh_sup[threadIdx.x >> 5];
+  uint2 *hb = sh_hit[threadIdx.x >> 5];
   int nbuf = 0;   // warp-uniform
+  int nhit = 0;   // warp-uniform: pending hits in hb
   const int64_t ie = min(n, A.i_end);
   const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
   // a warp takes 32 consecutive copies per round (warp-uniform loop)
@@ -1190,8 +1228,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
     const int ki = box_kind(vi.w, A.nV, A.nE);
     // the copy's range (i, end), 4 copies a step: neighbouring lanes read
     // neighbouring copies, so the loads coalesce and mostly hit L1; ids are
-    // loaded only for pairs that pass the tests on extents, kinds and cells
-    // (one per lane per round)
+    // loaded only for pairs that pass the tests on extents, kinds and cells,
+    // queued per warp and checked 32 at a time
     for (int64_t j0 = i + 1; __any_sync(0xFFFFFFFFu, j0 < end); j0 += 4) {
       unsigned hits = 0;
 #pragma unroll
@@ -1208,32 +1246,31 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
                       : 0u;
         }
       }
-      while (__any_sync(0xFFFFFFFFu, hits)) {
-        bool keep = false;
-        uint2 pr = make_uint2(0u, 0u);
-        if (hits) {
-          const int u = __ffs((int)hits) - 1;
-          hits &= hits - 1u;
-          int4 vj = A.s_vid[j0 + u];
-          const unsigned fj = ((uint32_t)vj.w >> 30) & 3u;
-          vj.w &= 0x3FFFFFFF;
-          bool vf;
-          int p0, p1;
-          if ((fi | fj) == 3u && candidate(vi, ki, vj, A.nV, A.nE, vf, p0, p1)) {
-            keep = true;
-            pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)p1);
-          }
-        }
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
-        if (m) {
-          if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
-          if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
-          nbuf += __popc(m);
-          __syncwarp();
-        }
+      // append this step's hits (copy i, copy j0 + u) to the warp's list
+      const unsigned nh = (unsigned)__popc(hits);
+      unsigned x = nh;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      const unsigned tot = __shfl_sync(0xFFFFFFFFu, x, 31);
+      int pos = nhit + (int)(x - nh);
+      while (hits) {
+        const int u = __ffs((int)hits) - 1;
+        hits &= hits - 1u;
+        hb[pos++] = make_uint2((uint32_t)i, (uint32_t)(j0 + u));
+      }
+      nhit += (int)tot;
+      __syncwarp();
+      while (nhit >= 32) {
+        nhit -= 32;
+        sweep_hits(A, hb + nhit, 32, buf, nbuf);
+        __syncwarp();
       }
     }
   }
+  if (nhit) sweep_hits(A, hb, nhit, buf, nbuf);
   if (nbuf) sup_flush(A, buf, nbuf);
 }
 
@@ -1242,28 +1279,25 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips(SweepArgs A) {
 // (cell, minimum) than (its cell, its maximum).
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
   __shared__ uint2 sh_sup[kSweepThreads / 32][kSupBuf];
+  __shared__ uint2 sh_hit[kSweepThreads / 32][kHitBuf];
   const int64_t n = (int64_t)*A.n_dev;
   const int lane = threadIdx.x & 31;
   uint2 *buf = sh_sup[threadIdx.x >> 5];
+  uint2 *hb = sh_hit[threadIdx.x >> 5];
   int nbuf = 0;   // warp-uniform
+  int nhit = 0;   // warp-uniform: pending hits in hb
   const int64_t ie = min(n, A.i_end);
   const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = A.i_begin + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ie;
        base += wstride) {
     const int64_t i = base + lane;
     longlong2 o1 = make_longlong2(0, 0), o2 = make_longlong2(0, 0);
-    int4 vi = make_int4(-1, -1, -1, 0);
-    unsigned fi = 0u;
     int64_t end = i + 1;
     if (i < ie) {
       o1 = A.s_oth64c[2 * i];
       o2 = A.s_oth64c[2 * i + 1];
-      vi = A.s_vid[i];
-      fi = ((uint32_t)vi.w >> 30) & 3u;   // first cell on each axis
-      vi.w &= 0x3FFFFFFF;
       end = range_end64(A.s_seg, A.s_key64, i, n, A.s_seg[i], A.s_ahi64c[i]);
     }
-    const int ki = box_kind(vi.w, A.nV, A.nE);
     for (int64_t j0 = i + 1; __any_sync(0xFFFFFFFFu, j0 < end); j0 += 4) {
       unsigned hits = 0;
 #pragma unroll
@@ -1273,32 +1307,31 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_strips64(SweepArgs A) {
           hits |= ((p1.x <= o1.y) & (o1.x <= p1.y) & (p2.x <= o2.y) & (o2.x <= p2.y)) ? 1u << u : 0u;
         }
       }
-      while (__any_sync(0xFFFFFFFFu, hits)) {
-        bool keep = false;
-        uint2 pr = make_uint2(0u, 0u);
-        if (hits) {
-          const int u = __ffs((int)hits) - 1;
-          hits &= hits - 1u;
-          int4 vj = A.s_vid[j0 + u];
-          const unsigned fj = ((uint32_t)vj.w >> 30) & 3u;
-          vj.w &= 0x3FFFFFFF;
-          bool vf;
-          int p0, q1;
-          if ((fi | fj) == 3u && candidate(vi, ki, vj, A.nV, A.nE, vf, p0, q1)) {
-            keep = true;
-            pr = make_uint2((uint32_t)p0 | (vf ? 0x80000000u : 0u), (uint32_t)q1);
-          }
-        }
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
-        if (m) {
-          if (nbuf + __popc(m) > kSupBuf) sup_flush(A, buf, nbuf);
-          if (keep) buf[nbuf + __popc(m & ((1u << lane) - 1u))] = pr;
-          nbuf += __popc(m);
-          __syncwarp();
-        }
+      // append this step's hits to the warp's list; check them 32 at a time
+      const unsigned nh = (unsigned)__popc(hits);
+      unsigned x = nh;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      const unsigned tot = __shfl_sync(0xFFFFFFFFu, x, 31);
+      int pos = nhit + (int)(x - nh);
+      while (hits) {
+        const int u = __ffs((int)hits) - 1;
+        hits &= hits - 1u;
+        hb[pos++] = make_uint2((uint32_t)i, (uint32_t)(j0 + u));
+      }
+      nhit += (int)tot;
+      __syncwarp();
+      while (nhit >= 32) {
+        nhit -= 32;
+        sweep_hits(A, hb + nhit, 32, buf, nbuf);
+        __syncwarp();
       }
     }
   }
+  if (nhit) sweep_hits(A, hb, nhit, buf, nbuf);
   if (nbuf) sup_flush(A, buf, nbuf);
 }
 
