@@ -860,6 +860,30 @@ __device__ __forceinline__ void load_record_stage(QueryData &Q, bool &vf, const 
 
 }  // namespace
 
+// Block queue (tail phase): a warp whose lanes all carry work hands its
+// lanes' shallowest owed siblings to the idle warps of its own block through
+// shared memory, so that a long query spreads over the block's four warps
+// without any L2 round trip on the busy warp (the device-wide ring, for
+// other blocks, costs several).  A cell at position p holds a unit when
+// seq == p + 1 and is free for position p + kBQ once its taker stores
+// seq = p + kBQ.  `local` counts the units handed out this way and not yet
+// finished (in the queue or in a lane); they are not in the device-wide
+// `pending` count, so a warp leaves only when its block's count is zero too.
+constexpr int kBQ = 64;                  // cells of a block's queue
+constexpr unsigned long long kBQMax = 32;   // units queued at most
+struct BlockQueue {
+  unsigned long long seq[kBQ];
+  unsigned long long w[kBQ][3];          // t, u, v: numerator | level << 54
+  uint32_t q[kBQ];
+  unsigned long long head, tail;         // positions, monotonic
+  int idle;                              // warps of the block that have no work
+  int local;                             // units handed out through the queue, not finished
+};
+
+__device__ __forceinline__ unsigned long long vload(const unsigned long long *p) {
+  return *(const volatile unsigned long long *)p;
+}
+
 constexpr int kIdleRounds = 1 << 14;   // idle warp rounds before a warp retires
 // idle back-off bounds (ns): warps polling the ring more often than this
 // slow the busy warps of the tail (measured: 0.25-2 us worse, 1-32 us best)
@@ -913,7 +937,15 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   const unsigned long long ring_cap = A.ring_mask + 1;
 
   __shared__ SharedQuery SQ;                 // FP64 part of each lane's query
+  __shared__ BlockQueue BQ;
   const int tid = threadIdx.x;
+  if (tid == 0) {
+    BQ.head = BQ.tail = 0;
+    BQ.idle = 0;
+    BQ.local = 0;
+  }
+  for (int i = tid; i < kBQ; i += blockDim.x) BQ.seq[i] = (unsigned long long)i;
+  __syncthreads();
   // single-precision filter data and split keys of the lane's query
   float c0f[3][3], dcf[3][3], tn[3], tm[3], wn[3];
   unsigned long long K[3] = {0, 0, 0};
@@ -924,6 +956,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   __shared__ unsigned long long SCN[2][kNarrowThreads];
   SCN[0][tid] = SCN[1][tid] = kInfBits;
   bool have = false, fresh = false, whole = false;
+  bool blocal = false;                       // the unit came through the block queue
+  bool widle = false;                        // warp-uniform: counted in BQ.idle
   bool exhausted = false;                    // warp-uniform
   int64_t q = -1;   // the query whose data the lane's registers and shared column hold (-1: none yet)
   Node N{0, 0, 0, 0, 0, 0};
@@ -948,6 +982,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
   unsigned flags = 0;
   unsigned n_eval = 0, n_eval64 = 0;          // per lane, per launch
   int idle_rounds = 0;                       // warp-uniform: idle rounds in a row
+  int bq_polls = 0;                          // warp-uniform: block-queue polls since the last round
   unsigned ended_acc = 0;                    // warp-uniform: ended units not yet subtracted from pending
   // Shared values (global t*, next query, the scene's t*) are read from L2
   // every kRefresh iterations into a second slot and used from the first,
@@ -1113,6 +1148,38 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
                             : 0;
         if (lane == 0 && got) atomicAdd(&ctl->pending, (unsigned long long)got);
       }
+      // A warp with no work at all takes first from its block's queue (up to
+      // one cell per lane: lanes test the cells' sequence numbers, lane 0
+      // claims the ready prefix with one shared-memory CAS).
+      if (exhausted && __ballot_sync(FULL, have) == 0) {
+        unsigned long long h = 0;
+        if (lane == 0) h = vload(&BQ.head);
+        h = __shfl_sync(FULL, h, 0);
+        const bool ready = vload(&BQ.seq[(h + lane) % kBQ]) == h + lane + 1;
+        const unsigned rb = __ballot_sync(FULL, ready);
+        const int r = rb == FULL ? 32 : __ffs(~rb) - 1;
+        int ok = 0;
+        if (r > 0 && lane == 0) ok = atomicCAS(&BQ.head, h, h + r) == h;
+        ok = __shfl_sync(FULL, ok, 0);
+        if (ok && lane < r) {
+          const int cell = (int)((h + lane) % kBQ);
+          __threadfence_block();   // the cell's contents after its sequence number
+          const unsigned long long w0 = BQ.w[cell][0], w1 = BQ.w[cell][1], w2 = BQ.w[cell][2];
+          const unsigned long long m54 = (1ull << 54) - 1;
+          q = BQ.q[cell];
+          N.n0 = w0 & m54;
+          N.n1 = w1 & m54;
+          N.n2 = w2 & m54;
+          N.l0 = (int)(w0 >> 54);
+          N.l1 = (int)(w1 >> 54);
+          N.l2 = (int)(w2 >> 54);
+          __threadfence_block();   // read before the cell is freed
+          *(volatile unsigned long long *)&BQ.seq[cell] = h + lane + kBQ;
+          have = fresh = true;
+          whole = false;
+          blocal = true;
+        }
+      }
       // Only a warp with no work at all takes from the ring: a warp with busy
       // lanes fills its idle ones by donation below (shuffles and shared
       // memory), which costs none of the ring's L2 round trips that would
@@ -1148,6 +1215,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           st_release_u64(&c->seq, pos + A.ring_mask + 1);   // free for the next lap
           have = fresh = true;
           whole = false;
+          blocal = false;
         }
       }
       // Intra-warp donation: lanes still idle (no query left; the ring is for
@@ -1241,6 +1309,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
             flags = 0;
             have = true;
             whole = false;
+            blocal = false;
           }
           if (give) {
             root_depth = dS;   // the donated sibling is no longer ours
@@ -1265,20 +1334,43 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         ended_acc = 0;
         __threadfence();
       }
+      if (!widle) {
+        if (lane == 0) atomicAdd(&BQ.idle, 1);
+        widle = true;
+      }
+      // While a warp of the block still works (it may queue units), poll the
+      // block's queue every kNapMin (at once while it holds units) and the
+      // device-wide state every 32 polls; otherwise back off, kNapMin
+      // doubling up to kNapMax.
+      const bool items = exhausted && vload(&BQ.tail) != vload(&BQ.head);
+      const bool mates_busy = *(volatile int *)&BQ.idle < (int)(blockDim.x >> 5);
+      if ((items || mates_busy) && ++bq_polls < 32) {
+        if (!items) __nanosleep(kNapMin);
+        continue;
+      }
+      bq_polls = 0;
       int stop = 0;
       if (lane == 0) {
         const unsigned long long h = ld_relaxed_u64(&ctl->q_head), t = ld_relaxed_u64(&ctl->q_tail);
         const unsigned long long pend = ld_relaxed_u64(&ctl->pending);
         wc.pf_occ = t > h ? t - h : 0;   // an idle warp sees new exports at once
-        stop = (exhausted && wc.pf_occ == 0 && pend == 0) || idle_rounds >= kIdleRounds;
+        stop = (exhausted && wc.pf_occ == 0 && pend == 0 && *(volatile int *)&BQ.local == 0) ||
+               idle_rounds >= kIdleRounds;
       }
-      if (__shfl_sync(FULL, stop, 0)) break;
-      // back off while nothing turns up: kNapMin doubling up to kNapMax
-      __nanosleep(min(kNapMin << min(idle_rounds, 5), kNapMax));
-      ++idle_rounds;
+      if (__shfl_sync(FULL, stop, 0)) {
+        if (lane == 0) atomicSub(&BQ.idle, 1);   // (no longer there to take units)
+        break;
+      }
+      __nanosleep(mates_busy ? kNapMin : min(kNapMin << min(idle_rounds, 5), kNapMax));
+      ++idle_rounds;   // (while a block mate works: one round per 32 polls of the block's queue)
       continue;
     }
     idle_rounds = 0;
+    bq_polls = 0;
+    if (widle) {
+      if (lane == 0) atomicSub(&BQ.idle, 1);
+      widle = false;
+    }
 
     // ---- 3. set up newly acquired units ------------------------------------
     if (fresh) {
@@ -1605,7 +1697,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     //         ring every 32 x `budget` evaluations of the warp, in one
     //         reservation ---------------------------------------------------
     {
-      bool trig = false;   // (the same in every lane)
+      bool trig = false;    // to the ring (the same in every lane)
+      bool btrig = false;   // to the block's queue (the same in every lane)
       if (tail_phase) {
         const int ne = __popc(__ballot_sync(FULL, evaluate));
         const long long ws = wc.wsince + ne;
@@ -1615,9 +1708,14 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           wc.n_eval_tail += ne;
           wc.wsince = trig ? 0 : ws;
         }
+        // a warp of the block idles and few units wait in the block's queue
+        int b = 0;
+        if (!trig && lane == 0)
+          b = *(volatile int *)&BQ.idle > 0 && vload(&BQ.tail) - vload(&BQ.head) < kBQMax / 4;
+        btrig = __shfl_sync(FULL, b, 0) != 0;
       }
-      const bool want_exp = trig && have && !unit_end;
-      if (trig && __any_sync(FULL, want_exp)) {   // (trig is the same in every lane)
+      const bool want_exp = (trig || btrig) && have && !unit_end;
+      if ((trig || btrig) && __any_sync(FULL, want_exp)) {   // (trig, btrig are the same in every lane)
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
         if (want_exp) {
@@ -1629,7 +1727,64 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
           }
         }
         const unsigned xm = __ballot_sync(FULL, dS > 0);
-        if (xm) {
+        if (xm && btrig) {
+          // block queue: reserve up to one cell per lane with a sibling
+          unsigned long long pos0 = ~0ull;
+          int mm = 0;
+          if (lane == 0) {
+            for (int tries = 0; tries < 32; ++tries) {
+              const unsigned long long t = vload(&BQ.tail), h = vload(&BQ.head);
+              const unsigned long long room = t - h >= kBQMax ? 0ull : kBQMax - (t - h);
+              mm = (int)min((unsigned long long)__popc(xm), room);
+              if (mm == 0) break;
+              if (atomicCAS(&BQ.tail, t, t + mm) == t) {
+                pos0 = t;
+                atomicAdd(&BQ.local, mm);   // counted before any of them is visible
+                break;
+              }
+            }
+          }
+          pos0 = __shfl_sync(FULL, pos0, 0);
+          mm = __shfl_sync(FULL, mm, 0);
+          const int rank = __popc(xm & lt_mask);
+          if (pos0 != ~0ull && dS > 0 && rank < mm) {
+            const unsigned long long pos = pos0 + rank;
+            const int cell = (int)(pos % kBQ);
+            // the cell's previous occupant (kBQ positions back) was taken
+            // already; wait until its taker has freed it
+            bool freed = true;
+            for (int spin = 0; vload(&BQ.seq[cell]) != pos; ++spin) {
+              if (spin > (1 << 20)) {
+                atomicExch(&ctl->status, CCD_ETIMEOUT);
+                freed = false;
+                break;
+              }
+              __nanosleep(32);
+            }
+            if (freed) {
+              if (tq != kInfBits) {
+                if (A.mode == 0)
+                  atomicMin(q < A.n_vf ? &A.toi_vf_bits[q] : &A.toi_ee_bits[q - A.n_vf], tq);
+                else if (A.mode == 2)
+                  atomicMin(&A.toi_scene[SID[tid]], tq);
+                else
+                  atomicMin(&ctl->toi_bits, tq);
+              }
+              atomicAdd(&A.qiters[q], (unsigned long long)cnt);
+              cap_left = min(kBudgetWindow, cap_left - cnt);   // (the query's budget is shared from now on)
+              cnt = 0;
+              whole = false;
+              BQ.w[cell][0] = pack1(S.n0, S.l0);
+              BQ.w[cell][1] = pack1(S.n1, S.l1);
+              BQ.w[cell][2] = pack1(S.n2, S.l2);
+              BQ.q[cell] = (uint32_t)q;
+              __threadfence_block();
+              *(volatile unsigned long long *)&BQ.seq[cell] = pos + 1;
+              root_depth = dS;
+              atomicAdd(&wc.n_don, 1u);
+            }
+          }
+        } else if (xm) {
           unsigned long long pos0 = ~0ull;
           if (lane == 0) {
             pos0 = ring_reserve(&ctl->q_tail, &ctl->q_head, (unsigned long long)__popc(xm), ring_cap >> 2);
@@ -1674,12 +1829,14 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       }
       if (flags) atomicOr(&A.qflags[q], flags);
       if (!whole && cnt) atomicAdd(&A.qiters[q], (unsigned long long)cnt);
+      if (blocal) atomicSub(&BQ.local, 1);
       have = false;
     }
     // units that ended: one pending decrement per warp for 64 of them (the
     // count stays an over-estimate until the warp flushes, at the latest
-    // before it idles)
-    ended_acc += __popc(__ballot_sync(FULL, unit_end));
+    // before it idles); units of the block queue are counted in BQ.local
+    ended_acc += __popc(__ballot_sync(FULL, unit_end && !blocal));
+    if (unit_end) blocal = false;
     if (ended_acc >= 64) {
       if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)ended_acc));
       ended_acc = 0;
