@@ -60,11 +60,11 @@ HBM_FALLBACK_GBS = 6800.0
 # / smsp__inst_executed.sum, sm__warps_active), keyed by the source hash.
 NCU_ISSUE = {
     # ncu --replay-mode application --clock-control none --metrics smsp__inst_executed.sum,
-    #     smsp__thread_inst_executed.sum,sm__warps_active... -k regex:"^k_narrow$|..." -s 24 -c 6
-    #     python bench.py --n 256 --steps 1 --warmup 3 --no-cpu-baseline --no-forms --no-autotune
-    #     (789.4M warp instructions over 18,578,774 intervals)
-    "k_narrow": {"warp_inst_per_interval": 42.49, "threads_per_inst": 18.67, "warps_active": 0.1859,
-                 "src": "09bafc2baa5205b7",
+    #     smsp__thread_inst_executed.sum,sm__warps_active...,smsp__issue_active...  -k regex:"^k_narrow$|^k_sweep_strips$"
+    #     -s 8 -c 2  python bench.py --n 256 --steps 1 --warmup 3 --no-cpu-baseline --no-forms --no-autotune
+    #     (804.2M warp instructions; 18.45M intervals, the mean of the three replayed runs)
+    "k_narrow": {"warp_inst_per_interval": 43.59, "threads_per_inst": 18.84, "warps_active": 0.1872,
+                 "src": "22d248e21b4a7a93",
                  "cmd": "ncu --replay-mode application, 256 x 256 cloth, bench.py --no-autotune"},
 }
 
@@ -75,8 +75,8 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
     #     -k regex:"^k_narrow$|..." -s 28 -c 7
     #     python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-forms --no-autotune
-    #     (1.605 GB read + 57.05 MB written)
-    "k_narrow": (1.605e9 + 57.05e6, "09bafc2baa5205b7"),
+    #     (1.610 GB read + 56.2 MB written)
+    "k_narrow": (1.610e9 + 56.21e6, "22d248e21b4a7a93"),
 }
 
 
