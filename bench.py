@@ -739,7 +739,7 @@ def form_batch(envs, steps, warmup):
             "batch512_ms": rep}
 
 
-def form_serve(envs, rate, n_slots=2, verify=32, clients=4):
+def form_serve(envs, rate, n_slots=2, verify=32, clients=8):
     """Serving form: the environments arrive as a Poisson stream; at its
     arrival time a client hands the scene, held in the arena's layout (V0, V1
     as [3][nV], E, F), to ccd_server_submit_scene, which copies it into the
