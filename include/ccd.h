@@ -124,7 +124,8 @@ typedef struct {
     int64_t n_launches;      /* kernels this context launched since creation */
     int64_t narrow_bulk_ns;  /* narrow kernel: start until every query was taken */
     int64_t narrow_tail_ns;  /* narrow kernel: from then until the last lane ended */
-    int64_t n_donated;       /* subtrees passed between lanes of one warp */
+    int64_t n_donated;       /* subtrees passed between lanes of one warp, or between
+                                warps of one block through shared memory */
     int64_t n_intervals_tail;  /* intervals evaluated after every query was taken */
     int64_t n_intervals_fp64;  /* intervals the single-precision filter left to FP64 */
     int64_t n_box_copies;    /* cell sweep: boxes placed in cells, counting each

@@ -31,7 +31,7 @@ struct DevCtl {
   unsigned long long n_exported, n_capped, queue_peak;
   long long pair_counts[2];      // ccd_step: pairs for the narrow phase (clamped)
   unsigned long long t_start, t_exhausted, t_end;  // %globaltimer stamps of the narrow kernel
-  unsigned long long n_donated;  // subtrees passed between lanes of a warp
+  unsigned long long n_donated;  // subtrees passed between lanes of a warp or warps of a block
   unsigned long long n_intervals_tail;  // intervals evaluated after the query list ran out
   unsigned long long n_intervals_fp64;  // intervals the FP32 filter could not decide
   int rerun;                     // zero-TOI rule: 1 when the second pass must run
