@@ -747,6 +747,7 @@ def form_serve(envs, rate, n_slots=2, verify=32, clients=8):
     in turn).
     Latency runs from the arrival (before the write) to the completion; a
     sample of results is compared with the scene stepped alone."""
+    import gc
     import threading
     from paper_2112_06300_gb300 import ccd
     srv = ccd.Server(0, n_slots=n_slots, max_scenes=256, memory_cap=BUDGET, arena_bytes=4 << 30,
@@ -761,6 +762,11 @@ def form_serve(envs, rate, n_slots=2, verify=32, clients=8):
     tickets = [None] * len(envs)
     late_ms = np.zeros(len(envs))                  # arrival -> the client starts writing
     write_ms = np.zeros(len(envs))                 # writing and queueing the scene
+    # Python's collector stops every client thread while it runs (tens of ms
+    # once the process holds the other configurations' data): collect before
+    # the arrivals start and not during them
+    gc.collect()
+    gc.disable()
     t0 = time.perf_counter() + 0.05
 
     def client(ks):
@@ -778,13 +784,16 @@ def form_serve(envs, rate, n_slots=2, verify=32, clients=8):
             late_ms[k] = (tw - (t0 + arrive[k])) * 1e3
 
     th = [threading.Thread(target=client, args=(range(i, len(envs), clients),)) for i in range(clients)]
-    for t in th:
-        t.start()
-    for t in th:
-        t.join()
-    t_sub = time.perf_counter() - t0
-    res = [srv.wait(t) for t in tickets]
-    t_all = time.perf_counter() - t0
+    try:
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        t_sub = time.perf_counter() - t0
+        res = [srv.wait(t) for t in tickets]
+        t_all = time.perf_counter() - t0
+    finally:
+        gc.enable()
     st = srv.stats()
     srv.close()
     lat_srv = np.array([r[1] for r in res])       # submission -> completion
