@@ -62,9 +62,9 @@ NCU_ISSUE = {
     # ncu --replay-mode application --clock-control none --metrics smsp__inst_executed.sum,
     #     smsp__thread_inst_executed.sum,sm__warps_active...,smsp__issue_active...  -k regex:"^k_narrow$|^k_sweep_strips$"
     #     -s 8 -c 2  python bench.py --n 256 --steps 1 --warmup 3 --no-cpu-baseline --no-forms --no-autotune
-    #     (804.2M warp instructions; 18.45M intervals, the mean of the three replayed runs)
-    "k_narrow": {"warp_inst_per_interval": 43.59, "threads_per_inst": 18.84, "warps_active": 0.1872,
-                 "src": "22d248e21b4a7a93",
+    #     (808.3M warp instructions; 18.49M intervals, the mean of the three replayed runs)
+    "k_narrow": {"warp_inst_per_interval": 43.72, "threads_per_inst": 18.92, "warps_active": 0.1873,
+                 "src": "75bbf3809412df04",
                  "cmd": "ncu --replay-mode application, 256 x 256 cloth, bench.py --no-autotune"},
 }
 
@@ -75,8 +75,8 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
     #     -k regex:"^k_narrow$|..." -s 28 -c 7
     #     python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-forms --no-autotune
-    #     (1.610 GB read + 56.2 MB written)
-    "k_narrow": (1.610e9 + 56.21e6, "22d248e21b4a7a93"),
+    #     (1.612 GB read + 56.4 MB written)
+    "k_narrow": (1.612e9 + 56.43e6, "75bbf3809412df04"),
 }
 
 

@@ -884,6 +884,16 @@ __device__ __forceinline__ unsigned long long vload(const unsigned long long *p)
   return *(const volatile unsigned long long *)p;
 }
 
+// Branches the bulk of the launch rarely takes (the tail's work sharing,
+// idling, the iteration and level caps, the full FP64 evaluation, paths
+// deeper than the masks): hinted, so that the common path stays contiguous
+// in the instruction cache.
+#ifndef CCD_NO_HINTS
+#define CCD_COLD(c) __builtin_expect(!!(c), 0)
+#else
+#define CCD_COLD(c) (c)
+#endif
+
 constexpr int kIdleRounds = 1 << 14;   // idle warp rounds before a warp retires
 // idle back-off bounds (ns): warps polling the ring more often than this
 // slow the busy warps of the tail (measured: 0.25-2 us worse, 1-32 us best)
@@ -1151,7 +1161,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       // A warp with no work at all takes first from its block's queue (up to
       // one cell per lane: lanes test the cells' sequence numbers, lane 0
       // claims the ready prefix with one shared-memory CAS).
-      if (exhausted && __ballot_sync(FULL, have) == 0) {
+      if (CCD_COLD(exhausted && __ballot_sync(FULL, have) == 0)) {
         unsigned long long h = 0;
         if (lane == 0) h = vload(&BQ.head);
         h = __shfl_sync(FULL, h, 0);
@@ -1184,7 +1194,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       // lanes fills its idle ones by donation below (shuffles and shared
       // memory), which costs none of the ring's L2 round trips that would
       // otherwise sit on the path of the tail's long queries.
-      if (exhausted && __ballot_sync(FULL, have) == 0 && wc.pf_occ > 0) {
+      if (CCD_COLD(exhausted && __ballot_sync(FULL, have) == 0 && wc.pf_occ > 0)) {
         // pop up to one cell per idle lane: lanes test the cells' sequence
         // numbers in parallel, lane 0 claims the ready prefix with one CAS
         const unsigned m = __ballot_sync(FULL, !have);
@@ -1223,7 +1233,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
       // own warp; the query data moves by shuffles, the donor keeps the rest
       // of its subtree (its root moves down to the donated sibling's depth).
       const unsigned idle = __ballot_sync(FULL, !have);
-      if (exhausted && __popc(idle) >= kDonateMin) {
+      if (CCD_COLD(exhausted && __popc(idle) >= kDonateMin)) {
         // candidate donors: the first busy lanes, one per idle lane; only they
         // walk their path to find the shallowest pending sibling
         const unsigned busy = __ballot_sync(FULL, have && !fresh);
@@ -1328,7 +1338,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     }
 
     // ---- 2. a warp with no work idles or retires (uniform) ----------------
-    if (__ballot_sync(FULL, have) == 0) {
+    if (CCD_COLD(__ballot_sync(FULL, have) == 0)) {
       if (ended_acc) {
         if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)ended_acc));
         ended_acc = 0;
@@ -1431,7 +1441,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     // ---- 4. ProcessInterval on the current node ---------------------------
     // shared values loaded during the previous iteration (stale values only
     // prune less or hand off later)
-    if (++pf_age == kRefresh) {
+    if (CCD_COLD(++pf_age == kRefresh)) {
       pf_age = 0;
       if (lane == 0) {
         wc.pf_toi = wc.nx_toi;
@@ -1470,7 +1480,8 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         // pruned: starts at or after the current t*
       } else if (vf && outside_simplex(N)) {
         // vertex-face: u_lo > 1 - v_lo, the interval lies outside the simplex
-      } else if (!(A.no_zero && N.n0 == 0) && ++cnt > cap_left && !next_budget_window(A, q, whole, cnt, cap_left)) {
+      } else if (CCD_COLD(!(A.no_zero && N.n0 == 0) && ++cnt > cap_left &&
+                          !next_budget_window(A, q, whole, cnt, cap_left))) {
         // iteration cap: t* = min(t*, earliest left end among the live intervals)
         unsigned long long m = dbits(dyadic(N.n0, N.l0));
         Node W = N;
@@ -1572,7 +1583,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         }
         decided = need == 0;   // split
       }
-      if (!decided) {
+      if (CCD_COLD(!decided)) {
         ++n_eval64;
         const double tr = dyadic(N.n0 + 1, N.l0);
         const double ul = dyadic(N.n1, N.l1), ur = dyadic(N.n1 + 1, N.l1);
@@ -1595,7 +1606,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         int a = -1;
         if (!accept) {
           a = split_axis(K, N);
-          if (a < 0) {
+          if (CCD_COLD(a < 0)) {
             accept = true;
             flags |= CCD_FLAG_LEVEL_CAP;
           }
@@ -1673,7 +1684,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         const bool outside = vf && outside_simplex(N);
         if (!pruned && !outside) break;
       }
-    } else if (have && node_done && !unit_end) {
+    } else if (CCD_COLD(have && node_done && !unit_end)) {
       while (true) {
         if (depth == root_depth) {
           unit_end = true;
@@ -1699,7 +1710,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
     {
       bool trig = false;    // to the ring (the same in every lane)
       bool btrig = false;   // to the block's queue (the same in every lane)
-      if (tail_phase) {
+      if (CCD_COLD(tail_phase)) {
         const int ne = __popc(__ballot_sync(FULL, evaluate));
         const long long ws = wc.wsince + ne;
         trig = ws >= 32ll * A.budget;
@@ -1715,7 +1726,7 @@ __device__ __forceinline__ void narrow_body(NarrowArgs A) {
         btrig = __shfl_sync(FULL, b, 0) != 0;
       }
       const bool want_exp = (trig || btrig) && have && !unit_end;
-      if ((trig || btrig) && __any_sync(FULL, want_exp)) {   // (trig, btrig are the same in every lane)
+      if (CCD_COLD((trig || btrig) && __any_sync(FULL, want_exp))) {   // (trig, btrig are the same in every lane)
         Node S{0, 0, 0, 0, 0, 0};
         int dS = 0;
         if (want_exp) {
