@@ -11,9 +11,10 @@
 //     the depth at which the lane took its unit.
 //   * Load balance at interval granularity: once every query has been
 //     claimed, idle lanes take the shallowest owed sibling of a busy lane of
-//     their warp, and every 32 x `budget` evaluations a warp hands its lanes'
-//     shallowest owed siblings to a device-wide bounded MPMC ring, which idle
-//     warps drain.  A near-degenerate query (tens of thousands of intervals)
+//     their warp, a warp hands its lanes' shallowest owed siblings to idle
+//     warps of its block through a queue in shared memory, and every
+//     32 x `budget` evaluations it hands them to a device-wide bounded MPMC
+//     ring, which idle warps drain.  A near-degenerate query (tens of thousands of intervals)
 //     is thus spread over many lanes, which is the point of the paper's
 //     per-interval parallelism, without its level-synchronous launches.
 //   * FP64 is the scarce unit on this GPU.  A full evaluation is 18 DFMA for
