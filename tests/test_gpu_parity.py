@@ -181,8 +181,10 @@ def test_narrow_stress_scaled_matches_oracle(ctx, ccd, scale, offset):
 
 def test_narrow_deep_trees_match_oracle(ctx, ccd):
     """delta = 1e-10 takes the bisection past 31 and 63 levels in total (most
-    of the evaluations here), beyond the depth the kernel's path masks cover; deeper units
-    backtrack by walking the path.  The reference is the oracle without an
+    of the evaluations here), beyond the 31 levels below a unit's start that
+    the kernel's path masks cover: deeper units backtrack by walking the path,
+    and the pieces other lanes take from them start masks of their own at
+    their depth.  The reference is the oracle without an
     iteration cap: the GPU result equals it wherever the GPU did not cap the
     query, and is never later where it did (a query split across lanes can
     reach the cap in a different place; capped results are conservative)."""
